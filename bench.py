@@ -1,0 +1,333 @@
+"""Benchmark: A_i + A_i^* pairs per second of GPU SPDHG at 512^2.
+
+Workload (synthetic, seeded; stands in for the paper's walnut/chest slices):
+512 x 512 phantom of 40 random ellipses, 720 angles x 729 bins, N = 10 rigid
+gates (rotation U[-8, 8] deg, shift U[-6, 6] px), data d_i = A_i x + noise at
+1% of the largest clean value, alpha = 1e-3.
+
+One step = one SPDHG epoch = N iterations of Algorithm 1, i.e. N gate draws,
+N warps, N forward projections with the fused dual update, N backprojections
+and N transpose warps with the fused z / zbar / prox update: N pairs.  The
+epoch is replayed as a CUDA graph.  Inputs stay resident in HBM; L2 (129 MB)
+is flushed between steps by writing a 256 MB buffer outside the timed events.
+
+--impl reference times the FP64 CPU oracle (a deliberately slow checker) on
+one pair per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+import mc_synth as S
+
+WORKLOAD = "rigid512"
+METRIC = "A_i+A_i^* pairs/s at 512^2"
+UNIT = "pairs/s"
+
+
+def workload_config(W):
+    return {
+        "workload": f"{W.name}: {W.n}x{W.n} image ({W.n_ellipses} ellipses), {W.n_angles} angles x "
+                    f"{W.n_bins} bins, N={W.n_gates} rigid gates (+-{W.max_rot_deg:g} deg, "
+                    f"+-{W.max_shift:g} px), alpha={W.alpha:g}, SPDHG",
+        "step": f"one SPDHG epoch = {W.n_gates} iterations = {W.n_gates} A_i+A_i^* pairs",
+        "l2": "flushed between steps (256 MB write outside the timed events)",
+    }
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [t.strip() for t in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ setup
+def make_problem(W, torch, mc, rank=0):
+    sd = S.seeds(W.cid, run=rank)
+    rig = S.rigid_motion(W.n_gates, W.max_rot_deg, W.max_shift, sd["motion"])
+    xt = S.phantom(W.n, W.n_ellipses, sd["phantom"], W.axis_lo, W.axis_hi)
+    eps = S.noise(W.n_gates, W.n_angles, W.n_bins, sd["noise"])
+    stream = torch.cuda.Stream()
+    ctx = mc.Context(W.n, W.n_angles, W.n_bins, W.n_gates, rigid=rig, stream=stream.cuda_stream)
+    # data model d_i = A_i x + eps_i, eps_i ~ N(0, sigma^2/N), computed with the GPU operators
+    x_t = torch.as_tensor(xt, dtype=torch.float32, device="cuda")
+    d = torch.empty((W.n_gates, W.n_angles, W.n_bins), dtype=torch.float32, device="cuda")
+    for i in range(W.n_gates):
+        ctx.forward(i, x_t, out=d[i])
+    torch.cuda.synchronize()
+    sigma = W.noise_level * float(d.max())
+    d += torch.as_tensor(eps * (sigma / math.sqrt(W.n_gates)), dtype=torch.float32, device="cuda")
+    ctx.set_data(d, W.alpha)
+    norms = ctx.norms(max_iter=40, tol=1e-7)
+    return ctx, stream, d, norms, sd
+
+
+def algorithmic_units(W):
+    """Joseph samples S per projection (in-image line crossings) and the
+    adjoint's (pixel, angle) pairs, counted from the geometry exactly."""
+    n, na, nb = W.n, W.n_angles, W.n_bins
+    h, hb = 0.5 * (n - 1), 0.5 * (nb - 1)
+    S_cnt = 0
+    for k in range(na):
+        phi = k * math.pi / na
+        c, s = math.cos(phi), math.sin(phi)
+        xd = na <= 4 * k <= 3 * na
+        inv, t = (1 / s, c / s) if xd else (1 / c, s / c)
+        b = np.arange(nb) - hb
+        l = np.arange(n) - h
+        u = b[:, None] * inv - l[None, :] * t + h       # position on each line
+        S_cnt += int(np.count_nonzero((u > -1.0) & (u < n)))
+    return S_cnt
+
+
+def run_ours(args, W):
+    import torch
+
+    import paper_2410_10503_gb300 as mc
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2410_10503_gb300 import build
+    build.build()
+
+    ctx, stream, d, norms, sd = make_problem(W, torch, mc, rank)
+    N = W.n_gates
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ctx.spdhg_run(1, seed=sd["gates"], x_out=False)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 0)):
+            step()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for a, b in evs:
+                flush.zero_()
+                a.record(stream)
+                step()
+                b.record(stream)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        tot_ms = float(sum(step_ms))
+        if dist:
+            t = torch.tensor([tot_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+            dist.barrier()
+    pairs = args.steps * N * world
+    value = pairs / (tot_ms / 1e3)
+
+    # ---- per-kernel durations: same steps, per-launch CUDA events on the
+    # context's stream (plain launches instead of the graph replay)
+    ctx.set_option(2, 1)
+    ctx.profile_reset()
+    with torch.cuda.stream(stream):
+        for _ in range(args.steps):
+            flush.zero_()
+            step()
+    prof = ctx.profile()
+    ctx.set_option(2, 0)
+    kernels = {k: {"launches": c, "avg_us": (ms * 1e3 / c) if c else None} for k, (c, ms) in prof.items()}
+
+    # ---- end to end through the C ABI with host buffers: upload the gated
+    # data from pinned memory, run one epoch, read x back (per step)
+    d_host = d.cpu().pin_memory()
+    x_host = torch.empty((W.n, W.n), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        ctx.set_data(d_host, W.alpha)
+        ctx.spdhg_run(1, seed=sd["gates"], x_out=x_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_data(d_host, W.alpha)
+        ctx.spdhg_run(1, seed=sd["gates"], x_out=x_host)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": args.steps * N * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(d_host.numel() * 4), "d2h_bytes_per_step": int(x_host.numel() * 4)}
+
+    # ---- roofline of the dominant kernel (on-chip gather bytes)
+    S_cnt = algorithmic_units(W)
+    dom = max(("project", "backproject"), key=lambda k: kernels[k]["avg_us"] or 0)
+    if dom == "project":
+        alg_bytes = 8.0 * S_cnt            # two texel reads per in-image sample
+    else:
+        alg_bytes = 8.0 * S_cnt            # one dual value per (pixel, bin) pair: 2S pairs x 4 B
+    avg_s = kernels[dom]["avg_us"] * 1e-6
+    peak = float(args.l1_peak_gbs)
+    achieved = alg_bytes / avg_s / 1e9
+    roof = {"bound": "l1", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
+            "peak_source": "152 SMs x 128 B/clk shared/L1 load x 2.07 GHz (derived)"}
+    hbm_peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            hbm_peak = json.load(f).get("hbm_gbs")
+    except Exception:
+        pass
+
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": workload_config(W) | {"parallelism": f"replicas x{world}"},
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * (1 + 4 * N),
+        "clocks": clk.summary(), "kernels": kernels,
+        "norms2_max": float(np.max(norms[:N])), "kappa_spdhg": ctx.steps()["kappa"],
+        "hbm_peak_gbs_measured": hbm_peak, "wall_s": round(wall, 3),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def _oracle_pair_setup(W):
+    import oracle as O
+    sd = S.seeds(W.cid)
+    g = O.Geometry(W.n, W.n_angles, W.n_bins)
+    rig = S.rigid_motion(W.n_gates, W.max_rot_deg, W.max_shift, sd["motion"])
+    P = O.Problem(g, O.Motion(rigid=rig), np.zeros((W.n_gates, W.n_angles, W.n_bins)), W.alpha)
+    x = S.phantom(W.n, W.n_ellipses, sd["phantom"], W.axis_lo, W.axis_hi)
+    y = S.random_sinogram(W.n_angles, W.n_bins, 5)
+    return O, P, x, y
+
+
+def cpu_baseline(W, samples=3):
+    """The FP64 oracle, as it stands (one thread), on a bounded sample:
+    `samples` A_i + A_i^* pairs of the same workload."""
+    O, P, x, y = _oracle_pair_setup(W)
+    t0 = time.perf_counter()
+    for i in range(samples):
+        O.Ai(x, P, i % W.n_gates)
+        O.Ait(y, P, i % W.n_gates)
+    dt = time.perf_counter() - t0
+    return {"value": round(samples / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{samples} A_i+A_i^* pairs of {W.name} (FP64, single thread)"}
+
+
+def run_reference(args, W):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    O, P, x, y = _oracle_pair_setup(W)
+    for i in range(max(args.warmup, 0)):
+        O.Ai(x, P, i % W.n_gates); O.Ait(y, P, i % W.n_gates)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        O.Ai(x, P, i % W.n_gates); O.Ait(y, P, i % W.n_gates)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    out = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "impl": "reference",
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": workload_config(W) | {"step": "one A_i+A_i^* pair (FP64 oracle, host)"},
+           "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"one A_i+A_i^* pair of {W.name} per step"},
+           "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(S.WORKLOADS))
+    ap.add_argument("--cpu-pairs", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--l1-peak-gbs", type=float, default=152 * 128 * 2.07)
+    args = ap.parse_args()
+    W = S.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, W)
+    else:
+        run_ours(args, W)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * libmc -- motion-compensated SPDHG on one GPU (sm_103a), C ABI.
+ *
+ * Method: Delplancke, Thielemans, Ehrhardt, "Accelerated Convergent Motion
+ * Compensated Image Reconstruction", arXiv 2410.10503.
+ *
+ * Model (Sec. II-A): N gates with data d_i = A_i x + eps_i, A_i = A D_i,
+ * solved as  min_x  O(x) = alpha ||x||^2 + sum_i N^-1 ||A_i x - d_i||^2
+ * by SPDHG (Algorithm 1, one gate drawn per iteration with p_i = 1/N) or by
+ * PDHG (p_i = 1, all gates every iteration).  One epoch = N SPDHG iterations
+ * = one PDHG iteration = N forward and N adjoint operator applications.
+ *
+ * Conventions shared by every entry point
+ *  - Images are n x n float32, row-major [r*n + c].  Pixel (r, c) has centre
+ *    (x, y) = (c - h, r - h), h = (n-1)/2, unit spacing.
+ *  - Sinograms are n_angles x n_bins float32, row-major [k*n_bins + b].
+ *    Angle k is phi_k = k*pi/n_angles; bin b has centre s_b = b - (n_bins-1)/2;
+ *    ray (k, b) is the line {p : p . (cos phi_k, sin phi_k) = s_b}.
+ *  - A is Joseph's ray-driven projector: rays with n_a <= 4k <= 3 n_a are
+ *    sampled once per image column (step 1/|sin phi|), the others once per row
+ *    (step 1/|cos phi|), linear interpolation, zero outside the image.
+ *  - D_i is a bilinear pull-back warp, (D_i x)(p) = x(q_i(p)), zero outside;
+ *    rigid: q = R(phi_i) p + t_i about the image centre; dense: q = p + u_i(p).
+ *  - Gate indices are 0-based.
+ *  - Array pointers may be HOST or DEVICE memory (detected per call); device
+ *    arrays must belong to the context's device.  Arrays are contiguous and
+ *    caller-owned; the library never keeps or frees them.  Host arrays are
+ *    staged through the context's own device buffers; such calls return after
+ *    the results have reached host memory.  Calls with device arrays are
+ *    ordered on the context's stream and may return before the GPU finishes.
+ *  - Every entry point validates its arguments on the host before any launch
+ *    and returns a status; nothing throws or aborts across the ABI.  The
+ *    message of the last failure is kept per context (mc_last_error).
+ *  - A context is not thread-safe: one host thread at a time.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mc_ctx mc_ctx;
+
+typedef enum {
+    MC_OK = 0,
+    MC_EINVAL = -1,    /* bad argument (null, out of range, wrong device ...) */
+    MC_ENOMEM = -2,    /* device or pinned host allocation failed            */
+    MC_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed         */
+    MC_ETIMEOUT = -4,  /* a bounded device-side wait ran out (error word set) */
+    MC_ESTATE = -5,    /* call out of order (e.g. run before mc_set_data)     */
+    MC_EDEVICE = -6    /* no usable CUDA device / wrong architecture          */
+} mc_status;
+
+typedef struct {
+    int32_t n;         /* image side, 2 <= n <= 2048                           */
+    int32_t n_angles;  /* angles over [0, pi), 1 <= n_angles <= 8192           */
+    int32_t n_bins;    /* detector bins at unit spacing, 1 <= n_bins <= 8192   */
+} mc_geometry;
+
+enum { MC_MOTION_RIGID = 0, MC_MOTION_FIELD = 1 };
+
+typedef struct {
+    int32_t kind;          /* MC_MOTION_RIGID or MC_MOTION_FIELD               */
+    const double* rigid;   /* RIGID: N x 3 {phi (rad), tx, ty (px)}, host;
+                              q = R(phi) p + (tx, ty), R(phi) = [[c,-s],[s,c]] */
+    const float* field;    /* FIELD: N x 2 x n x n {ux (column), uy (row)} in px,
+                              host or device; q = p + u(p)                     */
+} mc_motion;
+
+typedef struct {
+    uint64_t seed;         /* Philox4x32-10 key                                */
+    uint32_t stream;       /* counter word 1; lets runs share a seed           */
+} mc_sampling;
+
+/* Options for mc_set_option. */
+enum {
+    MC_OPT_GRAPH = 1,            /* 1 (default): replay each epoch as a CUDA graph */
+    MC_OPT_PROFILE = 2,          /* 1: time every launch with CUDA events (slower)  */
+    MC_OPT_TRACE_OBJECTIVE = 3   /* 1: trace also evaluates O(x) (N extra A_i x)    */
+};
+
+/* Create a context on the current CUDA device (Sec. II-A: geometry of A,
+ * N gates, motion of D_i).  Builds the angle tables, uploads the motion and
+ * builds each gate's transpose warp D_i^T as a CSR matrix (rows = source
+ * pixels, entries sorted by destination pixel, bilinear weights identical to
+ * those of D_i).  cuda_stream: a cudaStream_t to order all work on, or NULL
+ * for a stream the context creates.  On success *out owns all device memory
+ * of the context; release it with mc_destroy.  Errors: MC_EINVAL,
+ * MC_ENOMEM, MC_ECUDA, MC_EDEVICE (message: mc_last_error(NULL)). */
+mc_status mc_create(const mc_geometry* geom, int32_t n_gates, const mc_motion* motion,
+                    void* cuda_stream, mc_ctx** out);
+
+/* Free everything the context owns.  NULL is a no-op. */
+void mc_destroy(mc_ctx* ctx);
+
+/* Message of the last failed call on ctx (or of the last failed mc_create
+ * when ctx is NULL); "" if none.  Valid until the next call on ctx. */
+const char* mc_last_error(const mc_ctx* ctx);
+
+/* Set the gated data d (N x n_angles x n_bins, copied) and alpha > 0 of
+ * g(x) = alpha ||x||^2 (Sec. II-A).  Resets the solver state. */
+mc_status mc_set_data(mc_ctx* ctx, const float* d, double alpha);
+
+/* out = A_i x = A D_i x (Sec. II-A).  x: n x n; out: n_angles x n_bins. */
+mc_status mc_forward(mc_ctx* ctx, int32_t gate, const float* x, float* out);
+
+/* out = A_i^* y = D_i^T A^T y, the exact transpose of mc_forward (the
+ * operator SPDHG applies in step (iii) of Algorithm 1).  A^T is a pixel-
+ * driven gather with the same interpolation weights as A; D_i^T gathers
+ * through the gate's CSR.  y: n_angles x n_bins; out: n x n. */
+mc_status mc_adjoint(mc_ctx* ctx, int32_t gate, const float* y, float* out);
+
+/* out = A x (no motion) and out = A^T y: the ray transform alone. */
+mc_status mc_project(mc_ctx* ctx, const float* x, float* out);
+mc_status mc_backproject(mc_ctx* ctx, const float* y, float* out);
+
+/* out = D_i x and out = D_i^T v: the warp of gate i alone. */
+mc_status mc_warp(mc_ctx* ctx, int32_t gate, const float* x, float* out);
+mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out);
+
+/* Power iteration (Theorem, Sec. II-B) with float32 operators and float64
+ * reductions.  out (host or device, N+1 doubles): ||A_0||^2 .. ||A_{N-1}||^2,
+ * then ||(A_0; ...; A_{N-1})||^2 = lambda_max(sum_i A_i^T A_i).  Stops per
+ * norm after max_iter iterations or when the Rayleigh quotient changes by
+ * less than tol (relative).  The result also sets the step sizes. */
+mc_status mc_norms(mc_ctx* ctx, int32_t max_iter, double tol, double* out);
+
+/* Use these squared norms (N+1 doubles, same layout as mc_norms) for the
+ * step sizes instead of running mc_norms. */
+mc_status mc_set_norms(mc_ctx* ctx, const double* norms2);
+
+/* Step sizes in use (host out, 5 doubles): {sigma, tau, theta, kappa, omega}
+ * for SPDHG (pdhg = 0) or PDHG (pdhg = 1).  With mu_g = 2 alpha, mu_f = N/2,
+ * kappa = ||A||^2/(mu_g mu_f) (||A||^2 = max_i ||A_i||^2 for SPDHG, the stacked
+ * norm for PDHG), s = sqrt(1 + kappa), n = N (SPDHG) or 1 (PDHG):
+ * omega = 1 - 2/(n (1 + s)), sigma_i = 1/(mu_f (s - 1)),
+ * tau = (1 - omega)/(2 mu_g omega), theta = omega, so that the per-epoch rate
+ * is omega^n = l(kappa, n) of Sec. II-B.  MC_ESTATE before norms and data. */
+mc_status mc_get_steps(mc_ctx* ctx, int32_t pdhg, double* out);
+
+/* Reference solution x* (n x n) for the trace; y_i* = (2/N)(A_i x* - d_i)
+ * is derived from it.  Call after mc_set_data.  NULL clears it. */
+mc_status mc_set_reference(mc_ctx* ctx, const float* x_star);
+
+/* Zero the solver state (x = z = zbar = 0, y = 0) and the iteration count. */
+mc_status mc_reset(mc_ctx* ctx);
+
+/* Run `epochs` epochs (N iterations each) of SPDHG, Algorithm 1, continuing
+ * from the current state:
+ *   (i)   x^{k+1} = prox_{tau g}(x^k - tau zbar^k) = (x^k - tau zbar^k)/(1 + 2 tau alpha)
+ *   (ii)  draw i (Philox4x32-10 on the device, key = seed, counter =
+ *         (k mod 2^32, stream, k >> 32, 0), i = floor(word0 * N / 2^32));
+ *         y_i^{k+1} = prox_{sigma f_i^*}(y_i^k + sigma A_i x^{k+1})
+ *                   = (y_i^k + sigma (A_i x^{k+1} - d_i)) / (1 + sigma N/2)
+ *   (iii) z^{k+1} = z^k + A_i^* (y_i^{k+1} - y_i^k),
+ *         zbar^{k+1} = z^{k+1} + (theta / p_i) A_i^* (y_i^{k+1} - y_i^k).
+ * (Algorithm 1 as printed uses z^k in step (i) and accumulates zbar on
+ * zbar^k; this is read as the standard SPDHG above.)
+ * x_out (nullable, n x n): x^K after the K-th iteration of this context.
+ * trace (nullable, epochs x 3 doubles): per epoch
+ * {||x - x*||/||x*||, ||x - x*||^2 + sum_i ||y_i - y_i*||^2, O(x)}; NaN where the
+ * reference is unset or MC_OPT_TRACE_OBJECTIVE is off.
+ * MC_ESTATE if data or step sizes are missing. */
+mc_status mc_spdhg_run(mc_ctx* ctx, int32_t epochs, const mc_sampling* sampling,
+                       float* x_out, double* trace);
+
+/* Run `epochs` iterations of PDHG (p_i = 1, every gate each iteration,
+ * zbar^{k+1} = z^{k+1} + theta sum_i A_i^*(y_i^{k+1} - y_i^k)), continuing from
+ * the current state.  Arguments as for mc_spdhg_run. */
+mc_status mc_pdhg_run(mc_ctx* ctx, int32_t epochs, float* x_out, double* trace);
+
+/* The device gate draw alone: out[j] = gate of iteration k0 + j (int32,
+ * host or device, count >= 0).  Does not touch the solver state. */
+mc_status mc_draw_gates(mc_ctx* ctx, const mc_sampling* sampling, uint64_t k0,
+                        int32_t count, int32_t* out);
+
+/* O(x) = alpha ||x||^2 + sum_i N^-1 ||A_i x - d_i||^2 in float64 (Sec. II-A). */
+mc_status mc_objective(mc_ctx* ctx, const float* x, double* out);
+
+/* Set an MC_OPT_* option. */
+mc_status mc_set_option(mc_ctx* ctx, int32_t option, int64_t value);
+
+/* With MC_OPT_PROFILE on: per kernel class, launches and summed device time
+ * (ms) since the last mc_profile_reset.  names/counts/ms are host arrays of
+ * capacity `cap`; *n_out receives the number of classes.  Classes: "warp",
+ * "project", "backproject", "warp_adjoint_update", "gate_draw", "misc". */
+mc_status mc_profile_read(mc_ctx* ctx, int32_t cap, const char** names, int64_t* counts,
+                          double* ms, int32_t* n_out);
+mc_status mc_profile_reset(mc_ctx* ctx);
+
+/* Iteration counter k of the next SPDHG iteration (host out). */
+mc_status mc_iteration(mc_ctx* ctx, uint64_t* out);
+
+/* Library version string. */
+const char* mc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MC_H */

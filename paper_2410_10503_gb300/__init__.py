@@ -1,0 +1,249 @@
+"""GB300-native motion-compensated SPDHG (arXiv 2410.10503).
+
+Python face of libmc (include/mc.h): the same entry points, argument
+marshalling only.  Arrays may be torch tensors (CUDA or CPU) or numpy arrays;
+CUDA tensors are passed as device pointers, everything else as host pointers
+(the library stages those through its own device buffers).  Results come back
+as CUDA tensors when the input was one, else as numpy arrays.
+
+Every computation runs in the library's CUDA kernels; when libmc is not
+built, or no sm_103a GPU is present, the calls raise instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _native as N
+
+__all__ = ["Context", "MCError", "lib", "version"]
+
+try:  # torch is plumbing here (device memory, streams); optional for host arrays
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+
+class MCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{N.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    return N.load()
+
+
+def version() -> str:
+    return lib().mc_version().decode()
+
+
+def _is_tensor(a) -> bool:
+    return torch is not None and isinstance(a, torch.Tensor)
+
+
+def _arg(a, dtype, count: int, name: str):
+    """(pointer, keepalive) of a contiguous array with `count` elements."""
+    if _is_tensor(a):
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt:
+            raise TypeError(f"{name}: expected {tdt}, got {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name}: tensor must be contiguous")
+        if a.numel() != count:
+            raise ValueError(f"{name}: expected {count} elements, got {a.numel()}")
+        return a.data_ptr(), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    if arr.size != count:
+        raise ValueError(f"{name}: expected {count} elements, got {arr.size}")
+    return arr.ctypes.data, arr
+
+
+def _empty_like_kind(ref, shape, dtype=np.float32):
+    if _is_tensor(ref) and ref.is_cuda:
+        tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        return torch.empty(shape, dtype=tdt, device=ref.device)
+    return np.empty(shape, dtype=dtype)
+
+
+class Context:
+    """One reconstruction problem on the current CUDA device (mc_create)."""
+
+    def __init__(self, n: int, n_angles: int, n_bins: int, n_gates: int,
+                 rigid=None, fields=None, stream: Optional[int] = None):
+        L = lib()
+        self._L = L
+        self.n, self.n_angles, self.n_bins, self.n_gates = n, n_angles, n_bins, n_gates
+        g = N.mc_geometry(n, n_angles, n_bins)
+        keep = []
+        if (rigid is None) == (fields is None):
+            raise ValueError("give exactly one of rigid (N x 3) or fields (N x 2 x n x n)")
+        if rigid is not None:
+            p, k = _arg(rigid, np.float64, n_gates * 3, "rigid")
+            m = N.mc_motion(N.MC_MOTION_RIGID, p, None)
+        else:
+            p, k = _arg(fields, np.float32, n_gates * 2 * n * n, "fields")
+            m = N.mc_motion(N.MC_MOTION_FIELD, None, p)
+        keep.append(k)
+        out = ctypes.c_void_p()
+        st = L.mc_create(ctypes.byref(g), n_gates, ctypes.byref(m),
+                         ctypes.c_void_p(stream) if stream else None, ctypes.byref(out))
+        if st != 0:
+            raise MCError(st, L.mc_last_error(None).decode())
+        self._h = out.value
+        self.kind = "rigid" if rigid is not None else "field"
+
+    # -- plumbing --------------------------------------------------------------
+    def _check(self, st: int):
+        if st != 0:
+            raise MCError(st, self._L.mc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def img_count(self):
+        return self.n * self.n
+
+    @property
+    def sino_count(self):
+        return self.n_angles * self.n_bins
+
+    # -- operators ----------------------------------------------------------------
+    def _op(self, fn, args, x, n_in, out, out_shape):
+        px, kx = _arg(x, np.float32, n_in, "input")
+        if out is None:
+            out = _empty_like_kind(x, out_shape)
+        po, ko = _arg(out, np.float32, int(np.prod(out_shape)), "out")
+        self._check(fn(self._h, *args, px, po))
+        return out
+
+    def forward(self, gate: int, x, out=None):
+        """A_i x = A D_i x."""
+        return self._op(self._L.mc_forward, (gate,), x, self.img_count, out,
+                        (self.n_angles, self.n_bins))
+
+    def adjoint(self, gate: int, y, out=None):
+        """A_i^* y = D_i^T A^T y."""
+        return self._op(self._L.mc_adjoint, (gate,), y, self.sino_count, out, (self.n, self.n))
+
+    def project(self, x, out=None):
+        """A x (no motion)."""
+        return self._op(self._L.mc_project, (), x, self.img_count, out, (self.n_angles, self.n_bins))
+
+    def backproject(self, y, out=None):
+        """A^T y."""
+        return self._op(self._L.mc_backproject, (), y, self.sino_count, out, (self.n, self.n))
+
+    def warp(self, gate: int, x, out=None):
+        """D_i x."""
+        return self._op(self._L.mc_warp, (gate,), x, self.img_count, out, (self.n, self.n))
+
+    def warp_adjoint(self, gate: int, v, out=None):
+        """D_i^T v."""
+        return self._op(self._L.mc_warp_adjoint, (gate,), v, self.img_count, out, (self.n, self.n))
+
+    # -- problem ------------------------------------------------------------------
+    def set_data(self, d, alpha: float):
+        p, k = _arg(d, np.float32, self.n_gates * self.sino_count, "d")
+        self._check(self._L.mc_set_data(self._h, p, float(alpha)))
+
+    def norms(self, max_iter: int = 200, tol: float = 1e-6) -> np.ndarray:
+        out = np.empty(self.n_gates + 1)
+        self._check(self._L.mc_norms(self._h, max_iter, tol, out.ctypes.data))
+        return out
+
+    def set_norms(self, norms2):
+        p, k = _arg(norms2, np.float64, self.n_gates + 1, "norms2")
+        self._check(self._L.mc_set_norms(self._h, p))
+
+    def steps(self, pdhg: bool = False) -> dict:
+        out = np.empty(5)
+        self._check(self._L.mc_get_steps(self._h, 1 if pdhg else 0, out.ctypes.data))
+        return dict(zip(("sigma", "tau", "theta", "kappa", "omega"), out.tolist()))
+
+    def set_reference(self, x_star):
+        if x_star is None:
+            self._check(self._L.mc_set_reference(self._h, None))
+            return
+        p, k = _arg(x_star, np.float32, self.img_count, "x_star")
+        self._check(self._L.mc_set_reference(self._h, p))
+
+    def reset(self):
+        self._check(self._L.mc_reset(self._h))
+
+    def _run(self, which, epochs, seed, stream, x_out, trace, like):
+        if x_out is None:
+            x_out = _empty_like_kind(like, (self.n, self.n)) if like is not None else \
+                np.empty((self.n, self.n), np.float32)
+        elif x_out is False:
+            x_out = None
+        px = _arg(x_out, np.float32, self.img_count, "x_out")[0] if x_out is not None else None
+        tr = np.full((max(epochs, 0), 3), np.nan) if trace else None
+        pt = tr.ctypes.data if tr is not None else None
+        if which == 0:
+            s = N.mc_sampling(seed, stream)
+            self._check(self._L.mc_spdhg_run(self._h, epochs, ctypes.byref(s), px, pt))
+        else:
+            self._check(self._L.mc_pdhg_run(self._h, epochs, px, pt))
+        return x_out, tr
+
+    def spdhg_run(self, epochs: int, seed: int, stream: int = 0, x_out=None, trace=False, like=None):
+        """Algorithm 1 for `epochs` epochs; returns (x^K, trace or None).
+        x_out=False skips the copy of x (fully asynchronous with device arrays)."""
+        return self._run(0, epochs, seed, stream, x_out, trace, like)
+
+    def pdhg_run(self, epochs: int, x_out=None, trace=False, like=None):
+        return self._run(1, epochs, 0, 0, x_out, trace, like)
+
+    def draw_gates(self, seed: int, stream: int, k0: int, count: int, out=None):
+        if out is None:
+            out = np.empty(count, np.int32)
+        p = _arg(out, np.int32, count, "out")[0]
+        s = N.mc_sampling(seed, stream)
+        self._check(self._L.mc_draw_gates(self._h, ctypes.byref(s), k0, count, p))
+        return out
+
+    def objective(self, x) -> float:
+        p, k = _arg(x, np.float32, self.img_count, "x")
+        out = ctypes.c_double()
+        self._check(self._L.mc_objective(self._h, p, ctypes.addressof(out)))
+        return out.value
+
+    def set_option(self, option: int, value: int):
+        self._check(self._L.mc_set_option(self._h, option, int(value)))
+
+    def profile(self) -> dict:
+        cap = 16
+        names = (ctypes.c_char_p * cap)()
+        counts = (ctypes.c_int64 * cap)()
+        ms = (ctypes.c_double * cap)()
+        n_out = ctypes.c_int32()
+        self._check(self._L.mc_profile_read(self._h, cap, ctypes.addressof(names),
+                                            ctypes.addressof(counts), ctypes.addressof(ms),
+                                            ctypes.addressof(n_out)))
+        return {names[i].decode(): (int(counts[i]), float(ms[i])) for i in range(n_out.value)}
+
+    def profile_reset(self):
+        self._check(self._L.mc_profile_reset(self._h))
+
+    def iteration(self) -> int:
+        out = ctypes.c_uint64()
+        self._check(self._L.mc_iteration(self._h, ctypes.addressof(out)))
+        return out.value

@@ -1,0 +1,174 @@
+// K8 device gate draw (Algorithm 1 step (ii), serial uniform sampling
+// p_i = 1/N), K9 float64 reductions (Theorem norms, objective O(x) of
+// Sec. II-A, saddle-point distance), and small vector kernels.
+#include <cmath>
+
+#include "mc_kernels.h"
+
+namespace mcg {
+
+namespace {
+
+// One block.  kctr != null: k0 = *kctr and the counter advances by count
+// after every thread has read it (graph replays draw fresh gates).
+__global__ void k_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
+                             uint64_t k0_in, int count, int n_gates, int* out)
+{
+    const uint64_t k0 = kctr ? (uint64_t)*kctr : k0_in;
+    for (int j = threadIdx.x; j < count; j += blockDim.x) {
+        const uint32_t w = philox_word0(seed, stream, k0 + (uint64_t)j);
+        out[j] = (int)(((uint64_t)w * (uint64_t)n_gates) >> 32);
+    }
+    __syncthreads();
+    if (kctr && threadIdx.x == 0) *kctr = (unsigned long long)(k0 + (uint64_t)count);
+}
+
+__global__ void k_pad_sino(const float* __restrict__ y, float* dy, int na, int nb, int Pb, int Gb)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (b < nb) dy[(size_t)k * Pb + Gb + b] = y[(size_t)k * nb + b];
+}
+
+constexpr int kRedThreads = 256;
+constexpr int kRedParts = 1024;
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double sm[kRedThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sm[wid] = v;
+    __syncthreads();
+    v = 0.0;
+    if (wid == 0) {
+        v = (lane < kRedThreads / 32) ? sm[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+    return v;   // valid in thread 0
+}
+
+// Fixed grid (kRedParts blocks) and fixed orders: bitwise reproducible.
+__global__ void __launch_bounds__(kRedThreads) k_reduce(const float* __restrict__ a,
+                                                        const float* __restrict__ b, size_t len,
+                                                        int mode, double* partial)
+{
+    double acc = 0.0;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += stride) {
+        const double x = (double)a[i];
+        if (mode == kRedSumSq) acc += x * x;
+        else if (mode == kRedDiffSq) { const double d = x - (double)b[i]; acc += d * d; }
+        else acc += x * (double)b[i];
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const double* partial, int parts, double* out)
+{
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < parts; i += blockDim.x) acc += partial[i];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) *out = acc;
+}
+
+__global__ void k_axpby(float a, const float* __restrict__ x, float b, const float* __restrict__ y,
+                        float* out, size_t len)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < len) out[i] = y ? fmaf(a, x[i], b * y[i]) : a * x[i];
+}
+
+__global__ void k_normalize(float* x, const double* norm2, size_t len)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double nn = *norm2;
+    const float s = nn > 0.0 ? (float)(1.0 / sqrt(nn)) : 0.0f;
+    if (i < len) x[i] *= s;
+}
+
+__global__ void k_trace_combine(const double* dx2, const double* xs2, const double* dy2, double* out)
+{
+    out[0] = (*xs2 > 0.0) ? sqrt(*dx2 / *xs2) : nan("");
+    out[1] = dy2 ? (*dx2 + *dy2) : nan("");
+}
+
+__global__ void k_objective_combine(const double* xx, const double* res, int n_res, double alpha,
+                                    int N, double* out)
+{
+    double s = 0.0;
+    for (int i = 0; i < n_res; ++i) s += res[i];
+    *out = alpha * (*xx) + s / (double)N;
+}
+
+__global__ void k_fill_nan(double* p, int count)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) p[i] = nan("");
+}
+
+}  // namespace
+
+cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
+                              uint64_t k0, int count, int n_gates, int* out, cudaStream_t s)
+{
+    k_draw_gates<<<1, 256, 0, s>>>(seed, stream, kctr, k0, count, n_gates, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pad_sino(const float* y, float* dy, int na, int nb, int Pb, int Gb,
+                            cudaStream_t s)
+{
+    const dim3 grid((nb + 255) / 256, na);
+    k_pad_sino<<<grid, 256, 0, s>>>(y, dy, na, nb, Pb, Gb);
+    return cudaGetLastError();
+}
+
+int reduce_parts() { return kRedParts; }
+
+cudaError_t launch_reduce(const float* a, const float* b, size_t len, int mode,
+                          double* partial, double* out, cudaStream_t s)
+{
+    k_reduce<<<kRedParts, kRedThreads, 0, s>>>(a, b, len, mode, partial);
+    k_reduce_final<<<1, kRedThreads, 0, s>>>(partial, kRedParts, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(float a, const float* x, float b, const float* y, float* out,
+                         size_t len, cudaStream_t s)
+{
+    k_axpby<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(a, x, b, y, out, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(float* x, const double* norm2, size_t len, cudaStream_t s)
+{
+    k_normalize<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(x, norm2, len);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trace_combine(const double* dx2, const double* xs2, const double* dy2,
+                                 double* out, cudaStream_t s)
+{
+    k_trace_combine<<<1, 1, 0, s>>>(dx2, xs2, dy2, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective_combine(const double* xx, const double* res, int n_res,
+                                     double alpha, int N, double* out, cudaStream_t s)
+{
+    k_objective_combine<<<1, 1, 0, s>>>(xx, res, n_res, alpha, N, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    k_fill_nan<<<(count + 255) / 256, 256, 0, s>>>(p, count);
+    return cudaGetLastError();
+}
+
+}  // namespace mcg

@@ -1,0 +1,286 @@
+// K1 warp D_i, K2 transpose-CSR build, K5 transpose gather D_i^T with the
+// fused z / zbar / primal-prox epilogue of Algorithm 1 (arXiv 2410.10503,
+// Sec. II-A: A_i = A D_i; Algorithm 1 steps (i) and (iii)).
+#include "mc_kernels.h"
+
+namespace mcg {
+
+__device__ __forceinline__ int gate_of(const GateSel& s, int slot)
+{
+    return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
+}
+
+// Bilinear pull-back sample (D x)(r, c); weights are the products
+// (1-fr or fr) * (1-fc or fc), rounded once, exactly as stored in the CSR.
+__device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
+                                             const RigidGate* rg, const float* field,
+                                             int r, int c)
+{
+    int r0, c0;
+    float fr, fc;
+    warp_taps(rg, field, n, r, c, r0, c0, fr, fc);
+    const float wr[2] = {1.0f - fr, fr};
+    const float wc[2] = {1.0f - fc, fc};
+    float acc = 0.0f;
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) {
+            const int i = r0 + di, j = c0 + dj;
+            if (i >= 0 && i < n && j >= 0 && j < n)
+                acc = fmaf(__fmul_rn(wr[di], wc[dj]), __ldg(x + (size_t)i * n + j), acc);
+        }
+    return acc;
+}
+
+// Tile of 32 x 32 output pixels per block (32 x 8 threads, 4 rows each).
+template <bool LAYOUT>
+__global__ void __launch_bounds__(256) k_warp(WarpArgs a)
+{
+    __shared__ float tile[32][33];
+    const int slot = blockIdx.z;
+    const int gate = gate_of(a.sel, slot);
+    const int n = a.n;
+    const RigidGate* rg = a.rigid ? a.rigid + gate : nullptr;
+    const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
+    const int c = blockIdx.x * 32 + threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int tr = threadIdx.y + 8 * i;
+        const int r = blockIdx.y * 32 + tr;
+        float w = 0.0f;
+        if (r < n && c < n)
+            w = a.identity ? __ldg(a.x + (size_t)r * n + c)
+                           : warp_sample(a.x, n, rg, field, r, c);
+        if (LAYOUT) {
+            tile[tr][threadIdx.x] = w;
+            if (r < n && c < n)
+                a.lrow[slot * a.layout_stride + (size_t)r * a.P + kGuard + c] = w;
+        } else if (r < n && c < n) {
+            a.out[(size_t)slot * n * n + (size_t)r * n + c] = w;
+        }
+    }
+    if (LAYOUT) {
+        __syncthreads();
+        // column layout: line = image column, position = row
+        const int rr = blockIdx.y * 32 + threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int tc = threadIdx.y + 8 * i;
+            const int cc = blockIdx.x * 32 + tc;
+            if (cc < n && rr < n)
+                a.lcol[slot * a.layout_stride + (size_t)cc * a.P + kGuard + rr] =
+                    tile[threadIdx.x][tc];
+        }
+    }
+}
+
+cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
+{
+    dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 8);
+    k_warp<true><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_plain(const WarpArgs& a, cudaStream_t s)
+{
+    dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 8);
+    k_warp<false><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---- K2: CSR of D_i^T: row q lists (p, w) with w the weight of x[q] in (D x)(p)
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_csr_taps(int n, const RigidGate* rg, const float* field,
+                                                  int* cnt, const int* rowptr, int2* ent)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * n) return;
+    const int r = p / n, c = p - r * n;
+    int r0, c0;
+    float fr, fc;
+    warp_taps(rg, field, n, r, c, r0, c0, fr, fc);
+    const float wr[2] = {1.0f - fr, fr};
+    const float wc[2] = {1.0f - fc, fc};
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) {
+            const int i = r0 + di, j = c0 + dj;
+            const float w = __fmul_rn(wr[di], wc[dj]);
+            if (i >= 0 && i < n && j >= 0 && j < n && w != 0.0f) {
+                const int q = i * n + j;
+                if (FILL) {
+                    const int pos = rowptr[q] + atomicAdd(cnt + q, 1);
+                    ent[pos] = make_int2(p, __float_as_int(w));
+                } else {
+                    atomicAdd(cnt + q, 1);
+                }
+            }
+        }
+}
+
+cudaError_t launch_csr_count(int n, const RigidGate* rg, const float* field, int* cnt,
+                             cudaStream_t s)
+{
+    const int tot = n * n;
+    k_csr_taps<false><<<(tot + 255) / 256, 256, 0, s>>>(n, rg, field, cnt, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_fill(int n, const RigidGate* rg, const float* field,
+                            const int* rowptr, int* cursor, int2* ent, cudaStream_t s)
+{
+    const int tot = n * n;
+    k_csr_taps<true><<<(tot + 255) / 256, 256, 0, s>>>(n, rg, field, cursor, rowptr, ent);
+    return cudaGetLastError();
+}
+
+// Rows are short (about four entries); insertion sort by destination pixel
+// makes the summation order, and so the result, deterministic.
+__global__ void k_csr_sort(int rows, const int* rowptr, int2* ent)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= rows) return;
+    const int b = rowptr[q], e = rowptr[q + 1];
+    for (int i = b + 1; i < e; ++i) {
+        const int2 v = ent[i];
+        int j = i - 1;
+        while (j >= b && ent[j].x > v.x) { ent[j + 1] = ent[j]; --j; }
+        ent[j + 1] = v;
+    }
+}
+
+cudaError_t launch_csr_sort(int n, const int* rowptr, int2* ent, cudaStream_t s)
+{
+    const int rows = n * n;
+    k_csr_sort<<<(rows + 255) / 256, 256, 0, s>>>(rows, rowptr, ent);
+    return cudaGetLastError();
+}
+
+// ---- exclusive scan (3 phases, 1024 elements per block) ---------------------
+constexpr int kScanBlock = 1024;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* sm, int& total)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sm[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = (lane < (int)(blockDim.x >> 5)) ? sm[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += t;
+        }
+        sm[lane] = wi - w;          // exclusive warp offsets
+        if (lane == 31) sm[32] = wi;
+    }
+    __syncthreads();
+    total = sm[32];
+    const int r = sm[wid] + incl - v;
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_local(const int* in, int* out, int len,
+                                                           int* block_sums)
+{
+    __shared__ int sm[33];
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    const int v = (i < len) ? in[i] : 0;
+    int total;
+    const int ex = block_exclusive_scan(v, sm, total);
+    if (i < len) out[i] = ex;
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block sums in place (any count).
+__global__ void __launch_bounds__(kScanBlock) k_scan_sums(int* sums, int count, int* grand)
+{
+    __shared__ int sm[33];
+    int carry = 0;
+    for (int base = 0; base < count; base += kScanBlock) {
+        const int i = base + threadIdx.x;
+        const int v = (i < count) ? sums[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(v, sm, total);
+        if (i < count) sums[i] = ex + carry;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *grand = carry;
+}
+
+__global__ void k_scan_add(int* out, int len, const int* sums, const int* grand)
+{
+    const int i = blockIdx.x * kScanBlock + threadIdx.x;
+    if (i < len) out[i] += sums[blockIdx.x];
+    if (i == 0) out[len] = *grand;
+}
+
+int scan_scratch_len(int len) { return (len + kScanBlock - 1) / kScanBlock + 1; }
+
+cudaError_t launch_exclusive_scan(const int* in, int* out_rowptr, int len, int* scratch,
+                                  int scratch_len, cudaStream_t s)
+{
+    const int nb = (len + kScanBlock - 1) / kScanBlock;
+    if (scratch_len < nb + 1) return cudaErrorInvalidValue;
+    k_scan_local<<<nb, kScanBlock, 0, s>>>(in, out_rowptr, len, scratch);
+    k_scan_sums<<<1, kScanBlock, 0, s>>>(scratch, nb, scratch + nb);
+    k_scan_add<<<nb, kScanBlock, 0, s>>>(out_rowptr, len, scratch, scratch + nb);
+    return cudaGetLastError();
+}
+
+// ---- K5 (+K7) -------------------------------------------------------------
+template <bool UPDATE>
+__global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
+{
+    const int n2 = a.n * a.n;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n2) return;
+    float v = 0.0f;
+    for (int s = 0; s < a.n_slots; ++s) {
+        const int gate = gate_of(a.sel, s);
+        const int* rp = a.rowptr + (size_t)gate * (n2 + 1);
+        const int2* ent = a.ent + a.ent_off[gate];
+        const float* b = a.b + (size_t)s * n2;
+        const int e0 = __ldg(rp + q), e1 = __ldg(rp + q + 1);
+        for (int e = e0; e < e1; ++e) {
+            const int2 t = __ldg(ent + e);
+            v = fmaf(__int_as_float(t.y), __ldg(b + t.x), v);
+        }
+    }
+    if (UPDATE) {
+        // (iii) z^{k+1} = z^k + v, zbar^{k+1} = z^{k+1} + (theta/p_i) v, then
+        // (i) of the next iteration: x^{k+2} = (x^{k+1} - tau zbar^{k+1}) / (1 + 2 tau alpha)
+        const float zn = a.z[q] + v;
+        const float zbar = fmaf(a.coef, v, zn);
+        a.z[q] = zn;
+        a.x_out[q] = fmaf(-a.tau, zbar, a.x_in[q]) * a.prox_scale;
+    } else {
+        a.out[q] = v;
+    }
+}
+
+cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s)
+{
+    const int n2 = a.n * a.n;
+    k_warp_adjoint<false><<<(n2 + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s)
+{
+    const int n2 = a.n * a.n;
+    k_warp_adjoint<true><<<(n2 + 255) / 256, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mcg

@@ -1,0 +1,1191 @@
+// libmc host runtime: the C ABI of include/mc.h.
+//
+// Owns the per-context device state (tables, per-gate CSR of D_i^T, gated
+// data, SPDHG/PDHG iterates, per-slot scratch), validates every call on the
+// host, orders all work on the context's stream and replays whole epochs as
+// CUDA graphs.  No computation of the method runs on the host: every step
+// is one of the kernels in k_*.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "mc.h"
+#include "mc_kernels.h"
+
+using namespace mcg;
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_create_err;
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kNumClasses = 6;
+const char* kClassNames[kNumClasses] = {"warp", "project", "backproject",
+                                        "warp_adjoint_update", "gate_draw", "misc"};
+enum { C_WARP = 0, C_PROJ = 1, C_BP = 2, C_WADJ = 3, C_DRAW = 4, C_MISC = 5 };
+
+struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+struct Steps {
+    double sigma = 0, tau = 0, theta = 0, kappa = 0, omega = 0;
+};
+
+void split_f(double v, float& hi, float& lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+Steps make_steps(double norm2, double alpha, int N, int n_iter_per_epoch)
+{
+    // strongly convex PDHG/SPDHG steps: mu_g = 2 alpha, mu_f = N / 2
+    Steps s;
+    const double mu_g = 2.0 * alpha, mu_f = 0.5 * N;
+    s.kappa = norm2 / (mu_g * mu_f);
+    const double q = std::sqrt(1.0 + s.kappa);
+    s.omega = 1.0 - 2.0 / ((double)n_iter_per_epoch * (1.0 + q));
+    s.sigma = 1.0 / (mu_f * (q - 1.0));
+    s.tau = (1.0 - s.omega) / (2.0 * mu_g * s.omega);
+    s.theta = s.omega;
+    return s;
+}
+
+}  // namespace
+
+struct mc_ctx {
+    int dev = 0, sms = 0;
+    int n = 0, na = 0, nb = 0, N = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<void*> allocs;
+
+    // geometry
+    FwdAngle* d_fang = nullptr;
+    BpAngle* d_bang = nullptr;
+    int* d_order = nullptr;
+    RayItem* d_items = nullptr;
+    int n_items = 0, rpt = 1, lc = 1, P = 0, Gb = 0, Pb = 0, pj = 4;
+    size_t layout_stride = 0, dy_stride = 0;
+
+    // motion and D_i^T
+    int kind = 0;
+    RigidGate* d_rigid = nullptr;
+    float* d_field = nullptr;
+    int* d_rowptr = nullptr;
+    int2* d_ent = nullptr;
+    long long* d_ent_off = nullptr;
+    long long nnz_total = 0;
+
+    // data and iterates
+    float* d_d = nullptr;
+    float* d_y = nullptr;
+    float* d_x[2] = {nullptr, nullptr};
+    float* d_z = nullptr;
+    int cur = 0;
+    bool have_data = false;
+    double alpha = 0;
+
+    // scratch per gate slot
+    float* d_lrow = nullptr;
+    float* d_lcol = nullptr;
+    float* d_dy = nullptr;
+    float* d_b = nullptr;
+    float* d_sinoN = nullptr;
+    float* d_img[4] = {nullptr, nullptr, nullptr, nullptr};
+    float* d_sino_io = nullptr;
+
+    // control and reductions
+    unsigned long long* d_k = nullptr;
+    int* d_gates = nullptr;
+    int* d_err = nullptr;
+    int* d_draw_out = nullptr;
+    int draw_cap = 0;
+    uint64_t k_host = 0;
+    double* d_part = nullptr;
+    double* d_s = nullptr;        // scalar slots
+    double* d_trace = nullptr;
+    int trace_cap = 0;
+
+    // steps
+    bool have_norms = false;
+    std::vector<double> norms2;
+    Steps sS, sP;
+    bool steps_ok = false;
+
+    // reference
+    float* d_xstar = nullptr;
+    float* d_ystar = nullptr;
+    bool have_ref = false;
+
+    // options
+    bool graph_on = true, prof_on = false, trace_obj = false;
+
+    // graphs: [0] SPDHG, [1] PDHG; index parity of cur at capture
+    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    uint64_t g_seed[2] = {0, 0};
+    uint32_t g_stream[2] = {0, 0};
+
+    // profiling
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    long long prof_count[kNumClasses] = {0};
+    double prof_ms[kNumClasses] = {0};
+};
+
+// scalar slots in d_s
+enum { S_DX2 = 0, S_XS2 = 1, S_DY2 = 2, S_XX = 3, S_TMP = 4, S_LAM = 5, S_NRM = 6, S_RES = 16 };
+
+namespace {
+
+mc_status fail(mc_ctx* c, mc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        c->err = buf;
+    } else {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        g_create_err = buf;
+    }
+    return st;
+}
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(c, MC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+    } while (0)
+
+#define TRY(expr)                       \
+    do {                                \
+        mc_status s_ = (expr);          \
+        if (s_ != MC_OK) return s_;     \
+    } while (0)
+
+template <class T>
+mc_status dalloc(mc_ctx* c, T** p, size_t count)
+{
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, MC_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    e = cudaMemsetAsync(q, 0, bytes, c->stream);
+    if (e != cudaSuccess) return fail(c, MC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
+    *p = static_cast<T*>(q);
+    return MC_OK;
+}
+
+// 1 = device memory of this context's device, 0 = host, -1 = other device
+int ptr_kind(mc_ctx* c, const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return (a.device == c->dev) ? 1 : -1;
+    return 0;
+}
+
+mc_status check_ptr(mc_ctx* c, const void* p, const char* what)
+{
+    if (!p) return fail(c, MC_EINVAL, "%s is NULL", what);
+    if (ptr_kind(c, p) < 0) return fail(c, MC_EINVAL, "%s lives on another device", what);
+    return MC_OK;
+}
+
+cudaEvent_t ev_get(mc_ctx* c)
+{
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// launch through here: optional per-launch events for MC_OPT_PROFILE
+template <class F>
+mc_status launch(mc_ctx* c, int cls, const char* what, F&& f)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->prof_on) {
+        a = ev_get(c);
+        b = ev_get(c);
+        cudaEventRecord(a, c->stream);
+    }
+    const cudaError_t e = f();
+    if (c->prof_on) {
+        cudaEventRecord(b, c->stream);
+        c->prof.push_back({cls, a, b});
+    }
+    if (e != cudaSuccess) return fail(c, MC_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+    return MC_OK;
+}
+
+mc_status prof_collect(mc_ctx* c)
+{
+    if (c->prof.empty()) return MC_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto& r : c->prof) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            c->prof_count[r.cls] += 1;
+            c->prof_ms[r.cls] += ms;
+        } else {
+            cudaGetLastError();
+        }
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof.clear();
+    return MC_OK;
+}
+
+mc_status check_err_word(mc_ctx* c)
+{
+    int h = 0;
+    CK(cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (h != kErrNone) {
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        if (h == kErrTimeout) return fail(c, MC_ETIMEOUT, "a device-side wait ran out of polls");
+        return fail(c, MC_EDEVICE, "device error word %d (out-of-bounds sample)", h);
+    }
+    return MC_OK;
+}
+
+void drop_graphs(mc_ctx* c)
+{
+    for (auto& row : c->gexec)
+        for (auto& g : row)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+// ---- building blocks ------------------------------------------------------
+mc_status warp_into_layouts(mc_ctx* c, const float* x, GateSel sel, int n_slots, bool identity)
+{
+    WarpArgs a{};
+    a.x = x; a.n = c->n;
+    a.rigid = c->d_rigid; a.field = c->d_field; a.identity = identity ? 1 : 0;
+    a.sel = sel; a.n_slots = n_slots;
+    a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+    return launch(c, C_WARP, "warp", [&] { return launch_warp_layouts(a, c->stream); });
+}
+
+FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
+{
+    FwdArgs a{};
+    a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+    a.ang = c->d_fang; a.order = c->d_order; a.items = c->d_items; a.n_items = c->n_items;
+    a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
+    a.sel = sel; a.n_slots = n_slots;
+    a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
+    a.err = c->d_err;
+    return a;
+}
+
+mc_status project_store(mc_ctx* c, GateSel sel, int n_slots, float* out)
+{
+    FwdArgs a = fwd_args(c, sel, n_slots);
+    a.mode = 0; a.out = out;
+    return launch(c, C_PROJ, "project", [&] { return launch_forward(a, c->stream); });
+}
+
+mc_status backproject(mc_ctx* c, int n_slots, float* out)
+{
+    BpArgs a{};
+    a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
+    a.ang = c->d_bang; a.n = c->n; a.na = c->na; a.nb = c->nb; a.n_slots = n_slots;
+    a.pj = c->pj; a.out = out;
+    return launch(c, C_BP, "backproject", [&] { return launch_backproject(a, c->stream); });
+}
+
+WarpAdjArgs wadj_args(mc_ctx* c, GateSel sel, int n_slots, const float* b)
+{
+    WarpAdjArgs a{};
+    a.n = c->n; a.rowptr = c->d_rowptr; a.ent = c->d_ent; a.ent_off = c->d_ent_off;
+    a.sel = sel; a.n_slots = n_slots; a.b = b;
+    return a;
+}
+
+mc_status pad_sinos(mc_ctx* c, const float* y, int n_slots)
+{
+    for (int s = 0; s < n_slots; ++s) {
+        const float* ys = y + (size_t)s * c->na * c->nb;
+        float* dys = c->d_dy + (size_t)s * c->dy_stride;
+        TRY(launch(c, C_MISC, "pad", [&] {
+            return launch_pad_sino(ys, dys, c->na, c->nb, c->Pb, c->Gb, c->stream);
+        }));
+    }
+    return MC_OK;
+}
+
+mc_status reduce(mc_ctx* c, const float* a, const float* b, size_t len, int mode, double* out)
+{
+    return launch(c, C_MISC, "reduce", [&] {
+        return launch_reduce(a, b, len, mode, c->d_part, out, c->stream);
+    });
+}
+
+// A_i^* applied to N_slots sinograms (already padded in d_dy), summed, into out
+mc_status adjoint_from_dy(mc_ctx* c, GateSel sel, int n_slots, float* out)
+{
+    TRY(backproject(c, n_slots, c->d_b));
+    WarpAdjArgs a = wadj_args(c, sel, n_slots, c->d_b);
+    a.out = out;
+    return launch(c, C_WADJ, "warp_adjoint", [&] { return launch_warp_adjoint_store(a, c->stream); });
+}
+
+// ---- one epoch --------------------------------------------------------------
+mc_status enqueue_spdhg_epoch(mc_ctx* c, uint64_t seed, uint32_t stream)
+{
+    const int N = c->N;
+    TRY(launch(c, C_DRAW, "draw_gates", [&] {
+        return launch_draw_gates(seed, stream, c->d_k, 0, N, N, c->d_gates, c->stream);
+    }));
+    const float sigma = (float)c->sS.sigma;
+    const float inv_den = (float)(1.0 / (1.0 + c->sS.sigma * N / 2.0));
+    for (int j = 0; j < N; ++j) {
+        const GateSel sel{c->d_gates + j, -1};
+        float* xin = c->d_x[c->cur];
+        float* xout = c->d_x[c->cur ^ 1];
+        TRY(warp_into_layouts(c, xin, sel, 1, false));
+        FwdArgs fa = fwd_args(c, sel, 1);
+        fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y; fa.sigma = sigma; fa.inv_den = inv_den;
+        TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
+        TRY(backproject(c, 1, c->d_b));
+        WarpAdjArgs wa = wadj_args(c, sel, 1, c->d_b);
+        wa.z = c->d_z; wa.x_in = xin; wa.x_out = xout;
+        wa.coef = (float)(c->sS.theta * N);               // theta / p_i, p_i = 1/N
+        wa.tau = (float)c->sS.tau;
+        wa.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sS.tau * c->alpha));
+        TRY(launch(c, C_WADJ, "warp_adjoint_update", [&] {
+            return launch_warp_adjoint_update(wa, c->stream);
+        }));
+        c->cur ^= 1;
+    }
+    return MC_OK;
+}
+
+mc_status enqueue_pdhg_iter(mc_ctx* c)
+{
+    const int N = c->N;
+    const GateSel sel{nullptr, -1};
+    float* xin = c->d_x[c->cur];
+    float* xout = c->d_x[c->cur ^ 1];
+    TRY(warp_into_layouts(c, xin, sel, N, false));
+    FwdArgs fa = fwd_args(c, sel, N);
+    fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y;
+    fa.sigma = (float)c->sP.sigma;
+    fa.inv_den = (float)(1.0 / (1.0 + c->sP.sigma * N / 2.0));
+    TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
+    TRY(backproject(c, N, c->d_b));
+    WarpAdjArgs wa = wadj_args(c, sel, N, c->d_b);
+    wa.z = c->d_z; wa.x_in = xin; wa.x_out = xout;
+    wa.coef = (float)c->sP.theta;                          // p_i = 1
+    wa.tau = (float)c->sP.tau;
+    wa.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sP.tau * c->alpha));
+    TRY(launch(c, C_WADJ, "warp_adjoint_update", [&] { return launch_warp_adjoint_update(wa, c->stream); }));
+    c->cur ^= 1;
+    return MC_OK;
+}
+
+// Run one epoch of `which` (0 SPDHG, 1 PDHG), as a graph replay when enabled.
+mc_status run_epoch(mc_ctx* c, int which, uint64_t seed, uint32_t stream)
+{
+    auto enqueue = [&]() -> mc_status {
+        return which == 0 ? enqueue_spdhg_epoch(c, seed, stream) : enqueue_pdhg_iter(c);
+    };
+    const int flips = (which == 0) ? (c->N & 1) : 1;
+    if (!c->graph_on || c->prof_on) return enqueue();
+    const int par = c->cur;
+    if (which == 0 && c->gexec[0][par] && (c->g_seed[0] != seed || c->g_stream[0] != stream)) {
+        drop_graphs(c);
+    }
+    if (!c->gexec[which][par]) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const mc_status st = enqueue();
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        c->cur = par;
+        if (st != MC_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return fail(c, MC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        cudaGraphExec_t ge = nullptr;
+        const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) return fail(c, MC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
+        c->gexec[which][par] = ge;
+        if (which == 0) { c->g_seed[0] = seed; c->g_stream[0] = stream; }
+    }
+    CK(cudaGraphLaunch(c->gexec[which][par], c->stream));
+    c->cur ^= flips;
+    return MC_OK;
+}
+
+// trace entry e for the current state; x^K is the buffer that was the input
+// of the last iteration
+mc_status enqueue_trace(mc_ctx* c, int e)
+{
+    double* out = c->d_trace + 3 * (size_t)e;
+    const float* xk = c->d_x[c->cur ^ 1];
+    const size_t n2 = (size_t)c->n * c->n;
+    if (c->have_ref) {
+        TRY(reduce(c, xk, c->d_xstar, n2, kRedDiffSq, c->d_s + S_DX2));
+        TRY(reduce(c, c->d_y, c->d_ystar, (size_t)c->N * c->na * c->nb, kRedDiffSq, c->d_s + S_DY2));
+        TRY(launch(c, C_MISC, "trace", [&] {
+            return launch_trace_combine(c->d_s + S_DX2, c->d_s + S_XS2, c->d_s + S_DY2, out, c->stream);
+        }));
+    } else {
+        TRY(launch(c, C_MISC, "nan", [&] { return launch_fill_nan(out, 2, c->stream); }));
+    }
+    if (c->trace_obj) {
+        // O(x) with all N forward projections at once
+        const size_t ns = (size_t)c->na * c->nb;
+        TRY(warp_into_layouts(c, xk, GateSel{nullptr, -1}, c->N, false));
+        TRY(project_store(c, GateSel{nullptr, -1}, c->N, c->d_sinoN));
+        for (int i = 0; i < c->N; ++i)
+            TRY(reduce(c, c->d_sinoN + i * ns, c->d_d + i * ns, ns, kRedDiffSq, c->d_s + S_RES + i));
+        TRY(reduce(c, xk, nullptr, n2, kRedSumSq, c->d_s + S_XX));
+        TRY(launch(c, C_MISC, "objective", [&] {
+            return launch_objective_combine(c->d_s + S_XX, c->d_s + S_RES, c->N, c->alpha, c->N,
+                                            out + 2, c->stream);
+        }));
+    } else {
+        TRY(launch(c, C_MISC, "nan", [&] { return launch_fill_nan(out + 2, 1, c->stream); }));
+    }
+    return MC_OK;
+}
+
+mc_status update_steps(mc_ctx* c)
+{
+    if (!c->have_norms || !c->have_data) {
+        c->steps_ok = false;
+        drop_graphs(c);
+        return MC_OK;
+    }
+    double mx = 0;
+    for (int i = 0; i < c->N; ++i) mx = std::max(mx, c->norms2[i]);
+    if (!(mx > 0) || !(c->norms2[c->N] > 0)) {
+        c->steps_ok = false;
+        drop_graphs(c);
+        return fail(c, MC_EINVAL, "operator norms must be positive");
+    }
+    const Steps s = make_steps(mx, c->alpha, c->N, c->N);
+    const Steps p = make_steps(c->norms2[c->N], c->alpha, c->N, 1);
+    // captured epochs bake the steps into their kernel arguments
+    auto same = [](const Steps& a, const Steps& b) {
+        return a.sigma == b.sigma && a.tau == b.tau && a.theta == b.theta;
+    };
+    if (!c->steps_ok || !same(s, c->sS) || !same(p, c->sP)) drop_graphs(c);
+    c->sS = s;
+    c->sP = p;
+    c->steps_ok = true;
+    return MC_OK;
+}
+
+// copy an input to device memory if it is a host pointer
+mc_status stage_in(mc_ctx* c, const float* src, float* scratch, size_t count, const float** dev)
+{
+    if (ptr_kind(c, src) == 1) { *dev = src; return MC_OK; }
+    CK(cudaMemcpyAsync(scratch, src, count * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    *dev = scratch;
+    return MC_OK;
+}
+
+// write a device result to dst (host or device) and wait for host copies
+mc_status stage_out(mc_ctx* c, float* dst, const float* dev, size_t count)
+{
+    if (ptr_kind(c, dst) == 1) {
+        if (dst != dev)
+            CK(cudaMemcpyAsync(dst, dev, count * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        return MC_OK;
+    }
+    CK(cudaMemcpyAsync(dst, dev, count * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MC_OK;
+}
+
+mc_status finish(mc_ctx* c)
+{
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(c, MC_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+    if (c->prof_on) TRY(prof_collect(c));
+    return MC_OK;
+}
+
+mc_status check_gate(mc_ctx* c, int gate)
+{
+    if (gate < 0 || gate >= c->N) return fail(c, MC_EINVAL, "gate %d out of range [0, %d)", gate, c->N);
+    return MC_OK;
+}
+
+// ---- creation ---------------------------------------------------------------
+mc_status build_tables(mc_ctx* c)
+{
+    const int n = c->n, na = c->na, nb = c->nb;
+    std::vector<FwdAngle> fa(na);
+    std::vector<BpAngle> ba(na);
+    std::vector<int> order;
+    order.reserve(na);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < na; ++k) {
+            const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
+            if ((pass == 1) == xd) order.push_back(k);
+        }
+    int ny = 0;
+    for (int k = 0; k < na; ++k) {
+        const double phi = (double)k * kPi / (double)na;
+        const double cs = std::cos(phi), sn = std::sin(phi);
+        const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
+        if (!xd) ++ny;
+        const double inv = xd ? 1.0 / sn : 1.0 / cs;
+        const double t = xd ? cs / sn : sn / cs;
+        FwdAngle f{};
+        split_f(inv, f.inv_hi, f.inv_lo);
+        split_f(t, f.t_hi, f.t_lo);
+        f.delta = (float)std::fabs(inv);
+        f.dir = xd ? 1 : 0;
+        fa[k] = f;
+        BpAngle b{};
+        split_f(cs, b.cos_hi, b.cos_lo);
+        split_f(sn, b.sin_hi, b.sin_lo);
+        b.m = (float)std::fabs(inv);
+        b.m2 = (float)(inv * inv);
+        ba[k] = b;
+    }
+    // ray items: rows-driven rays first, then columns-driven; blocks of 256*rpt
+    const long long rays_y = (long long)ny * nb, rays_all = (long long)na * nb;
+    int rpt = 8;
+    while (rpt > 1 && rays_all / (256LL * rpt) < c->sms) rpt >>= 1;
+    c->rpt = rpt;
+    std::vector<RayItem> items;
+    const long long blk = 256LL * rpt;
+    for (int cls = 0; cls < 2; ++cls) {
+        const long long b0 = cls == 0 ? 0 : rays_y, b1 = cls == 0 ? rays_y : rays_all;
+        for (long long s = b0; s < b1; s += blk)
+            items.push_back(RayItem{(int)s, (int)std::min(b1, s + blk), cls, 0});
+    }
+    c->n_items = (int)items.size();
+    TRY(dalloc(c, &c->d_fang, na));
+    TRY(dalloc(c, &c->d_bang, na));
+    TRY(dalloc(c, &c->d_order, na));
+    TRY(dalloc(c, &c->d_items, items.size()));
+    CK(cudaMemcpyAsync(c->d_fang, fa.data(), na * sizeof(FwdAngle), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_bang, ba.data(), na * sizeof(BpAngle), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_order, order.data(), na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));   // host vectors go out of scope
+    // line layouts: guard kGuard in front, >= 4 zero cells behind, 16-byte pitch
+    c->P = ((n + 2 * kGuard) + 3) / 4 * 4;
+    c->layout_stride = (size_t)n * c->P;
+    int lc = (int)(40960 / ((size_t)c->P * sizeof(float)));
+    c->lc = std::max(1, std::min(32, lc));
+    // dual increment layout: guards wide enough for every pixel's two bins
+    const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
+    const int pj_max = 8;
+    c->Gb = std::max(2, (int)std::ceil(std::sqrt(2.0) * (h + pj_max + 1) - hb) + 2);
+    c->Pb = (nb + 2 * c->Gb + 2 + 3) / 4 * 4;
+    c->dy_stride = (size_t)na * c->Pb;
+    c->pj = 4;
+    return MC_OK;
+}
+
+mc_status build_motion(mc_ctx* c, const mc_motion* m)
+{
+    const int n = c->n, N = c->N;
+    c->kind = m->kind;
+    if (m->kind == MC_MOTION_RIGID) {
+        std::vector<RigidGate> rg(N);
+        const double h = 0.5 * (n - 1);
+        for (int i = 0; i < N; ++i) {
+            const double phi = m->rigid[3 * i], tx = m->rigid[3 * i + 1], ty = m->rigid[3 * i + 2];
+            if (!std::isfinite(phi) || !std::isfinite(tx) || !std::isfinite(ty))
+                return fail(c, MC_EINVAL, "rigid motion of gate %d is not finite", i);
+            RigidGate g{};
+            split_f(std::cos(phi), g.cos_hi, g.cos_lo);
+            split_f(std::sin(phi), g.sin_hi, g.sin_lo);
+            split_f(tx + h, g.offx_hi, g.offx_lo);
+            split_f(ty + h, g.offy_hi, g.offy_lo);
+            rg[i] = g;
+        }
+        TRY(dalloc(c, &c->d_rigid, N));
+        CK(cudaMemcpyAsync(c->d_rigid, rg.data(), N * sizeof(RigidGate), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        const size_t cnt = (size_t)N * 2 * n * n;
+        TRY(dalloc(c, &c->d_field, cnt));
+        const int pk = ptr_kind(c, m->field);
+        if (pk < 0) return fail(c, MC_EINVAL, "motion field lives on another device");
+        CK(cudaMemcpyAsync(c->d_field, m->field, cnt * sizeof(float),
+                           pk == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        // reject non-finite or absurd displacements (positions must stay < 2^22)
+        std::vector<float> hf(cnt);
+        CK(cudaMemcpy(hf.data(), c->d_field, cnt * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < cnt; ++i)
+            if (!std::isfinite(hf[i]) || std::fabs(hf[i]) > 1.0e5f)
+                return fail(c, MC_EINVAL, "motion field value %zu is not finite or |u| > 1e5", i);
+    }
+    return MC_OK;
+}
+
+mc_status build_csr(mc_ctx* c)
+{
+    const int n = c->n, N = c->N, n2 = n * n;
+    TRY(dalloc(c, &c->d_rowptr, (size_t)N * (n2 + 1)));
+    int* cnt = nullptr;
+    const int sl = scan_scratch_len(n2);
+    int* scratch = nullptr;
+    TRY(dalloc(c, &cnt, n2));
+    TRY(dalloc(c, &scratch, sl));
+    std::vector<long long> off(N + 1, 0);
+    for (int g = 0; g < N; ++g) {
+        const RigidGate* rg = c->d_rigid ? c->d_rigid + g : nullptr;
+        const float* fl = c->d_field ? c->d_field + (size_t)g * 2 * n2 : nullptr;
+        int* rp = c->d_rowptr + (size_t)g * (n2 + 1);
+        CK(cudaMemsetAsync(cnt, 0, n2 * sizeof(int), c->stream));
+        CK(launch_csr_count(n, rg, fl, cnt, c->stream));
+        CK(launch_exclusive_scan(cnt, rp, n2, scratch, sl, c->stream));
+        int tot = 0;
+        CK(cudaMemcpyAsync(&tot, rp + n2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        off[g + 1] = off[g] + tot;
+    }
+    c->nnz_total = off[N];
+    TRY(dalloc(c, &c->d_ent, (size_t)std::max<long long>(off[N], 1)));
+    TRY(dalloc(c, &c->d_ent_off, N + 1));
+    CK(cudaMemcpyAsync(c->d_ent_off, off.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice,
+                       c->stream));
+    for (int g = 0; g < N; ++g) {
+        const RigidGate* rg = c->d_rigid ? c->d_rigid + g : nullptr;
+        const float* fl = c->d_field ? c->d_field + (size_t)g * 2 * n2 : nullptr;
+        int* rp = c->d_rowptr + (size_t)g * (n2 + 1);
+        CK(cudaMemsetAsync(cnt, 0, n2 * sizeof(int), c->stream));
+        CK(launch_csr_fill(n, rg, fl, rp, cnt, c->d_ent + off[g], c->stream));
+        CK(launch_csr_sort(n, rp, c->d_ent + off[g], c->stream));
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    return MC_OK;
+}
+
+mc_status alloc_state(mc_ctx* c)
+{
+    const size_t n2 = (size_t)c->n * c->n, ns = (size_t)c->na * c->nb;
+    const int N = c->N;
+    TRY(dalloc(c, &c->d_d, N * ns));
+    TRY(dalloc(c, &c->d_y, N * ns));
+    TRY(dalloc(c, &c->d_x[0], n2));
+    TRY(dalloc(c, &c->d_x[1], n2));
+    TRY(dalloc(c, &c->d_z, n2));
+    TRY(dalloc(c, &c->d_lrow, N * c->layout_stride));
+    TRY(dalloc(c, &c->d_lcol, N * c->layout_stride));
+    TRY(dalloc(c, &c->d_dy, N * c->dy_stride));
+    TRY(dalloc(c, &c->d_b, N * n2));
+    TRY(dalloc(c, &c->d_sinoN, N * ns));
+    for (auto& p : c->d_img) TRY(dalloc(c, &p, n2));
+    TRY(dalloc(c, &c->d_sino_io, ns));
+    TRY(dalloc(c, &c->d_k, 1));
+    TRY(dalloc(c, &c->d_gates, std::max(N, 1)));
+    TRY(dalloc(c, &c->d_err, 1));
+    TRY(dalloc(c, &c->d_part, reduce_parts()));
+    TRY(dalloc(c, &c->d_s, S_RES + N + 8));
+    return MC_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* mc_version(void) { return "libmc 0.1 (sm_103a)"; }
+
+const char* mc_last_error(const mc_ctx* ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    static thread_local std::string copy;
+    copy = g_create_err;
+    return copy.c_str();
+}
+
+void mc_destroy(mc_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+mc_status mc_create(const mc_geometry* geom, int32_t n_gates, const mc_motion* motion,
+                    void* cuda_stream, mc_ctx** out)
+{
+    mc_ctx* c = nullptr;
+    if (!out) return fail(nullptr, MC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!geom || !motion) return fail(nullptr, MC_EINVAL, "geometry or motion is NULL");
+    if (geom->n < 2 || geom->n > 2048) return fail(nullptr, MC_EINVAL, "n=%d outside [2, 2048]", geom->n);
+    if (geom->n_angles < 1 || geom->n_angles > 8192)
+        return fail(nullptr, MC_EINVAL, "n_angles=%d outside [1, 8192]", geom->n_angles);
+    if (geom->n_bins < 1 || geom->n_bins > 8192)
+        return fail(nullptr, MC_EINVAL, "n_bins=%d outside [1, 8192]", geom->n_bins);
+    if (n_gates < 1 || n_gates > 4096) return fail(nullptr, MC_EINVAL, "n_gates=%d outside [1, 4096]", n_gates);
+    if (motion->kind == MC_MOTION_RIGID) {
+        if (!motion->rigid) return fail(nullptr, MC_EINVAL, "rigid motion requires motion->rigid");
+    } else if (motion->kind == MC_MOTION_FIELD) {
+        if (!motion->field) return fail(nullptr, MC_EINVAL, "field motion requires motion->field");
+    } else {
+        return fail(nullptr, MC_EINVAL, "unknown motion kind %d", motion->kind);
+    }
+    int dev = 0, ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        return fail(nullptr, MC_EDEVICE, "no CUDA device");
+    }
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, MC_EDEVICE, "cudaGetDevice failed");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+        return fail(nullptr, MC_EDEVICE, "cudaGetDeviceProperties failed");
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(nullptr, MC_EDEVICE, "libmc is built for sm_103a; device %d is sm_%d%d", dev,
+                    prop.major, prop.minor);
+
+    c = new (std::nothrow) mc_ctx();
+    if (!c) return fail(nullptr, MC_ENOMEM, "host allocation failed");
+    c->dev = dev;
+    c->sms = prop.multiProcessorCount;
+    c->n = geom->n; c->na = geom->n_angles; c->nb = geom->n_bins; c->N = n_gates;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(nullptr, MC_ECUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    mc_status st = build_tables(c);
+    if (st == MC_OK) {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t need = forward_smem_bytes(c->lc, c->P);
+        if ((size_t)optin < need) st = fail(c, MC_EDEVICE, "forward needs %zu B shared memory", need);
+        else if (forward_prepare(optin) != cudaSuccess) st = fail(c, MC_ECUDA, "cudaFuncSetAttribute failed");
+    }
+    if (st == MC_OK) st = alloc_state(c);
+    if (st == MC_OK) st = build_motion(c, motion);
+    if (st == MC_OK) st = build_csr(c);
+    if (st == MC_OK) {
+        const cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) st = fail(c, MC_ECUDA, "setup failed: %s", cudaGetErrorString(e));
+    }
+    if (st != MC_OK) {
+        fail(nullptr, st, "%s", c->err.c_str());
+        mc_destroy(c);
+        return st;
+    }
+    *out = c;
+    return MC_OK;
+}
+
+mc_status mc_reset(mc_ctx* c)
+{
+    if (!c) return MC_EINVAL;
+    const size_t n2 = (size_t)c->n * c->n, ns = (size_t)c->na * c->nb;
+    CK(cudaMemsetAsync(c->d_x[0], 0, n2 * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->d_x[1], 0, n2 * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->d_z, 0, n2 * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->d_y, 0, (size_t)c->N * ns * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->d_k, 0, sizeof(unsigned long long), c->stream));
+    c->cur = 0;
+    c->k_host = 0;
+    return finish(c);
+}
+
+mc_status mc_set_data(mc_ctx* c, const float* d, double alpha)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_ptr(c, d, "d"));
+    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MC_EINVAL, "alpha must be finite and > 0");
+    const size_t cnt = (size_t)c->N * c->na * c->nb;
+    CK(cudaMemcpyAsync(c->d_d, d, cnt * sizeof(float),
+                       ptr_kind(c, d) == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->alpha = alpha;
+    c->have_data = true;
+    c->have_ref = false;
+    TRY(mc_reset(c));
+    TRY(update_steps(c));
+    CK(cudaStreamSynchronize(c->stream));
+    return finish(c);
+}
+
+mc_status mc_forward(mc_ctx* c, int32_t gate, const float* x, float* out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_gate(c, gate));
+    TRY(check_ptr(c, x, "x"));
+    TRY(check_ptr(c, out, "out"));
+    const float* xd;
+    TRY(stage_in(c, x, c->d_img[0], (size_t)c->n * c->n, &xd));
+    const bool dev_out = ptr_kind(c, out) == 1;
+    float* o = dev_out ? out : c->d_sino_io;
+    TRY(warp_into_layouts(c, xd, GateSel{nullptr, gate}, 1, false));
+    TRY(project_store(c, GateSel{nullptr, gate}, 1, o));
+    TRY(stage_out(c, out, o, (size_t)c->na * c->nb));
+    return finish(c);
+}
+
+mc_status mc_project(mc_ctx* c, const float* x, float* out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_ptr(c, x, "x"));
+    TRY(check_ptr(c, out, "out"));
+    const float* xd;
+    TRY(stage_in(c, x, c->d_img[0], (size_t)c->n * c->n, &xd));
+    const bool dev_out = ptr_kind(c, out) == 1;
+    float* o = dev_out ? out : c->d_sino_io;
+    TRY(warp_into_layouts(c, xd, GateSel{nullptr, 0}, 1, true));
+    TRY(project_store(c, GateSel{nullptr, 0}, 1, o));
+    TRY(stage_out(c, out, o, (size_t)c->na * c->nb));
+    return finish(c);
+}
+
+mc_status mc_adjoint(mc_ctx* c, int32_t gate, const float* y, float* out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_gate(c, gate));
+    TRY(check_ptr(c, y, "y"));
+    TRY(check_ptr(c, out, "out"));
+    const float* yd;
+    TRY(stage_in(c, y, c->d_sino_io, (size_t)c->na * c->nb, &yd));
+    TRY(pad_sinos(c, yd, 1));
+    const bool dev_out = ptr_kind(c, out) == 1;
+    float* o = dev_out ? out : c->d_img[1];
+    TRY(adjoint_from_dy(c, GateSel{nullptr, gate}, 1, o));
+    TRY(stage_out(c, out, o, (size_t)c->n * c->n));
+    return finish(c);
+}
+
+mc_status mc_backproject(mc_ctx* c, const float* y, float* out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_ptr(c, y, "y"));
+    TRY(check_ptr(c, out, "out"));
+    const float* yd;
+    TRY(stage_in(c, y, c->d_sino_io, (size_t)c->na * c->nb, &yd));
+    TRY(pad_sinos(c, yd, 1));
+    const bool dev_out = ptr_kind(c, out) == 1;
+    float* o = dev_out ? out : c->d_img[1];
+    TRY(backproject(c, 1, o));
+    TRY(stage_out(c, out, o, (size_t)c->n * c->n));
+    return finish(c);
+}
+
+mc_status mc_warp(mc_ctx* c, int32_t gate, const float* x, float* out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_gate(c, gate));
+    TRY(check_ptr(c, x, "x"));
+    TRY(check_ptr(c, out, "out"));
+    const float* xd;
+    TRY(stage_in(c, x, c->d_img[0], (size_t)c->n * c->n, &xd));
+    const bool dev_out = ptr_kind(c, out) == 1;
+    float* o = dev_out ? out : c->d_img[1];
+    WarpArgs a{};
+    a.x = xd; a.n = c->n; a.rigid = c->d_rigid; a.field = c->d_field;
+    a.sel = GateSel{nullptr, gate}; a.n_slots = 1; a.out = o;
+    TRY(launch(c, C_WARP, "warp", [&] { return launch_warp_plain(a, c->stream); }));
+    TRY(stage_out(c, out, o, (size_t)c->n * c->n));
+    return finish(c);
+}
+
+mc_status mc_warp_adjoint(mc_ctx* c, int32_t gate, const float* v, float* out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_gate(c, gate));
+    TRY(check_ptr(c, v, "v"));
+    TRY(check_ptr(c, out, "out"));
+    const float* vd;
+    TRY(stage_in(c, v, c->d_img[0], (size_t)c->n * c->n, &vd));
+    const bool dev_out = ptr_kind(c, out) == 1;
+    float* o = dev_out ? out : c->d_img[1];
+    WarpAdjArgs a = wadj_args(c, GateSel{nullptr, gate}, 1, vd);
+    a.out = o;
+    TRY(launch(c, C_WADJ, "warp_adjoint", [&] { return launch_warp_adjoint_store(a, c->stream); }));
+    TRY(stage_out(c, out, o, (size_t)c->n * c->n));
+    return finish(c);
+}
+
+mc_status mc_norms(mc_ctx* c, int32_t max_iter, double tol, double* out)
+{
+    if (!c) return MC_EINVAL;
+    if (max_iter < 1 || !(tol >= 0)) return fail(c, MC_EINVAL, "max_iter >= 1 and tol >= 0 required");
+    if (out && ptr_kind(c, out) < 0) return fail(c, MC_EINVAL, "out lives on another device");
+    const size_t n2 = (size_t)c->n * c->n;
+    float* v = c->d_img[2];
+    float* w = c->d_img[3];
+    std::vector<double> res(c->N + 1, 0.0);
+    for (int which = 0; which <= c->N; ++which) {
+        const bool stacked = which == c->N;
+        const int slots = stacked ? c->N : 1;
+        const GateSel sel = stacked ? GateSel{nullptr, -1} : GateSel{nullptr, which};
+        // v = constant image of unit norm
+        std::vector<float> ones(n2, (float)(1.0 / std::sqrt((double)n2)));
+        CK(cudaMemcpyAsync(v, ones.data(), n2 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        double lam = 0;
+        for (int it = 0; it < max_iter; ++it) {
+            TRY(warp_into_layouts(c, v, sel, slots, false));
+            TRY(project_store(c, sel, slots, c->d_sinoN));
+            TRY(pad_sinos(c, c->d_sinoN, slots));
+            TRY(adjoint_from_dy(c, sel, slots, w));
+            TRY(reduce(c, v, w, n2, kRedDot, c->d_s + S_LAM));
+            TRY(reduce(c, w, nullptr, n2, kRedSumSq, c->d_s + S_NRM));
+            TRY(launch(c, C_MISC, "normalize", [&] { return launch_normalize(w, c->d_s + S_NRM, n2, c->stream); }));
+            std::swap(v, w);
+            double lam_new = 0;
+            CK(cudaMemcpyAsync(&lam_new, c->d_s + S_LAM, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            const bool conv = lam > 0 && std::fabs(lam_new - lam) <= tol * lam_new;
+            lam = lam_new;
+            if (conv) break;
+        }
+        res[which] = lam;
+    }
+    c->norms2 = res;
+    c->have_norms = true;
+    TRY(update_steps(c));
+    if (out) {
+        if (ptr_kind(c, out) == 1)
+            CK(cudaMemcpyAsync(out, res.data(), res.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        else
+            std::memcpy(out, res.data(), res.size() * sizeof(double));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return finish(c);
+}
+
+mc_status mc_set_norms(mc_ctx* c, const double* norms2)
+{
+    if (!c) return MC_EINVAL;
+    if (!norms2) return fail(c, MC_EINVAL, "norms2 is NULL");
+    std::vector<double> v(c->N + 1);
+    if (ptr_kind(c, norms2) == 1) {
+        CK(cudaMemcpy(v.data(), norms2, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(v.data(), norms2, v.size() * sizeof(double));
+    }
+    for (double x : v)
+        if (!(x > 0) || !std::isfinite(x)) return fail(c, MC_EINVAL, "norms must be finite and > 0");
+    c->norms2 = v;
+    c->have_norms = true;
+    TRY(update_steps(c));
+    return finish(c);
+}
+
+mc_status mc_get_steps(mc_ctx* c, int32_t pdhg, double* out)
+{
+    if (!c) return MC_EINVAL;
+    if (!out) return fail(c, MC_EINVAL, "out is NULL");
+    if (!c->steps_ok) return fail(c, MC_ESTATE, "step sizes need mc_set_data and mc_norms/mc_set_norms");
+    const Steps& s = pdhg ? c->sP : c->sS;
+    const double v[5] = {s.sigma, s.tau, s.theta, s.kappa, s.omega};
+    std::memcpy(out, v, sizeof v);
+    return MC_OK;
+}
+
+mc_status mc_set_reference(mc_ctx* c, const float* x_star)
+{
+    if (!c) return MC_EINVAL;
+    if (!x_star) { c->have_ref = false; return MC_OK; }
+    if (!c->have_data) return fail(c, MC_ESTATE, "mc_set_reference needs mc_set_data first");
+    TRY(check_ptr(c, x_star, "x_star"));
+    const size_t n2 = (size_t)c->n * c->n, ns = (size_t)c->na * c->nb;
+    if (!c->d_xstar) {
+        TRY(dalloc(c, &c->d_xstar, n2));
+        TRY(dalloc(c, &c->d_ystar, (size_t)c->N * ns));
+    }
+    CK(cudaMemcpyAsync(c->d_xstar, x_star, n2 * sizeof(float),
+                       ptr_kind(c, x_star) == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       c->stream));
+    TRY(reduce(c, c->d_xstar, nullptr, n2, kRedSumSq, c->d_s + S_XS2));
+    // y_i* = (2/N)(A_i x* - d_i), all gates at once
+    TRY(warp_into_layouts(c, c->d_xstar, GateSel{nullptr, -1}, c->N, false));
+    TRY(project_store(c, GateSel{nullptr, -1}, c->N, c->d_ystar));
+    const float s = (float)(2.0 / c->N);
+    TRY(launch(c, C_MISC, "axpby", [&] {
+        return launch_axpby(s, c->d_ystar, -s, c->d_d, c->d_ystar, (size_t)c->N * ns, c->stream);
+    }));
+    c->have_ref = true;
+    CK(cudaStreamSynchronize(c->stream));
+    return finish(c);
+}
+
+static mc_status run_common(mc_ctx* c, int which, int32_t epochs, const mc_sampling* smp,
+                            float* x_out, double* trace)
+{
+    if (!c) return MC_EINVAL;
+    if (epochs < 0) return fail(c, MC_EINVAL, "epochs must be >= 0");
+    if (which == 0 && !smp) return fail(c, MC_EINVAL, "sampling is NULL");
+    if (!c->have_data || !c->steps_ok)
+        return fail(c, MC_ESTATE, "runs need mc_set_data and mc_norms/mc_set_norms first");
+    if (x_out && ptr_kind(c, x_out) < 0) return fail(c, MC_EINVAL, "x_out lives on another device");
+    if (trace && ptr_kind(c, trace) < 0) return fail(c, MC_EINVAL, "trace lives on another device");
+    if (trace && epochs > c->trace_cap) {
+        TRY(dalloc(c, &c->d_trace, 3 * (size_t)epochs));
+        c->trace_cap = epochs;
+    }
+    const uint64_t seed = smp ? smp->seed : 0;
+    const uint32_t strm = smp ? smp->stream : 0;
+    for (int e = 0; e < epochs; ++e) {
+        TRY(run_epoch(c, which, seed, strm));
+        if (which == 0) c->k_host += (uint64_t)c->N;
+        if (trace) TRY(enqueue_trace(c, e));
+    }
+    if (x_out) TRY(stage_out(c, x_out, c->d_x[c->cur ^ 1], (size_t)c->n * c->n));
+    if (trace && epochs > 0) {
+        const bool dev = ptr_kind(c, trace) == 1;
+        CK(cudaMemcpyAsync(trace, c->d_trace, 3 * (size_t)epochs * sizeof(double),
+                           dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+        if (!dev) CK(cudaStreamSynchronize(c->stream));
+    }
+    if (c->prof_on) TRY(prof_collect(c));
+    if (!x_out && !trace) {
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return fail(c, MC_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+        return MC_OK;
+    }
+    TRY(check_err_word(c));
+    return finish(c);
+}
+
+mc_status mc_spdhg_run(mc_ctx* c, int32_t epochs, const mc_sampling* sampling, float* x_out,
+                       double* trace)
+{
+    return run_common(c, 0, epochs, sampling, x_out, trace);
+}
+
+mc_status mc_pdhg_run(mc_ctx* c, int32_t epochs, float* x_out, double* trace)
+{
+    return run_common(c, 1, epochs, nullptr, x_out, trace);
+}
+
+mc_status mc_draw_gates(mc_ctx* c, const mc_sampling* smp, uint64_t k0, int32_t count, int32_t* out)
+{
+    if (!c) return MC_EINVAL;
+    if (!smp) return fail(c, MC_EINVAL, "sampling is NULL");
+    if (count < 0) return fail(c, MC_EINVAL, "count must be >= 0");
+    if (count == 0) return MC_OK;
+    TRY(check_ptr(c, out, "out"));
+    const bool dev = ptr_kind(c, out) == 1;
+    int* o = out;
+    if (!dev) {
+        if (count > c->draw_cap) {
+            TRY(dalloc(c, &c->d_draw_out, (size_t)count));
+            c->draw_cap = count;
+        }
+        o = c->d_draw_out;
+    }
+    TRY(launch(c, C_DRAW, "draw_gates", [&] {
+        return launch_draw_gates(smp->seed, smp->stream, nullptr, k0, count, c->N, o, c->stream);
+    }));
+    if (!dev) {
+        CK(cudaMemcpyAsync(out, o, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return finish(c);
+}
+
+mc_status mc_objective(mc_ctx* c, const float* x, double* out)
+{
+    if (!c) return MC_EINVAL;
+    if (!c->have_data) return fail(c, MC_ESTATE, "mc_objective needs mc_set_data first");
+    TRY(check_ptr(c, x, "x"));
+    if (!out) return fail(c, MC_EINVAL, "out is NULL");
+    const size_t n2 = (size_t)c->n * c->n, ns = (size_t)c->na * c->nb;
+    const float* xd;
+    TRY(stage_in(c, x, c->d_img[0], n2, &xd));
+    TRY(warp_into_layouts(c, xd, GateSel{nullptr, -1}, c->N, false));
+    TRY(project_store(c, GateSel{nullptr, -1}, c->N, c->d_sinoN));
+    for (int i = 0; i < c->N; ++i)
+        TRY(reduce(c, c->d_sinoN + i * ns, c->d_d + i * ns, ns, kRedDiffSq, c->d_s + S_RES + i));
+    TRY(reduce(c, xd, nullptr, n2, kRedSumSq, c->d_s + S_XX));
+    TRY(launch(c, C_MISC, "objective", [&] {
+        return launch_objective_combine(c->d_s + S_XX, c->d_s + S_RES, c->N, c->alpha, c->N,
+                                        c->d_s + S_TMP, c->stream);
+    }));
+    double v = 0;
+    CK(cudaMemcpyAsync(&v, c->d_s + S_TMP, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (ptr_kind(c, out) == 1) CK(cudaMemcpy(out, &v, sizeof v, cudaMemcpyHostToDevice));
+    else *out = v;
+    return finish(c);
+}
+
+mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
+{
+    if (!c) return MC_EINVAL;
+    switch (option) {
+    case MC_OPT_GRAPH: c->graph_on = value != 0; if (!c->graph_on) drop_graphs(c); return MC_OK;
+    case MC_OPT_PROFILE: c->prof_on = value != 0; return MC_OK;
+    case MC_OPT_TRACE_OBJECTIVE: c->trace_obj = value != 0; return MC_OK;
+    default: return fail(c, MC_EINVAL, "unknown option %d", option);
+    }
+}
+
+mc_status mc_profile_read(mc_ctx* c, int32_t cap, const char** names, int64_t* counts, double* ms,
+                          int32_t* n_out)
+{
+    if (!c) return MC_EINVAL;
+    TRY(prof_collect(c));
+    if (n_out) *n_out = kNumClasses;
+    for (int i = 0; i < kNumClasses && i < cap; ++i) {
+        if (names) names[i] = kClassNames[i];
+        if (counts) counts[i] = c->prof_count[i];
+        if (ms) ms[i] = c->prof_ms[i];
+    }
+    return MC_OK;
+}
+
+mc_status mc_profile_reset(mc_ctx* c)
+{
+    if (!c) return MC_EINVAL;
+    TRY(prof_collect(c));
+    for (int i = 0; i < kNumClasses; ++i) { c->prof_count[i] = 0; c->prof_ms[i] = 0; }
+    return MC_OK;
+}
+
+mc_status mc_iteration(mc_ctx* c, uint64_t* out)
+{
+    if (!c || !out) return MC_EINVAL;
+    *out = c->k_host;
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,143 @@
+// Device-side layouts, tables and helpers shared by the libmc kernels.
+//
+// HBM layouts (per gate slot):
+//   line layouts  Two copies of the warped image w = D_i x, each as n lines
+//                 of pitch P floats with kGuard zero cells before the data:
+//                 ROWS  line l = image row l    (used by rows-driven angles),
+//                 COLS  line l = image column l (used by columns-driven angles).
+//                 Zero guards make the Joseph interpolation branch-free.
+//   dy            Dual increment y_i^{k+1} - y_i^k as n_angles lines of pitch
+//                 Pb floats with Gb zero bins before the data, so that the
+//                 pixel-driven gather reads both interpolation bins without
+//                 bounds checks.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mcg {
+
+constexpr int kGuard = 4;                 // zero cells before each image line
+constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23
+constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
+
+// Joseph sampling table of one angle (host float64 -> float32 pairs).
+// Along a line l of the driving axis the ray (k, b) sits at the padded
+// position u = (b - hb) * inv - (l - h) * t + h + kGuard.
+struct FwdAngle {
+    float inv_hi, inv_lo;   // 1/sin (columns-driven) or 1/cos (rows-driven)
+    float t_hi, t_lo;       // cos/sin or sin/cos
+    float delta;            // |inv| = sample step length
+    int dir;                // 1: lines are image columns, 0: image rows
+    int pad0, pad1;
+};
+
+// Pixel-driven gather table of one angle: pixel (r, c) projects to the
+// detector coordinate beta = (c - h) cos + (r - h) sin + hb (+ Gb padding).
+struct BpAngle {
+    float cos_hi, cos_lo, sin_hi, sin_lo;
+    float m;                // 1/max(|sin|, |cos|): step length, also hat slope
+    float m2;               // m*m
+    float pad0, pad1;
+};
+
+// Rigid warp of one gate: q = R(phi) p + t about the image centre, stored as
+// float pairs so that positions are exact to ~1e-6 px at any image size.
+struct RigidGate {
+    float cos_hi, cos_lo, sin_hi, sin_lo;
+    float offx_hi, offx_lo, offy_hi, offy_lo;   // tx + h, ty + h
+};
+
+// One block of forward rays: flattened ray indices [begin, end) of the
+// angle order table, all with the same driving axis.
+struct RayItem {
+    int begin, end, dir, pad;
+};
+
+// ---- exact little helpers ------------------------------------------------
+// floor(v) as float, and its integer in i (valid for |v| < 2^22): adding
+// 1.5*2^23 with round-toward-minus-infinity leaves floor(v) in the mantissa.
+__device__ __forceinline__ float floor_magic(float v, int& i)
+{
+    const float t = __fadd_rd(v, kMagic);
+    i = __float_as_int(t) - kMagicBits;
+    return __fsub_rn(t, kMagic);
+}
+
+// Error-free sum: s + e == a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// x * (yhi + ylo) as a float pair (x exactly representable, |x| < 2^12).
+__device__ __forceinline__ void mul_df(float x, float yhi, float ylo, float& hi, float& lo)
+{
+    hi = __fmul_rn(x, yhi);
+    lo = fmaf(x, ylo, fmaf(x, yhi, -hi));
+}
+
+// Split hi + lo (|lo| << 1) into an integer part and a fraction in [0, 1).
+__device__ __forceinline__ void split_int_frac(float hi, float lo, int& ip, float& frac)
+{
+    const float f = floorf(hi);
+    ip = (int)f;
+    frac = __fadd_rn(__fsub_rn(hi, f), lo);
+    if (frac < 0.0f) { frac = __fadd_rn(frac, 1.0f); ip -= 1; }
+    else if (frac >= 1.0f) { frac = __fsub_rn(frac, 1.0f); ip += 1; }
+}
+
+// Bilinear taps of the pull-back warp at output pixel (r, c): top-left
+// source pixel (r0, c0) and fractions (fr, fc).  Rigid positions are
+// computed in float-pair arithmetic; dense fields split u into integer and
+// fraction exactly.  K1 (warp) and K2 (transpose CSR) both call this, so
+// D_i^T is the exact transpose of D_i.
+__device__ __forceinline__ void warp_taps(const RigidGate* rg, const float* field, int n,
+                                          int r, int c, int& r0, int& c0, float& fr, float& fc)
+{
+    if (field) {
+        const size_t p = (size_t)r * n + c;
+        const float ux = field[p], uy = field[(size_t)n * n + p];
+        const float fx = floorf(ux), fy = floorf(uy);
+        c0 = c + (int)fx; fc = __fsub_rn(ux, fx);
+        r0 = r + (int)fy; fr = __fsub_rn(uy, fy);
+    } else {
+        const float h = 0.5f * (float)(n - 1);
+        const float X = (float)c - h, Y = (float)r - h;    // exact
+        float a_hi, a_lo, b_hi, b_lo, s, e, s2, e2;
+        // column: X cos - Y sin + (tx + h)
+        mul_df(X, rg->cos_hi, rg->cos_lo, a_hi, a_lo);
+        mul_df(-Y, rg->sin_hi, rg->sin_lo, b_hi, b_lo);
+        two_sum(a_hi, b_hi, s, e);
+        two_sum(s, rg->offx_hi, s2, e2);
+        split_int_frac(s2, ((a_lo + b_lo) + (e + e2)) + rg->offx_lo, c0, fc);
+        // row: X sin + Y cos + (ty + h)
+        mul_df(X, rg->sin_hi, rg->sin_lo, a_hi, a_lo);
+        mul_df(Y, rg->cos_hi, rg->cos_lo, b_hi, b_lo);
+        two_sum(a_hi, b_hi, s, e);
+        two_sum(s, rg->offy_hi, s2, e2);
+        split_int_frac(s2, ((a_lo + b_lo) + (e + e2)) + rg->offy_lo, r0, fr);
+    }
+}
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) ----------------------------------
+__device__ __forceinline__ uint32_t philox_word0(uint64_t seed, uint32_t stream, uint64_t k)
+{
+    uint32_t c0 = (uint32_t)k, c1 = stream, c2 = (uint32_t)(k >> 32), c3 = 0u;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+    return c0;
+}
+
+// ---- error word ----------------------------------------------------------
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrBounds = 2 };
+
+}  // namespace mcg

@@ -1,0 +1,135 @@
+// Host-side launchers of the libmc kernels (one translation unit each).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mc_device.cuh"
+
+namespace mcg {
+
+// Which gate a gate slot works on: list[slot] if list, else fixed if >= 0,
+// else the slot index itself (PDHG: slot i is gate i).
+struct GateSel {
+    const int* list;
+    int fixed;
+};
+
+// ---- K1: warp w = D_i x into the two line layouts (or a plain image) ------
+struct WarpArgs {
+    const float* x;            // n*n input image (shared by all slots)
+    int n;
+    const RigidGate* rigid;    // per gate, or null
+    const float* field;        // per gate 2*n*n, or null
+    int identity;              // 1: w = x (no motion; the ray transform alone)
+    GateSel sel;
+    int n_slots;
+    float* lrow;               // line layouts, slot stride layout_stride floats
+    float* lcol;
+    size_t layout_stride;
+    int P;                     // line pitch (floats)
+    float* out;                // plain mode: n*n per slot
+};
+cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s);
+cudaError_t launch_warp_plain(const WarpArgs& a, cudaStream_t s);
+
+// ---- K2: per-gate CSR of D_i^T --------------------------------------------
+cudaError_t launch_csr_count(int n, const RigidGate* rg, const float* field, int* cnt,
+                             cudaStream_t s);
+cudaError_t launch_exclusive_scan(const int* in, int* out_rowptr, int len, int* scratch,
+                                  int scratch_len, cudaStream_t s);
+int scan_scratch_len(int len);
+cudaError_t launch_csr_fill(int n, const RigidGate* rg, const float* field,
+                            const int* rowptr, int* cursor, int2* ent, cudaStream_t s);
+cudaError_t launch_csr_sort(int n, const int* rowptr, int2* ent, cudaStream_t s);
+
+// ---- K5 (+K7): v = sum_slots D_gate^T b_slot, then store or update ----------
+struct WarpAdjArgs {
+    int n;
+    const int* rowptr;         // gate g: rowptr + g*(n*n+1)
+    const int2* ent;           // gate g: ent + ent_off[g]
+    const long long* ent_off;
+    GateSel sel;
+    int n_slots;
+    const float* b;            // slot stride n*n
+    // store mode
+    float* out;
+    // update mode (fused z / zbar / primal prox of Algorithm 1)
+    float* z;
+    const float* x_in;
+    float* x_out;
+    float coef;                // theta / p_i
+    float tau;
+    float prox_scale;          // 1 / (1 + 2 tau alpha)
+};
+cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s);
+cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s);
+
+// ---- K3 (+K6): Joseph forward projection ------------------------------------
+struct FwdArgs {
+    const float* lrow;
+    const float* lcol;
+    size_t layout_stride;
+    int P;
+    const FwdAngle* ang;
+    const int* order;          // angle order: rows-driven first, then columns-driven
+    const RayItem* items;
+    int n_items;
+    int rpt;                   // rays per thread (1, 2, 4, 8)
+    int lc;                    // lines per staged chunk
+    int n, na, nb;
+    GateSel sel;
+    int n_slots;
+    int mode;                  // 0: store A w; 1: dual update of Algorithm 1 (ii)
+    float* out;                // mode 0: slot stride na*nb
+    const float* d;            // mode 1: gate stride na*nb
+    float* y;
+    float* dy;                 // slot stride dy_stride, pitch Pb, guard Gb
+    size_t dy_stride;
+    int Pb, Gb;
+    float sigma;
+    float inv_den;             // 1 / (1 + sigma N / 2)
+    int* err;
+};
+cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
+size_t forward_smem_bytes(int lc, int P);
+cudaError_t forward_prepare(int max_smem);
+
+// ---- K4: pixel-driven gather backprojection ---------------------------------
+struct BpArgs {
+    const float* dy;           // slot stride dy_stride, pitch Pb, guard Gb
+    size_t dy_stride;
+    int Pb, Gb;
+    const BpAngle* ang;
+    int n, na, nb;
+    int n_slots;
+    int pj;                    // pixels per thread along a column (4 or 8)
+    float* out;                // slot stride n*n
+};
+cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
+
+// ---- misc -------------------------------------------------------------------
+cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
+                              uint64_t k0, int count, int n_gates, int* out, cudaStream_t s);
+// copy a na x nb sinogram into the padded dy layout (guards stay zero)
+cudaError_t launch_pad_sino(const float* y, float* dy, int na, int nb, int Pb, int Gb,
+                            cudaStream_t s);
+// FP64 reductions, deterministic; result in out[0] (device)
+enum { kRedSumSq = 0, kRedDiffSq = 1, kRedDot = 2 };
+int reduce_parts();
+cudaError_t launch_reduce(const float* a, const float* b, size_t len, int mode,
+                          double* partial, double* out, cudaStream_t s);
+// out[i] = a * x[i] + b * y[i]  (y may be null -> b ignored)
+cudaError_t launch_axpby(float a, const float* x, float b, const float* y, float* out,
+                         size_t len, cudaStream_t s);
+// x[i] *= scale where scale = 1/sqrt(*norm2) read on the device
+cudaError_t launch_normalize(float* x, const double* norm2, size_t len, cudaStream_t s);
+// trace entry: out[0] = sqrt(dx2 / xs2), out[1] = dx2 + dy2 (device scalars)
+cudaError_t launch_trace_combine(const double* dx2, const double* xs2, const double* dy2,
+                                 double* out, cudaStream_t s);
+// out = alpha * xx + sum(res) / N
+cudaError_t launch_objective_combine(const double* xx, const double* res, int n_res,
+                                     double alpha, int N, double* out, cudaStream_t s);
+cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s);
+
+}  // namespace mcg

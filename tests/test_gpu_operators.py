@@ -1,0 +1,185 @@
+"""GPU parity of every operator kernel against the FP64 oracle, called
+through the C ABI.  Tolerance: 1e-5 relative L2 per float32 operator
+application; the transpose pair passes the float32 dot test to ~1e-6;
+integer work (gate draw) is bit-exact."""
+import math
+
+import numpy as np
+import pytest
+
+import mc_synth as S
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def cuda(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float32)).cuda().contiguous()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module")
+def mc():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2410_10503_gb300 as M
+    from paper_2410_10503_gb300 import build
+    build.build()
+    return M
+
+
+GEOMS = [
+    (2, 1, 1), (3, 2, 4), (9, 4, 13), (16, 8, 23), (37, 41, 53), (64, 60, 64),
+    (100, 36, 141), (128, 180, 183),
+]
+
+
+def _rigid(N, seed, rot=5.0, shift=3.0):
+    return S.rigid_motion(N, rot, shift, seed)
+
+
+@pytest.mark.parametrize("n,na,nb", GEOMS)
+def test_project_matches_oracle(mc, n, na, nb):
+    g = O.Geometry(n, na, nb)
+    ctx = mc.Context(n, na, nb, 1, rigid=np.zeros((1, 3)))
+    for x in (S.phantom(n, 6, 1, n / 16 + 0.5, n / 4 + 1), S.random_image(n, 2) - 0.5):
+        y = host(ctx.project(cuda(x)))
+        assert rel_l2(y, O.A(x, g)) <= TOL
+
+
+@pytest.mark.parametrize("n,na,nb", GEOMS)
+def test_backproject_matches_oracle(mc, n, na, nb):
+    g = O.Geometry(n, na, nb)
+    ctx = mc.Context(n, na, nb, 1, rigid=np.zeros((1, 3)))
+    y = S.random_sinogram(na, nb, 3)
+    x = host(ctx.backproject(cuda(y)))
+    assert rel_l2(x, O.At(y, g)) <= TOL
+
+
+@pytest.mark.parametrize("kind", ["rigid", "field"])
+@pytest.mark.parametrize("n", [16, 37, 128])
+def test_warp_and_transpose_match_oracle(mc, kind, n):
+    N = 3
+    if kind == "rigid":
+        rig = _rigid(N, 5, rot=8.0, shift=6.0)
+        m = O.Motion(rigid=rig)
+        ctx = mc.Context(n, 4, n + 3, N, rigid=rig)
+    else:
+        f = S.rbf_fields(n, N, seed=6, width=max(2.0, n / 8), max_disp=max(1.5, n / 16))
+        m = O.Motion(fields=f)
+        ctx = mc.Context(n, 4, n + 3, N, fields=cuda(f))
+    x = S.random_image(n, 7)
+    v = S.random_image(n, 8) - 0.5
+    for i in range(N):
+        assert rel_l2(host(ctx.warp(i, cuda(x))), O.D(x, m, i, n)) <= TOL
+        assert rel_l2(host(ctx.warp_adjoint(i, cuda(v))), O.Dt(v, m, i, n)) <= TOL
+
+
+def test_zero_motion_warp_is_exact_identity(mc):
+    n = 40
+    ctx = mc.Context(n, 4, 43, 2, rigid=np.zeros((2, 3)))
+    x = cuda(S.random_image(n, 9))
+    assert torch.equal(ctx.warp(1, x), x)
+    assert torch.equal(ctx.warp_adjoint(1, x), x)
+
+
+@pytest.mark.parametrize("kind", ["rigid", "field"])
+def test_gated_forward_adjoint_match_oracle(mc, kind):
+    n, na, nb, N = 128, 180, 183, 4
+    g = O.Geometry(n, na, nb)
+    if kind == "rigid":
+        rig = _rigid(N, 10)
+        m = O.Motion(rigid=rig)
+        ctx = mc.Context(n, na, nb, N, rigid=rig)
+    else:
+        f = S.rbf_fields(n, N, seed=11, width=20.0, max_disp=4.0)
+        m = O.Motion(fields=f)
+        ctx = mc.Context(n, na, nb, N, fields=f)
+    P = O.Problem(g, m, np.zeros((N, na, nb)), 1.0)
+    x = S.phantom(n, 10, 12, 5, 40)
+    xr = S.random_image(n, 13) - 0.5
+    y = S.random_sinogram(na, nb, 14)
+    for i in range(N):
+        assert rel_l2(host(ctx.forward(i, cuda(x))), O.Ai(x, P, i)) <= TOL
+        assert rel_l2(host(ctx.forward(i, cuda(xr))), O.Ai(xr, P, i)) <= TOL
+        assert rel_l2(host(ctx.adjoint(i, cuda(y))), O.Ait(y, P, i)) <= TOL
+
+
+def test_float32_dot_test(mc):
+    """<A_i x, y> = <x, A_i^* y> with both sides from the GPU kernels."""
+    n, na, nb, N = 128, 180, 183, 3
+    rig = _rigid(N, 15)
+    ctx = mc.Context(n, na, nb, N, rigid=rig)
+    x = S.random_image(n, 16)
+    y = S.random_sinogram(na, nb, 17)
+    for i in range(N):
+        ax = host(ctx.forward(i, cuda(x)))
+        aty = host(ctx.adjoint(i, cuda(y)))
+        lhs, rhs = float(np.sum(ax * y)), float(np.sum(x * aty))
+        assert abs(lhs - rhs) <= 2e-6 * math.sqrt(np.sum(ax ** 2) * np.sum(y ** 2))
+
+
+def test_headline_size_operators(mc):
+    """512^2 image, 720 angles x 729 bins, N = 10 rigid gates (the benchmark
+    workload), full outputs against the oracle."""
+    n, na, nb, N = 512, 720, 729, 10
+    g = O.Geometry(n, na, nb)
+    rig = S.rigid_motion(N, 8.0, 6.0, seed=2002)
+    ctx = mc.Context(n, na, nb, N, rigid=rig)
+    P = O.Problem(g, O.Motion(rigid=rig), np.zeros((N, na, nb)), 1.0)
+    x = S.phantom(n, 40, 1002)
+    y = S.random_sinogram(na, nb, 18)
+    i = 7
+    assert rel_l2(host(ctx.forward(i, cuda(x))), O.Ai(x, P, i)) <= TOL
+    assert rel_l2(host(ctx.adjoint(i, cuda(y))), O.Ait(y, P, i)) <= TOL
+
+
+def test_host_and_device_pointers_agree(mc):
+    n, na, nb = 64, 60, 64
+    rig = _rigid(2, 19)
+    ctx = mc.Context(n, na, nb, 2, rigid=rig)
+    x = S.random_image(n, 20).astype(np.float32)
+    y = S.random_sinogram(na, nb, 21).astype(np.float32)
+    np.testing.assert_array_equal(ctx.forward(1, x), host(ctx.forward(1, cuda(x))).astype(np.float32))
+    np.testing.assert_array_equal(ctx.adjoint(1, y), host(ctx.adjoint(1, cuda(y))).astype(np.float32))
+
+
+def test_operators_are_deterministic(mc):
+    n, na, nb = 96, 90, 101
+    rig = _rigid(2, 22)
+    ctx = mc.Context(n, na, nb, 2, rigid=rig)
+    x, y = cuda(S.random_image(n, 23)), cuda(S.random_sinogram(na, nb, 24))
+    assert torch.equal(ctx.forward(1, x), ctx.forward(1, x))
+    assert torch.equal(ctx.adjoint(1, y), ctx.adjoint(1, y))
+
+
+def test_gate_draw_bit_exact(mc):
+    ctx = mc.Context(8, 4, 9, 10, rigid=np.zeros((10, 3)))
+    for seed, stream, k0 in [(4002, 0, 0), (12345678901, 3, 2**32 - 5), (7, 1, 10**9)]:
+        got = ctx.draw_gates(seed, stream, k0, 5000)
+        np.testing.assert_array_equal(got, O.draw_gates(seed, stream, k0, 5000, 10))
+
+
+def test_invalid_gate_and_state_errors(mc):
+    ctx = mc.Context(16, 8, 23, 2, rigid=np.zeros((2, 3)))
+    with pytest.raises(mc.MCError) as e:
+        ctx.forward(2, cuda(np.zeros((16, 16))))
+    assert "MC_EINVAL" in str(e.value)
+    with pytest.raises(mc.MCError) as e:
+        ctx.spdhg_run(1, seed=1)
+    assert "MC_ESTATE" in str(e.value)
+    with pytest.raises(mc.MCError):
+        ctx.set_data(np.zeros(2 * 8 * 23, np.float32), alpha=-1.0)
