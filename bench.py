@@ -264,6 +264,34 @@ def run_ours(args, W):
         print(json.dumps(out))
 
 
+def run_ncu_case(args, W):
+    """Kernel-profiling driver: warm-up + timed SPDHG epochs of the workload as
+    plain launches (41 per epoch at N = 10), nothing else on the GPU after the
+    data setup.  Step sizes come from a fixed squared norm, which changes no
+    kernel's work."""
+    import torch
+
+    import paper_2410_10503_gb300 as mc
+    from paper_2410_10503_gb300 import build
+    build.build()
+    sd = S.seeds(W.cid)
+    rig = S.rigid_motion(W.n_gates, W.max_rot_deg, W.max_shift, sd["motion"])
+    ctx = mc.Context(W.n, W.n_angles, W.n_bins, W.n_gates, rigid=rig)
+    x_t = torch.as_tensor(S.phantom(W.n, W.n_ellipses, sd["phantom"], W.axis_lo, W.axis_hi),
+                          dtype=torch.float32, device="cuda")
+    d = torch.empty((W.n_gates, W.n_angles, W.n_bins), dtype=torch.float32, device="cuda")
+    for i in range(W.n_gates):
+        ctx.forward(i, x_t, out=d[i])
+    ctx.set_data(d, W.alpha)
+    ctx.set_norms(np.full(W.n_gates + 1, 3.5e5))
+    ctx.set_option(1, 0)
+    for _ in range(args.warmup + args.steps):
+        ctx.spdhg_run(1, seed=sd["gates"], x_out=False)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"ncu_case": W.name, "epochs": args.warmup + args.steps}))
+
+
 def _oracle_pair_setup(W):
     import oracle as O
     sd = S.seeds(W.cid)
@@ -321,10 +349,15 @@ def main():
     ap.add_argument("--cpu-pairs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--l1-peak-gbs", type=float, default=152 * 128 * 2.07)
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="profiling driver: set up the workload, then only warm-up + timed "
+                         "epochs as plain launches (no norms, e2e, profile or CPU legs)")
     args = ap.parse_args()
     W = S.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, W)
+    elif args.ncu_case:
+        run_ncu_case(args, W)
     else:
         run_ours(args, W)
 

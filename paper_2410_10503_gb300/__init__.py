@@ -6,6 +6,11 @@ CUDA tensors are passed as device pointers, everything else as host pointers
 (the library stages those through its own device buffers).  Results come back
 as CUDA tensors when the input was one, else as numpy arrays.
 
+Streams: the library orders its work on the context's stream.  Calls that
+take CUDA tensors are ordered after the caller's current torch stream (the
+context stream waits on it) and the current stream waits for the context
+stream afterwards, so results behave as if computed on the current stream.
+
 Every computation runs in the library's CUDA kernels; when libmc is not
 built, or no sm_103a GPU is present, the calls raise instead of falling back.
 """
@@ -87,6 +92,13 @@ class Context:
             p, k = _arg(fields, np.float32, n_gates * 2 * n * n, "fields")
             m = N.mc_motion(N.MC_MOTION_FIELD, None, p)
         keep.append(k)
+        self._stream = None
+        if torch is not None and torch.cuda.is_available():
+            self._stream = (torch.cuda.ExternalStream(stream) if stream
+                            else torch.cuda.Stream())
+            stream = self._stream.cuda_stream
+        if keep and _is_tensor(keep[0]) and keep[0].is_cuda:
+            self._stream.wait_stream(torch.cuda.current_stream())
         out = ctypes.c_void_p()
         st = L.mc_create(ctypes.byref(g), n_gates, ctypes.byref(m),
                          ctypes.c_void_p(stream) if stream else None, ctypes.byref(out))
@@ -99,6 +111,27 @@ class Context:
     def _check(self, st: int):
         if st != 0:
             raise MCError(st, self._L.mc_last_error(self._h).decode())
+
+    @property
+    def stream(self):
+        """The torch stream the context orders its work on (None without CUDA)."""
+        return self._stream
+
+    def _call(self, fn, *args, cuda_args=()):
+        """Run one C call ordered after the current torch stream when any of
+        `cuda_args` is a CUDA tensor, and make the current stream wait for it."""
+        handoff = self._stream is not None and any(
+            _is_tensor(a) and a.is_cuda for a in cuda_args)
+        if handoff:
+            cur = torch.cuda.current_stream()
+            if cur != self._stream:
+                self._stream.wait_stream(cur)
+        st = fn(self._h, *args)
+        if handoff:
+            cur = torch.cuda.current_stream()
+            if cur != self._stream:
+                cur.wait_stream(self._stream)
+        self._check(st)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -131,7 +164,7 @@ class Context:
         if out is None:
             out = _empty_like_kind(x, out_shape)
         po, ko = _arg(out, np.float32, int(np.prod(out_shape)), "out")
-        self._check(fn(self._h, *args, px, po))
+        self._call(fn, *args, px, po, cuda_args=(x, out))
         return out
 
     def forward(self, gate: int, x, out=None):
@@ -162,7 +195,7 @@ class Context:
     # -- problem ------------------------------------------------------------------
     def set_data(self, d, alpha: float):
         p, k = _arg(d, np.float32, self.n_gates * self.sino_count, "d")
-        self._check(self._L.mc_set_data(self._h, p, float(alpha)))
+        self._call(self._L.mc_set_data, p, float(alpha), cuda_args=(d,))
 
     def norms(self, max_iter: int = 200, tol: float = 1e-6) -> np.ndarray:
         out = np.empty(self.n_gates + 1)
@@ -183,7 +216,7 @@ class Context:
             self._check(self._L.mc_set_reference(self._h, None))
             return
         p, k = _arg(x_star, np.float32, self.img_count, "x_star")
-        self._check(self._L.mc_set_reference(self._h, p))
+        self._call(self._L.mc_set_reference, p, cuda_args=(x_star,))
 
     def reset(self):
         self._check(self._L.mc_reset(self._h))
@@ -199,9 +232,9 @@ class Context:
         pt = tr.ctypes.data if tr is not None else None
         if which == 0:
             s = N.mc_sampling(seed, stream)
-            self._check(self._L.mc_spdhg_run(self._h, epochs, ctypes.byref(s), px, pt))
+            self._call(self._L.mc_spdhg_run, epochs, ctypes.byref(s), px, pt, cuda_args=(x_out,))
         else:
-            self._check(self._L.mc_pdhg_run(self._h, epochs, px, pt))
+            self._call(self._L.mc_pdhg_run, epochs, px, pt, cuda_args=(x_out,))
         return x_out, tr
 
     def spdhg_run(self, epochs: int, seed: int, stream: int = 0, x_out=None, trace=False, like=None):
@@ -217,13 +250,13 @@ class Context:
             out = np.empty(count, np.int32)
         p = _arg(out, np.int32, count, "out")[0]
         s = N.mc_sampling(seed, stream)
-        self._check(self._L.mc_draw_gates(self._h, ctypes.byref(s), k0, count, p))
+        self._call(self._L.mc_draw_gates, ctypes.byref(s), k0, count, p, cuda_args=(out,))
         return out
 
     def objective(self, x) -> float:
         p, k = _arg(x, np.float32, self.img_count, "x")
         out = ctypes.c_double()
-        self._check(self._L.mc_objective(self._h, p, ctypes.addressof(out)))
+        self._call(self._L.mc_objective, p, ctypes.addressof(out), cuda_args=(x,))
         return out.value
 
     def set_option(self, option: int, value: int):
