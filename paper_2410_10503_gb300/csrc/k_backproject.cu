@@ -6,13 +6,17 @@
 // hat(t) = max(0, 1 - |t|).  As a function of the bin, u - p = (b - beta) * inv_k
 // with beta the detector coordinate of the pixel centre, so pixel (r, c)
 // collects from exactly two bins per angle, floor(beta) and floor(beta) + 1,
-// with weights m * max(0, 1 - d m) and m * max(0, 1 - (1 - d) m), d = frac(beta),
+// with weights m * sat(1 - d m) and m * sat(1 - (1 - d) m), d = frac(beta),
 // m = |inv_k| = Delta_k.  This is the transpose of the forward matrix; no
-// atomics, every pixel is written once.
+// atomics, every pixel is written once.  The dual increment arrives as pairs
+// (m dy[b], m dy[b+1]) so one 8-byte load feeds both weights.
 //
-// Each thread owns PJ consecutive rows of one column.  Per angle it forms
-// beta of its first pixel in float-pair arithmetic (integer bin + fraction)
-// and steps the fraction by sin(phi) down the column, so d is exact to ~1e-6.
+// A block owns a tile of 32 columns x PJ rows; its 8 warps all cover that
+// tile, each for every 8th angle, and their partial sums are added in a fixed
+// order through shared memory at the end.  A thread owns PJ consecutive rows
+// of one column: per angle it forms beta of its first pixel in float-pair
+// arithmetic (integer bin + fraction) and steps the fraction by sin(phi) down
+// the column, so d is exact to ~1e-6 whatever the image size.
 #include "mc_kernels.h"
 
 namespace mcg {
@@ -20,35 +24,35 @@ namespace mcg {
 namespace {
 
 constexpr int kAngChunk = 256;   // angle-table entries staged in shared memory
+constexpr int kGroups = 8;       // warps per block = interleaved angle groups
 
 template <int PJ>
 __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 {
     __shared__ BpAngle s_ang[kAngChunk];
+    __shared__ float s_red[kGroups][PJ][32];
     const int n = a.n;
     const int slot = blockIdx.z;
-    const int c = blockIdx.x * 32 + (int)threadIdx.x;
-    const int r0 = (blockIdx.y * 8 + (int)threadIdx.y) * PJ;
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const int r0 = blockIdx.y * PJ;
     const int cc = min(c, n - 1);
     const float h = 0.5f * (float)(n - 1);
     const float X = (float)cc - h;                 // exact
     const float Y0 = (float)r0 - h;                // exact
     const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
-    const float* dys = a.dy + slot * a.dy_stride;
+    const float2* dys = a.dy + slot * a.dy_stride;
 
     float acc[PJ];
 #pragma unroll
     for (int j = 0; j < PJ; ++j) acc[j] = 0.0f;
 
-    // warps whose rows all lie below the image only help stage the tables
-    const bool active = r0 < n;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
     for (int k0 = 0; k0 < a.na; k0 += kAngChunk) {
         const int cnt = min(kAngChunk, a.na - k0);
         __syncthreads();
-        for (int i = tid; i < cnt; i += 256) s_ang[i] = a.ang[k0 + i];
+        for (int i = threadIdx.x; i < cnt; i += 256) s_ang[i] = a.ang[k0 + i];
         __syncthreads();
-        for (int i = 0; active && i < cnt; ++i) {
+        for (int i = g; i < cnt; i += kGroups) {
             const BpAngle T = s_ang[i];
             float ah, al, bh, bl, s, e, s2, e2;
             mul_df(X, T.cos_hi, T.cos_lo, ah, al);
@@ -58,27 +62,31 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
             int bi;
             float frac;
             split_int_frac(s2, (al + bl) + (e + e2), bi, frac);
-            const float* row = dys + (size_t)(k0 + i) * a.Pb + bi;
-            const float m = T.m, m2 = T.m2, mm = T.m - T.m2;
+            const float2* row = dys + (size_t)(k0 + i) * a.Pb + bi;
+            const float m = T.m, om = 1.0f - T.m;
 #pragma unroll
             for (int j = 0; j < PJ; ++j) {
                 const float beta = fmaf((float)j, T.sin_hi, frac);
                 int fi;
                 const float fb = floor_magic(beta, fi);
                 const float d = beta - fb;
-                const float w0 = fmaxf(0.0f, fmaf(-d, m2, m));
-                const float w1 = fmaxf(0.0f, fmaf(d, m2, mm));
-                const float y0 = __ldg(row + fi), y1 = __ldg(row + fi + 1);
-                acc[j] = fmaf(w0, y0, fmaf(w1, y1, acc[j]));
+                const float h0 = __saturatef(fmaf(-d, m, 1.0f));
+                const float h1 = __saturatef(fmaf(d, m, om));
+                const float2 yy = __ldg(row + fi);
+                acc[j] = fmaf(h0, yy.x, fmaf(h1, yy.y, acc[j]));
             }
         }
     }
-    if (c < n) {
+    // fixed-order sum of the eight angle groups
 #pragma unroll
-        for (int j = 0; j < PJ; ++j) {
-            const int r = r0 + j;
-            if (r < n) a.out[(size_t)slot * n * n + (size_t)r * n + c] = acc[j];
-        }
+    for (int j = 0; j < PJ; ++j) s_red[g][j][lane] = acc[j];
+    __syncthreads();
+    for (int j = g; j < PJ; j += kGroups) {
+        float v = 0.0f;
+#pragma unroll
+        for (int q = 0; q < kGroups; ++q) v += s_red[q][j][lane];
+        const int r = r0 + j;
+        if (c < n && r < n) a.out[(size_t)slot * n * n + (size_t)r * n + c] = v;
     }
 }
 
@@ -86,12 +94,11 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 
 cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s)
 {
-    const int rows_per_block = 8 * a.pj;
-    const dim3 grid((a.n + 31) / 32, (a.n + rows_per_block - 1) / rows_per_block, a.n_slots);
-    const dim3 block(32, 8);
+    const dim3 grid((a.n + 31) / 32, (a.n + a.pj - 1) / a.pj, a.n_slots);
     switch (a.pj) {
-    case 4: k_backproject<4><<<grid, block, 0, s>>>(a); break;
-    case 8: k_backproject<8><<<grid, block, 0, s>>>(a); break;
+    case 4: k_backproject<4><<<grid, 256, 0, s>>>(a); break;
+    case 8: k_backproject<8><<<grid, 256, 0, s>>>(a); break;
+    case 16: k_backproject<16><<<grid, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

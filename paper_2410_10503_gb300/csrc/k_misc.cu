@@ -23,11 +23,17 @@ __global__ void k_draw_gates(uint64_t seed, uint32_t stream, unsigned long long*
     if (kctr && threadIdx.x == 0) *kctr = (unsigned long long)(k0 + (uint64_t)count);
 }
 
-__global__ void k_pad_sino(const float* __restrict__ y, float* dy, int na, int nb, int Pb, int Gb)
+// dy pairs (m_k y[b], m_k y[b+1]) of one sinogram; y[nb] = 0
+__global__ void k_pad_sino(const float* __restrict__ y, float2* dy, const BpAngle* ang, int na,
+                           int nb, int Pb, int Gb)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x - 1;
     const int k = blockIdx.y;
-    if (b < nb) dy[(size_t)k * Pb + Gb + b] = y[(size_t)k * nb + b];
+    if (b >= nb) return;
+    const float m = ang[k].m;
+    const float v0 = (b >= 0) ? m * y[(size_t)k * nb + b] : 0.0f;
+    const float v1 = (b + 1 < nb) ? m * y[(size_t)k * nb + b + 1] : 0.0f;
+    dy[(size_t)k * Pb + Gb + b] = make_float2(v0, v1);
 }
 
 constexpr int kRedThreads = 256;
@@ -119,11 +125,11 @@ cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long
     return cudaGetLastError();
 }
 
-cudaError_t launch_pad_sino(const float* y, float* dy, int na, int nb, int Pb, int Gb,
-                            cudaStream_t s)
+cudaError_t launch_pad_sino(const float* y, float2* dy, const BpAngle* ang, int na, int nb,
+                            int Pb, int Gb, cudaStream_t s)
 {
-    const dim3 grid((nb + 255) / 256, na);
-    k_pad_sino<<<grid, 256, 0, s>>>(y, dy, na, nb, Pb, Gb);
+    const dim3 grid((nb + 1 + 255) / 256, na);
+    k_pad_sino<<<grid, 256, 0, s>>>(y, dy, ang, na, nb, Pb, Gb);
     return cudaGetLastError();
 }
 

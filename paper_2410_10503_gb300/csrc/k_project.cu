@@ -2,13 +2,25 @@
 // Algorithm 1 step (ii) fused into its epilogue (arXiv 2410.10503, Sec. II-A
 // and Algorithm 1: y_i^{k+1} = prox_{sigma f_i^*}(y_i^k + sigma A_i x^{k+1})).
 //
-// Each block owns up to 256*RPT rays that share a driving axis and streams
-// the whole warped image through shared memory in chunks of `lc` lines:
-// one bulk TMA copy (cp.async.bulk) per chunk, two stages, mbarrier
-// completion.  Every ray then samples the chunk's lines from shared memory.
-// Sample positions are carried as an integer plus a float fraction relative
-// to the chunk's first line (float-pair base per ray and chunk), so the
-// interpolation weights are exact to ~1e-6 px whatever the image size.
+// Rays are processed in warp-wide groups of up to 32 consecutive bins of one
+// angle.  Work items are ranges of groups that share a driving axis, cut on
+// the host so that every item has the same number of samples; one block per
+// SM takes `ipb` consecutive items and streams the whole warped image through
+// shared memory for each, in chunks of LC lines.  One producer warp issues a
+// bulk TMA copy (cp.async.bulk) per chunk into a ring of kStages buffers; the
+// consumer warps wait on the chunk's "full" mbarrier and release it through
+// its "empty" mbarrier, so warps drift by up to kStages - 1 chunks instead of
+// meeting at a block barrier every chunk.
+//
+// A group visits only the chunks its rays cross.  In interior chunks (every
+// lane's ray crosses all LC lines) a sample is an FMA for the position, one
+// round-down add whose bits give both floor and shared address, one 8-byte
+// shared load of the (w, next - w) pair and one FMA; in the few edge chunks
+// the position is clamped into the zero guard cells instead of predicating
+// lanes.  A ray's position is carried as an integer plus a float fraction:
+// computed in float-pair arithmetic at its first line, advanced between
+// chunks by the angle's exact integer/fraction split of LC * t, and stepped
+// by j * t inside a chunk, so interpolation weights stay exact to ~1e-6 px.
 #include "mc_kernels.h"
 
 namespace mcg {
@@ -24,6 +36,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
@@ -63,195 +80,271 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up
-constexpr int kThreads = 256;
+constexpr int kConsumers = 24;               // consumer warps per block
+constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
+constexpr int kBlock = kThreads + 32;        // plus one producer warp
+constexpr int kStages = 5;
 
 __device__ __forceinline__ int gate_of(const GateSel& s, int slot)
 {
     return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
 }
 
-template <int RPT>
-__global__ void __launch_bounds__(kThreads) k_forward(FwdArgs a)
+__device__ __forceinline__ float2 lds64(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// Samples of one ray over the LC lines of a staged chunk.  The magic
+// constant of line j is kMagic + j * P: adding it with round-down leaves
+// floor(w) + j * P in the low mantissa bits, so the shared address of the pair
+// is one shift-add away and the fraction needs one more subtraction.  CLAMP
+// confines positions to [-ui, P - 2 - ui], i.e. into the zero guard cells,
+// and skips lines j >= lines of a short last chunk (warp-uniform).
+template <int LC, bool CLAMP>
+__device__ __forceinline__ float sample_lines(uint32_t ray_base, float fr, float t, const float* mj,
+                                              float wlo, float whi, int lines, float acc)
+{
+#pragma unroll
+    for (int j = 0; j < LC; ++j) {
+        if (CLAMP && j >= lines) break;
+        float w = fmaf(-(float)j, t, fr);
+        if (CLAMP) w = fminf(fmaxf(w, wlo), whi);
+        const float t1 = __fadd_rd(w, mj[j]);
+        const float f = w - (t1 - mj[j]);
+        const float2 v = lds64(ray_base + ((uint32_t)__float_as_int(t1) << 3));
+        acc += fmaf(f, v.y, v.x);
+    }
+    return acc;
+}
+
+// Per-warp, per-slot group description kept in shared memory.
+struct GroupState {
+    float t, step_frac;
+    int step_int, k;
+    int c_lo, c_hi, in_lo, in_hi;     // chunk range and interior chunk range
+};
+
+template <int RPT, int LC>
+__global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-    int* s_flag = reinterpret_cast<int*>(smem + 16);
-    float* stage0 = reinterpret_cast<float*>(smem + 128);
-    const size_t stage_floats = (size_t)a.lc * a.P;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kStages;
+    int* s_flag = reinterpret_cast<int*>(smem + 96);
+    GroupState* s_grp = reinterpret_cast<GroupState*>(smem + 128);          // [kConsumers][RPT]
+    float2* stage0 = reinterpret_cast<float2*>(smem + 128 + sizeof(GroupState) * kConsumers * RPT);
+    const size_t stage_pairs = (size_t)LC * a.P;
 
-    const RayItem item = a.items[blockIdx.x];
     const int slot = blockIdx.y;
-    const int gate = gate_of(a.sel, slot);
-    const float* src = (item.dir ? a.lcol : a.lrow) + slot * a.layout_stride;
     const int n = a.n, nb = a.nb;
-    const float h = 0.5f * (float)(n - 1);
-    const float hb = 0.5f * (float)(nb - 1);
-    const float off = h + (float)kGuard;
+    const int nch = (n + LC - 1) / LC;
+    const int it0 = blockIdx.x * a.ipb;
+    const int n_it = min(a.ipb, a.n_items - it0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // ---- ray setup ----------------------------------------------------------
-    float pbh[RPT], pbl[RPT], th[RPT], tl[RPT], acc[RPT];
-    int lo[RPT], hi[RPT], kk[RPT], bb[RPT];
-#pragma unroll
-    for (int m = 0; m < RPT; ++m) {
-        const int rho = item.begin + m * kThreads + (int)threadIdx.x;
-        acc[m] = 0.0f;
-        lo[m] = 1; hi[m] = 0; kk[m] = -1; bb[m] = 0;
-        pbh[m] = pbl[m] = th[m] = tl[m] = 0.0f;
-        if (rho < item.end) {
-            const int o = rho / nb;
-            const int b = rho - o * nb;
-            const int k = __ldg(a.order + o);
-            const FwdAngle T = a.ang[k];
-            kk[m] = k; bb[m] = b;
-            th[m] = T.t_hi; tl[m] = T.t_lo;
-            const float B = (float)b - hb;                 // exact
-            float ph, pl, s, e;
-            mul_df(B, T.inv_hi, T.inv_lo, ph, pl);
-            two_sum(ph, off, s, e);
-            pbh[m] = s; pbl[m] = pl + e;                   // B*inv + h + guard
-            // position at line 0 is pbh + h*t; lines with a non-zero weight
-            // have u in (kGuard - 1, kGuard + n); widen by up to two lines
-            const float u0 = fmaf(h, T.t_hi, s);
-            const float t = T.t_hi;
-            if (fabsf(t) < 1e-6f) {
-                if (u0 > (float)kGuard - 2.0f && u0 < (float)(kGuard + n) + 1.0f) { lo[m] = 0; hi[m] = n - 1; }
-            } else {
-                const float e1 = (u0 - (float)(kGuard + n)) / t;
-                const float e2 = (u0 - (float)(kGuard - 1)) / t;
-                float l_lo = floorf(fminf(e1, e2)) - 1.0f;
-                float l_hi = ceilf(fmaxf(e1, e2)) + 1.0f;
-                l_lo = fmaxf(l_lo, 0.0f);
-                l_hi = fminf(l_hi, (float)(n - 1));
-                if (l_lo <= l_hi) { lo[m] = (int)l_lo; hi[m] = (int)l_hi; }
-            }
-        }
-    }
-
-    // ---- staged sweep over the image lines ---------------------------------
-    const int nch = (n + a.lc - 1) / a.lc;
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kConsumers);
+        }
         *s_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < 2 && c < nch; ++c) {
-            const int l0 = c * a.lc;
-            const int lines = min(a.lc, n - l0);
-            bulk_load(stage0 + c * stage_floats, src + (size_t)l0 * a.P,
-                      (uint32_t)(lines * a.P * sizeof(float)), &bar[c]);
-        }
-    }
-    bool ok = true;
-    for (int ch = 0; ch < nch; ++ch) {
-        const int st = ch & 1;
-        if (!mbar_wait(&bar[st], (uint32_t)((ch >> 1) & 1), kWaitLimit)) {
-            ok = false;
-            *s_flag = 1;
-        }
-        __syncthreads();
-        if (*s_flag) { ok = false; break; }
-        const float* sb = stage0 + st * stage_floats;
-        const int l0 = ch * a.lc;
-        const int lines = min(a.lc, n - l0);
-        const float L0 = (float)l0 - h;                      // exact
-#pragma unroll
-        for (int m = 0; m < RPT; ++m) {
-            const int jlo = max(lo[m] - l0, 0);
-            const int jhi = min(hi[m] - l0, lines - 1);
-            if (jlo > jhi) continue;
-            float qh, ql, s, e;
-            mul_df(L0, th[m], tl[m], qh, ql);
-            two_sum(pbh[m], -qh, s, e);
-            int ui;
-            float frac;
-            split_int_frac(s, (pbl[m] - ql) + e, ui, frac);
-            const float* base = sb + ui;
-            const float t = th[m];
-            float a_m = acc[m];
-            float jf = (float)jlo;
-            for (int j = jlo; j <= jhi; ++j, jf += 1.0f) {
-                const float w = fmaf(-jf, t, frac);
-                int fi;
-                const float fl = floor_magic(w, fi);
-                const float f = w - fl;
-                const float* q = base + j * a.P + fi;
-#ifdef MC_CHECKED
-                const long off_q = (long)(q - sb);
-                if (off_q < (long)j * a.P || off_q + 1 >= (long)(j + 1) * a.P) {
-                    atomicExch(a.err, kErrBounds);
-                    continue;
+
+    // ---- producer warp: fill the ring, item after item ----------------------
+    if (warp == kConsumers) {
+        if (lane == 0) {
+            for (int g = 0; g < n_it * nch; ++g) {
+                const int it = g / nch, c = g - it * nch;
+                const float2* src = (a.items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
+                const int st = g % kStages;
+                if (g >= kStages &&
+                    !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), kWaitLimit)) {
+                    atomicExch(s_flag, 1);
+                    atomicExch(a.err, kErrTimeout);
+                    break;
                 }
-#endif
-                const float v0 = q[0], v1 = q[1];
-                a_m += fmaf(f, v1 - v0, v0);
+                if (*(volatile int*)s_flag) break;
+                const int l0 = c * LC;
+                const int lines = min(LC, n - l0);
+                bulk_load(stage0 + st * stage_pairs, src + (size_t)l0 * a.P,
+                          (uint32_t)(lines * a.P * sizeof(float2)), &full[st]);
             }
-            acc[m] = a_m;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0 && ch + 2 < nch) {
-            const int l2 = (ch + 2) * a.lc;
-            const int lines2 = min(a.lc, n - l2);
-            bulk_load(stage0 + st * stage_floats, src + (size_t)l2 * a.P,
-                      (uint32_t)(lines2 * a.P * sizeof(float)), &bar[st]);
-        }
-    }
-    if (!ok) {
-        if (threadIdx.x == 0) {
-            atomicExch(a.err, kErrTimeout);
-            // give copies still in flight a bounded chance to land
-            for (int c = 0; c < 2; ++c) mbar_wait(&bar[c], 0u, 1u << 16);
         }
         return;
     }
 
-    // ---- epilogue -------------------------------------------------------------
+    // ---- consumers ------------------------------------------------------------
+    const int gate = gate_of(a.sel, slot);
+    const float h = 0.5f * (float)(n - 1);
+    const float hb = 0.5f * (float)(nb - 1);
+    const float off = h + (float)kGuard;
+    float mj[LC];
 #pragma unroll
-    for (int m = 0; m < RPT; ++m) {
-        if (kk[m] < 0) continue;
-        const int k = kk[m], b = bb[m];
-        const float val = a.ang[k].delta * acc[m];
-        const size_t idx = (size_t)k * nb + b;
-        if (a.mode == 0) {
-            a.out[(size_t)slot * a.na * nb + idx] = val;
-        } else {
-            const size_t gi = (size_t)gate * a.na * nb + idx;
-            const float yo = a.y[gi];
-            const float yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
-            a.y[gi] = yn;
-            a.dy[slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b] = yn - yo;
+    for (int j = 0; j < LC; ++j) mj[j] = kMagic + (float)(j * a.P);
+    const uint32_t magic_off = (uint32_t)kMagicBits << 3;
+    GroupState* my = s_grp + warp * RPT;
+
+    for (int it = 0; it < n_it; ++it) {
+        const RayItem item = a.items[it0 + it];
+        // this warp's groups: item.begin + warp + m * kConsumers
+        const int ns = max(0, min(RPT, (item.end - item.begin - warp + kConsumers - 1) / kConsumers));
+        float frac[RPT], acc[RPT];
+        int ui[RPT];
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            acc[m] = 0.0f; frac[m] = 0.0f; ui[m] = 0;
+            if (m >= ns) continue;
+            const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+            const int k = grp.x;
+            const int b = min(grp.y + lane, nb - 1);           // idle lanes repeat the last ray
+            const FwdAngle T = a.ang[k];
+            const float B = (float)b - hb;                      // exact
+            const float t = T.t_hi;
+            // lines with a non-zero weight have u in (kGuard - 1, kGuard + n);
+            // widen by up to two lines (guards absorb the extra samples)
+            const float u0 = fmaf(h, t, fmaf(B, T.inv_hi, off));
+            int lo = n, hi = -1;
+            if (fabsf(t) < 1e-6f) {
+                if (u0 > (float)kGuard - 2.0f && u0 < (float)(kGuard + n) + 1.0f) { lo = 0; hi = n - 1; }
+            } else {
+                const float e1 = (u0 - (float)(kGuard + n)) / t;
+                const float e3 = (u0 - (float)(kGuard - 1)) / t;
+                const float l_lo = fmaxf(floorf(fminf(e1, e3)) - 1.0f, 0.0f);
+                const float l_hi = fminf(ceilf(fmaxf(e1, e3)) + 1.0f, (float)(n - 1));
+                if (l_lo <= l_hi) { lo = (int)l_lo; hi = (int)l_hi; }
+            }
+            // group chunk range (union) and interior (every lane covers all LC lines)
+            const int lo_min = __reduce_min_sync(0xffffffffu, lo);
+            const int hi_max = __reduce_max_sync(0xffffffffu, hi);
+            const int lo_max = __reduce_max_sync(0xffffffffu, lo);
+            const int hi_min = __reduce_min_sync(0xffffffffu, hi);
+            const int c_lo = (hi_max >= lo_min) ? lo_min / LC : nch;
+            const int c_hi = (hi_max >= lo_min) ? hi_max / LC : -1;
+            const int in_lo = (lo_max + LC - 1) / LC;
+            const int in_hi = (hi_min + 1) / LC - 1;
+            if (lane == 0) {
+                GroupState gs;
+                gs.t = t; gs.step_frac = T.step_frac; gs.step_int = T.step_int; gs.k = k;
+                gs.c_lo = c_lo; gs.c_hi = c_hi;
+                gs.in_lo = (hi_min >= lo_max && in_lo <= in_hi) ? in_lo : 1;
+                gs.in_hi = (hi_min >= lo_max && in_lo <= in_hi) ? in_hi : 0;
+                my[m] = gs;
+            }
+            // position at the group's first line L = c_lo * LC:
+            // u(L) = B inv - (L - h) t + h + guard, in float pairs
+            const float L = (float)(min(c_lo, nch - 1) * LC) - h;   // exact
+            float ph, pl, qh, ql, s, e, s2, e2;
+            mul_df(B, T.inv_hi, T.inv_lo, ph, pl);
+            mul_df(-L, T.t_hi, T.t_lo, qh, ql);
+            two_sum(ph, qh, s, e);
+            two_sum(s, off, s2, e2);
+            split_int_frac(s2, (pl + ql) + (e + e2), ui[m], frac[m]);
         }
+        __syncwarp();
+
+        for (int ch = 0; ch < nch; ++ch) {
+            const int g = it * nch + ch;
+            const int st = g % kStages;
+            if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), kWaitLimit) ||
+                *(volatile int*)s_flag) {
+                atomicExch(s_flag, 1);
+                atomicExch(a.err, kErrTimeout);
+                return;
+            }
+            const uint32_t sb = smem_u32(stage0 + st * stage_pairs) - magic_off;
+            const int lines = min(LC, n - ch * LC);
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (m >= ns) break;
+                const GroupState gs = my[m];
+                if (ch < gs.c_lo || ch > gs.c_hi) continue;
+                const uint32_t rb = sb + ((uint32_t)ui[m] << 3);
+                if (ch >= gs.in_lo && ch <= gs.in_hi) {
+                    acc[m] = sample_lines<LC, false>(rb, frac[m], gs.t, mj, 0.0f, 0.0f, LC, acc[m]);
+                } else {
+                    const float wlo = -(float)ui[m], whi = (float)(a.P - 2 - ui[m]);
+                    acc[m] = sample_lines<LC, true>(rb, frac[m], gs.t, mj, wlo, whi, lines, acc[m]);
+                }
+                // advance to the first line of the next chunk: u -= LC * t
+                float nf = frac[m] - gs.step_frac;
+                int nu = ui[m] - gs.step_int;
+                if (nf < 0.0f) { nf += 1.0f; nu -= 1; }
+                frac[m] = nf;
+                ui[m] = nu;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
+        }
+
+        // ---- epilogue ---------------------------------------------------------
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+            if (m >= ns) break;
+            const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+            const int k = grp.x, b = grp.y + lane;
+            if (b >= nb) continue;
+            const float delta = __ldg(&a.ang[k].delta);
+            const float val = delta * acc[m];
+            const size_t idx = (size_t)k * nb + b;
+            if (a.mode == 0) {
+                a.out[(size_t)slot * a.na * nb + idx] = val;
+            } else {
+                const size_t gi = (size_t)gate * a.na * nb + idx;
+                const float yo = a.y[gi];
+                const float yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
+                a.y[gi] = yn;
+                // dy pairs scaled by the angle's step: (m dy[b], m dy[b+1])
+                const float v = delta * (yn - yo);
+                float* dyp = reinterpret_cast<float*>(a.dy + slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b);
+                dyp[0] = v;
+                dyp[-1] = v;
+            }
+        }
+        __syncwarp();
     }
 }
 
 }  // namespace
 
-size_t forward_smem_bytes(int lc, int P) { return 128 + 2 * (size_t)lc * P * sizeof(float); }
+int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
+
+size_t forward_smem_bytes(int lc, int P)
+{
+    return 128 + sizeof(GroupState) * kConsumers * 8 + kStages * (size_t)lc * P * sizeof(float2);
+}
+
+#define MC_FWD_INSTANCES(X) \
+    X(2, 2) X(4, 2) X(8, 2) X(2, 4) X(4, 4) X(8, 4) X(2, 8) X(4, 8) X(8, 8)
 
 cudaError_t forward_prepare(int max_smem)
 {
-    cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_forward<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_forward<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_forward<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    if ((e = cudaFuncSetAttribute(k_forward<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem))) return e;
-    return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+#define MC_SET_ATTR(R, L)                                                                   \
+    if (e == cudaSuccess)                                                                  \
+        e = cudaFuncSetAttribute(k_forward<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 max_smem);
+    MC_FWD_INSTANCES(MC_SET_ATTR)
+#undef MC_SET_ATTR
+    return e;
 }
 
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
 {
-    const dim3 grid(a.n_items, a.n_slots);
+    const dim3 grid((a.n_items + a.ipb - 1) / a.ipb, a.n_slots);
     const size_t smem = forward_smem_bytes(a.lc, a.P);
-    switch (a.rpt) {
-    case 1: k_forward<1><<<grid, kThreads, smem, s>>>(a); break;
-    case 2: k_forward<2><<<grid, kThreads, smem, s>>>(a); break;
-    case 4: k_forward<4><<<grid, kThreads, smem, s>>>(a); break;
-    case 8: k_forward<8><<<grid, kThreads, smem, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
+#define MC_LAUNCH(R, L)                                              \
+    if (a.rpt == R && a.lc == L) {                                   \
+        k_forward<R, L><<<grid, kBlock, smem, s>>>(a);               \
+        return cudaGetLastError();                                   \
     }
-    return cudaGetLastError();
+    MC_FWD_INSTANCES(MC_LAUNCH)
+#undef MC_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mcg

@@ -33,11 +33,59 @@ __device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
     return acc;
 }
 
-// Tile of 32 x 32 output pixels per block (32 x 8 threads, 4 rows each).
-template <bool LAYOUT>
-__global__ void __launch_bounds__(256) k_warp(WarpArgs a)
+// Layout mode: a 32 x 32 tile of w = D x plus a one-pixel halo (33 x 33) is
+// computed into shared memory, then written as (w, next - w) pairs into the
+// row-line and the column-line layouts (the halo supplies "next"; pixels past
+// the image edge are zero).  The pair just before each line's data,
+// (0, w[0]), is written by the tile that holds position 0.
+__global__ void __launch_bounds__(256) k_warp_layouts(WarpArgs a)
 {
-    __shared__ float tile[32][33];
+    __shared__ float w_s[33][34];
+    const int slot = blockIdx.z;
+    const int gate = gate_of(a.sel, slot);
+    const int n = a.n;
+    const RigidGate* rg = a.rigid ? a.rigid + gate : nullptr;
+    const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
+    const int r_t = blockIdx.y * 32, c_t = blockIdx.x * 32;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int idx = tid; idx < 33 * 33; idx += 256) {
+        const int rr = idx / 33, cc = idx - rr * 33;
+        const int r = r_t + rr, c = c_t + cc;
+        float w = 0.0f;
+        if (r < n && c < n)
+            w = a.identity ? __ldg(a.x + (size_t)r * n + c) : warp_sample(a.x, n, rg, field, r, c);
+        w_s[rr][cc] = w;
+    }
+    __syncthreads();
+    float2* lrow = a.lrow + slot * a.layout_stride;
+    float2* lcol = a.lcol + slot * a.layout_stride;
+    // row lines: lanes along the columns of one row
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int rr = threadIdx.y + 8 * i, cc = threadIdx.x;
+        const int r = r_t + rr, c = c_t + cc;
+        if (r < n && c < n) {
+            const float v = w_s[rr][cc];
+            lrow[(size_t)r * a.P + kGuard + c] = make_float2(v, w_s[rr][cc + 1] - v);
+            if (c == 0) lrow[(size_t)r * a.P + kGuard - 1] = make_float2(0.0f, v);
+        }
+    }
+    // column lines: lanes along the rows of one column
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int cc = threadIdx.y + 8 * i, rr = threadIdx.x;
+        const int r = r_t + rr, c = c_t + cc;
+        if (r < n && c < n) {
+            const float v = w_s[rr][cc];
+            lcol[(size_t)c * a.P + kGuard + r] = make_float2(v, w_s[rr + 1][cc] - v);
+            if (r == 0) lcol[(size_t)c * a.P + kGuard - 1] = make_float2(0.0f, v);
+        }
+    }
+}
+
+// Plain mode: w = D x as an n x n image.
+__global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
+{
     const int slot = blockIdx.z;
     const int gate = gate_of(a.sel, slot);
     const int n = a.n;
@@ -46,46 +94,24 @@ __global__ void __launch_bounds__(256) k_warp(WarpArgs a)
     const int c = blockIdx.x * 32 + threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int tr = threadIdx.y + 8 * i;
-        const int r = blockIdx.y * 32 + tr;
-        float w = 0.0f;
+        const int r = blockIdx.y * 32 + threadIdx.y + 8 * i;
         if (r < n && c < n)
-            w = a.identity ? __ldg(a.x + (size_t)r * n + c)
-                           : warp_sample(a.x, n, rg, field, r, c);
-        if (LAYOUT) {
-            tile[tr][threadIdx.x] = w;
-            if (r < n && c < n)
-                a.lrow[slot * a.layout_stride + (size_t)r * a.P + kGuard + c] = w;
-        } else if (r < n && c < n) {
-            a.out[(size_t)slot * n * n + (size_t)r * n + c] = w;
-        }
-    }
-    if (LAYOUT) {
-        __syncthreads();
-        // column layout: line = image column, position = row
-        const int rr = blockIdx.y * 32 + threadIdx.x;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int tc = threadIdx.y + 8 * i;
-            const int cc = blockIdx.x * 32 + tc;
-            if (cc < n && rr < n)
-                a.lcol[slot * a.layout_stride + (size_t)cc * a.P + kGuard + rr] =
-                    tile[threadIdx.x][tc];
-        }
+            a.out[(size_t)slot * n * n + (size_t)r * n + c] =
+                a.identity ? __ldg(a.x + (size_t)r * n + c) : warp_sample(a.x, n, rg, field, r, c);
     }
 }
 
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
 {
     dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 8);
-    k_warp<true><<<grid, block, 0, s>>>(a);
+    k_warp_layouts<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_warp_plain(const WarpArgs& a, cudaStream_t s)
 {
     dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 8);
-    k_warp<false><<<grid, block, 0, s>>>(a);
+    k_warp_plain<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -72,9 +72,9 @@ struct mc_ctx {
     // geometry
     FwdAngle* d_fang = nullptr;
     BpAngle* d_bang = nullptr;
-    int* d_order = nullptr;
+    int2* d_groups = nullptr;
     RayItem* d_items = nullptr;
-    int n_items = 0, rpt = 1, lc = 1, P = 0, Gb = 0, Pb = 0, pj = 4;
+    int n_items = 0, ipb = 1, rpt = 1, lc = 1, P = 0, Gb = 0, Pb = 0, pj = 4;
     size_t layout_stride = 0, dy_stride = 0;
 
     // motion and D_i^T
@@ -96,9 +96,9 @@ struct mc_ctx {
     double alpha = 0;
 
     // scratch per gate slot
-    float* d_lrow = nullptr;
-    float* d_lcol = nullptr;
-    float* d_dy = nullptr;
+    float2* d_lrow = nullptr;
+    float2* d_lcol = nullptr;
+    float2* d_dy = nullptr;
     float* d_b = nullptr;
     float* d_sinoN = nullptr;
     float* d_img[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -298,8 +298,8 @@ FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
 {
     FwdArgs a{};
     a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
-    a.ang = c->d_fang; a.order = c->d_order; a.items = c->d_items; a.n_items = c->n_items;
-    a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
+    a.ang = c->d_fang; a.groups = c->d_groups; a.items = c->d_items; a.n_items = c->n_items;
+    a.ipb = c->ipb; a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
     a.sel = sel; a.n_slots = n_slots;
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
     a.err = c->d_err;
@@ -334,9 +334,9 @@ mc_status pad_sinos(mc_ctx* c, const float* y, int n_slots)
 {
     for (int s = 0; s < n_slots; ++s) {
         const float* ys = y + (size_t)s * c->na * c->nb;
-        float* dys = c->d_dy + (size_t)s * c->dy_stride;
+        float2* dys = c->d_dy + (size_t)s * c->dy_stride;
         TRY(launch(c, C_MISC, "pad", [&] {
-            return launch_pad_sino(ys, dys, c->na, c->nb, c->Pb, c->Gb, c->stream);
+            return launch_pad_sino(ys, dys, c->d_bang, c->na, c->nb, c->Pb, c->Gb, c->stream);
         }));
     }
     return MC_OK;
@@ -542,9 +542,30 @@ mc_status check_gate(mc_ctx* c, int gate)
 }
 
 // ---- creation ---------------------------------------------------------------
+// Number of lines on which ray (k, b) has a non-zero interpolation weight:
+// positions u(l) = (b - hb) inv - (l - h) t + h in (-1, n), l = 0..n-1.
+long long ray_samples(int n, double hb, double inv, double t, int b)
+{
+    const double h = 0.5 * (n - 1);
+    const double a = (b - hb) * inv + h * t + h;        // u(0); u(l) = a - l t
+    if (std::fabs(t) < 1e-12) return (a > -1.0 && a < n) ? n : 0;
+    double l1 = (a - n) / t, l2 = (a + 1.0) / t;       // u = n and u = -1
+    if (l1 > l2) std::swap(l1, l2);
+    const long long lo = std::max<long long>(0, (long long)std::floor(l1) + 1);
+    const long long hi = std::min<long long>(n - 1, (long long)std::ceil(l2) - 1);
+    return hi >= lo ? hi - lo + 1 : 0;
+}
+
 mc_status build_tables(mc_ctx* c)
 {
     const int n = c->n, na = c->na, nb = c->nb;
+    // line layouts: kGuard zero pairs in front, >= 4 behind, 16-byte pitch;
+    // chunks of lc in {8, 4, 2} lines per ring stage (five stages of at most
+    // ~34 KB in the one block per SM)
+    c->P = ((n + 2 * kGuard) + 3) / 4 * 4;
+    c->layout_stride = (size_t)n * c->P;
+    c->lc = 8;
+    while (c->lc > 2 && (size_t)c->lc * c->P * sizeof(float2) > 34816) c->lc >>= 1;
     std::vector<FwdAngle> fa(na);
     std::vector<BpAngle> ba(na);
     std::vector<int> order;
@@ -554,6 +575,7 @@ mc_status build_tables(mc_ctx* c)
             const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
             if ((pass == 1) == xd) order.push_back(k);
         }
+    std::vector<double> inv_k(na), t_k(na);
     int ny = 0;
     for (int k = 0; k < na; ++k) {
         const double phi = (double)k * kPi / (double)na;
@@ -562,9 +584,16 @@ mc_status build_tables(mc_ctx* c)
         if (!xd) ++ny;
         const double inv = xd ? 1.0 / sn : 1.0 / cs;
         const double t = xd ? cs / sn : sn / cs;
+        inv_k[k] = inv;
+        t_k[k] = t;
         FwdAngle f{};
         split_f(inv, f.inv_hi, f.inv_lo);
         split_f(t, f.t_hi, f.t_lo);
+        const double step = (double)c->lc * t;
+        const double si = std::floor(step);
+        f.step_int = (int)si;
+        f.step_frac = (float)(step - si);
+        if (f.step_frac >= 1.0f) { f.step_frac = 0.0f; f.step_int += 1; }
         f.delta = (float)std::fabs(inv);
         f.dir = xd ? 1 : 0;
         fa[k] = f;
@@ -575,41 +604,80 @@ mc_status build_tables(mc_ctx* c)
         b.m2 = (float)(inv * inv);
         ba[k] = b;
     }
-    // ray items: rows-driven rays first, then columns-driven; blocks of 256*rpt
-    const long long rays_y = (long long)ny * nb, rays_all = (long long)na * nb;
-    int rpt = 8;
-    while (rpt > 1 && rays_all / (256LL * rpt) < c->sms) rpt >>= 1;
-    c->rpt = rpt;
-    std::vector<RayItem> items;
-    const long long blk = 256LL * rpt;
-    for (int cls = 0; cls < 2; ++cls) {
-        const long long b0 = cls == 0 ? 0 : rays_y, b1 = cls == 0 ? rays_y : rays_all;
-        for (long long s = b0; s < b1; s += blk)
-            items.push_back(RayItem{(int)s, (int)std::min(b1, s + blk), cls, 0});
+    // forward ray groups: up to 32 consecutive bins of one angle, rows-driven
+    // angles first; work items cut each axis class into group ranges with
+    // equal sample counts; one block per SM takes ipb consecutive items
+    const double hb = 0.5 * (nb - 1);
+    const int gpa = (nb + 31) / 32;                        // groups per angle
+    std::vector<int2> groups;
+    std::vector<long long> cum(1, 0);
+    groups.reserve((size_t)na * gpa);
+    cum.reserve((size_t)na * gpa + 1);
+    for (int o = 0; o < na; ++o) {
+        const int k = order[o];
+        for (int g = 0; g < gpa; ++g) {
+            long long w = 64;                              // per-group setup cost
+            for (int b = g * 32; b < std::min(nb, g * 32 + 32); ++b)
+                w += ray_samples(n, hb, inv_k[k], t_k[k], b);
+            groups.push_back(make_int2(k, g * 32));
+            cum.push_back(cum.back() + w);
+        }
     }
+    const long long g_y = (long long)ny * gpa, g_all = (long long)na * gpa;
+    std::vector<RayItem> items;
+    int rpt = 2, ipb = 1;
+    for (;; ++ipb) {
+        const int target = ipb * c->sms;
+        items.clear();
+        long long max_groups = 0;
+        const double total = (double)cum[g_all];
+        for (int cls = 0; cls < 2; ++cls) {
+            const long long b0 = cls == 0 ? 0 : g_y, b1 = cls == 0 ? g_y : g_all;
+            if (b1 <= b0) continue;
+            const double w = (double)(cum[b1] - cum[b0]);
+            const int cnt = std::max(1, (int)std::lround(target * w / total));
+            long long s = b0;
+            for (int i = 1; i <= cnt && s < b1; ++i) {
+                const long long goal = cum[b0] + (long long)std::llround(w * i / cnt);
+                long long e = std::lower_bound(cum.begin() + s + 1, cum.begin() + b1 + 1, goal) - cum.begin();
+                e = std::min(std::max(e, s + 1), b1);
+                if (i == cnt) e = b1;
+                items.push_back(RayItem{(int)s, (int)e, cls, 0});
+                max_groups = std::max(max_groups, e - s);
+                s = e;
+            }
+        }
+        rpt = 2;
+        while (rpt < 8 && forward_groups_per_block(rpt) < max_groups) rpt <<= 1;
+        if (forward_groups_per_block(rpt) >= max_groups) break;
+    }
+    c->ipb = ipb;
+    c->rpt = rpt;
     c->n_items = (int)items.size();
     TRY(dalloc(c, &c->d_fang, na));
     TRY(dalloc(c, &c->d_bang, na));
-    TRY(dalloc(c, &c->d_order, na));
+    TRY(dalloc(c, &c->d_groups, groups.size()));
     TRY(dalloc(c, &c->d_items, items.size()));
     CK(cudaMemcpyAsync(c->d_fang, fa.data(), na * sizeof(FwdAngle), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_bang, ba.data(), na * sizeof(BpAngle), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_order, order.data(), na * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_groups, groups.data(), groups.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                       c->stream));
     CK(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));   // host vectors go out of scope
-    // line layouts: guard kGuard in front, >= 4 zero cells behind, 16-byte pitch
-    c->P = ((n + 2 * kGuard) + 3) / 4 * 4;
-    c->layout_stride = (size_t)n * c->P;
-    int lc = (int)(40960 / ((size_t)c->P * sizeof(float)));
-    c->lc = std::max(1, std::min(32, lc));
+    // backprojection tiles: 32 columns x pj rows per block of 8 warps; the
+    // largest pj that still gives about 24 warps per SM
+    c->pj = 4;
+    for (int pj : {16, 8}) {
+        const long long warps = 8LL * ((n + 31) / 32) * ((n + pj - 1) / pj);
+        if (warps >= 24LL * c->sms) { c->pj = pj; break; }
+    }
     // dual increment layout: guards wide enough for every pixel's two bins
-    const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
-    const int pj_max = 8;
+    const double h = 0.5 * (n - 1);
+    const int pj_max = 16;
     c->Gb = std::max(2, (int)std::ceil(std::sqrt(2.0) * (h + pj_max + 1) - hb) + 2);
     c->Pb = (nb + 2 * c->Gb + 2 + 3) / 4 * 4;
     c->dy_stride = (size_t)na * c->Pb;
-    c->pj = 4;
     return MC_OK;
 }
 

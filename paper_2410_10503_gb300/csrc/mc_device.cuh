@@ -2,14 +2,17 @@
 //
 // HBM layouts (per gate slot):
 //   line layouts  Two copies of the warped image w = D_i x, each as n lines
-//                 of pitch P floats with kGuard zero cells before the data:
+//                 of pitch P float2 "pairs" (w[p], w[p+1] - w[p]) with kGuard
+//                 zero cells before the data:
 //                 ROWS  line l = image row l    (used by rows-driven angles),
 //                 COLS  line l = image column l (used by columns-driven angles).
-//                 Zero guards make the Joseph interpolation branch-free.
-//   dy            Dual increment y_i^{k+1} - y_i^k as n_angles lines of pitch
-//                 Pb floats with Gb zero bins before the data, so that the
-//                 pixel-driven gather reads both interpolation bins without
-//                 bounds checks.
+//                 One 8-byte load gives both interpolation taps, and the zero
+//                 guards make the Joseph interpolation branch-free.
+//   dy            Dual increment of one gate as n_angles lines of pitch Pb
+//                 float2 pairs (m_k dy[b], m_k dy[b+1]), pre-scaled by the
+//                 angle's sample step m_k, with Gb zero bins before the data,
+//                 so that the pixel-driven gather reads both of its bins with
+//                 one 8-byte load and no bounds checks.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -20,15 +23,19 @@ constexpr int kGuard = 4;                 // zero cells before each image line
 constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 
-// Joseph sampling table of one angle (host float64 -> float32 pairs).
+// Joseph sampling table of one angle (host float64 -> float32).
 // Along a line l of the driving axis the ray (k, b) sits at the padded
-// position u = (b - hb) * inv - (l - h) * t + h + kGuard.
+// position u = (b - hb) * inv - (l - h) * t + h + kGuard.  Between the first
+// lines of two consecutive staged chunks u moves by -lc * t, split exactly
+// into step_int + step_frac (step_frac in [0, 1)).
 struct FwdAngle {
-    float inv_hi, inv_lo;   // 1/sin (columns-driven) or 1/cos (rows-driven)
-    float t_hi, t_lo;       // cos/sin or sin/cos
+    float t_hi;             // cos/sin or sin/cos (first 16 bytes: chunk loop)
+    float step_frac;
+    int step_int;
     float delta;            // |inv| = sample step length
+    float inv_hi, inv_lo;   // 1/sin (columns-driven) or 1/cos (rows-driven)
+    float t_lo;
     int dir;                // 1: lines are image columns, 0: image rows
-    int pad0, pad1;
 };
 
 // Pixel-driven gather table of one angle: pixel (r, c) projects to the
@@ -47,8 +54,9 @@ struct RigidGate {
     float offx_hi, offx_lo, offy_hi, offy_lo;   // tx + h, ty + h
 };
 
-// One block of forward rays: flattened ray indices [begin, end) of the
-// angle order table, all with the same driving axis.
+// One block's share of the forward rays: ray groups [begin, end) of the
+// group table, all with the same driving axis.  A ray group is up to 32
+// consecutive bins of one angle (one warp).
 struct RayItem {
     int begin, end, dir, pad;
 };

@@ -24,10 +24,10 @@ struct WarpArgs {
     int identity;              // 1: w = x (no motion; the ray transform alone)
     GateSel sel;
     int n_slots;
-    float* lrow;               // line layouts, slot stride layout_stride floats
-    float* lcol;
+    float2* lrow;              // pair line layouts, slot stride layout_stride pairs
+    float2* lcol;
     size_t layout_stride;
-    int P;                     // line pitch (floats)
+    int P;                     // line pitch (pairs)
     float* out;                // plain mode: n*n per slot
 };
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s);
@@ -67,16 +67,17 @@ cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s);
 
 // ---- K3 (+K6): Joseph forward projection ------------------------------------
 struct FwdArgs {
-    const float* lrow;
-    const float* lcol;
+    const float2* lrow;
+    const float2* lcol;
     size_t layout_stride;
     int P;
     const FwdAngle* ang;
-    const int* order;          // angle order: rows-driven first, then columns-driven
-    const RayItem* items;
+    const int2* groups;        // ray groups {angle k, first bin}, rows-driven first
+    const RayItem* items;      // group ranges
     int n_items;
-    int rpt;                   // rays per thread (1, 2, 4, 8)
-    int lc;                    // lines per staged chunk
+    int ipb;                   // items per block (one block per SM)
+    int rpt;                   // group slots per consumer warp (2, 4, 8)
+    int lc;                    // lines per staged chunk (2, 4, 8)
     int n, na, nb;
     GateSel sel;
     int n_slots;
@@ -84,7 +85,7 @@ struct FwdArgs {
     float* out;                // mode 0: slot stride na*nb
     const float* d;            // mode 1: gate stride na*nb
     float* y;
-    float* dy;                 // slot stride dy_stride, pitch Pb, guard Gb
+    float2* dy;                // pairs, slot stride dy_stride, pitch Pb, guard Gb
     size_t dy_stride;
     int Pb, Gb;
     float sigma;
@@ -92,18 +93,19 @@ struct FwdArgs {
     int* err;
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
+int forward_groups_per_block(int rpt);
 size_t forward_smem_bytes(int lc, int P);
 cudaError_t forward_prepare(int max_smem);
 
 // ---- K4: pixel-driven gather backprojection ---------------------------------
 struct BpArgs {
-    const float* dy;           // slot stride dy_stride, pitch Pb, guard Gb
+    const float2* dy;          // pairs, slot stride dy_stride, pitch Pb, guard Gb
     size_t dy_stride;
     int Pb, Gb;
     const BpAngle* ang;
     int n, na, nb;
     int n_slots;
-    int pj;                    // pixels per thread along a column (4 or 8)
+    int pj;                    // pixels per thread along a column (4, 8 or 16)
     float* out;                // slot stride n*n
 };
 cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
@@ -111,9 +113,10 @@ cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
 // ---- misc -------------------------------------------------------------------
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
                               uint64_t k0, int count, int n_gates, int* out, cudaStream_t s);
-// copy a na x nb sinogram into the padded dy layout (guards stay zero)
-cudaError_t launch_pad_sino(const float* y, float* dy, int na, int nb, int Pb, int Gb,
-                            cudaStream_t s);
+// write a na x nb sinogram into the padded, m_k-scaled pair layout of dy
+// (guards stay zero)
+cudaError_t launch_pad_sino(const float* y, float2* dy, const BpAngle* ang, int na, int nb,
+                            int Pb, int Gb, cudaStream_t s);
 // FP64 reductions, deterministic; result in out[0] (device)
 enum { kRedSumSq = 0, kRedDiffSq = 1, kRedDot = 2 };
 int reduce_parts();
