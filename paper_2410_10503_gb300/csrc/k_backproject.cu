@@ -13,24 +13,97 @@
 //
 // A block owns a tile of 32 columns x PJ rows; its 8 warps all cover that
 // tile, each for every 8th angle, and their partial sums are added in a fixed
-// order through shared memory at the end.  A thread owns PJ consecutive rows
-// of one column: per angle it forms beta of its first pixel in float-pair
-// arithmetic (integer bin + fraction) and steps the fraction by sin(phi) down
-// the column, so d is exact to ~1e-6 whatever the image size.
+// order through shared memory at the end.  Angles are processed in chunks of
+// kChunk: for each angle one bulk TMA copy brings the window of dy pairs that
+// the tile projects onto (WL pairs) into shared memory, double-buffered and
+// completed on an mbarrier, so the gathers are shared-memory loads whose lanes
+// (consecutive columns, |cos| <= 1 bin apart) rarely share a bank.  A thread
+// owns PJ consecutive rows of one column: per angle it forms beta of its first
+// pixel in float-pair arithmetic (integer bin + fraction) and steps the
+// fraction by sin(phi) down the column, two rows at a time in paired FP32
+// arithmetic, so d is exact to ~1e-6 whatever the image size.
+#include <algorithm>
+#include <cmath>
+
 #include "mc_kernels.h"
 
 namespace mcg {
 
 namespace {
 
-constexpr int kAngChunk = 256;   // angle-table entries staged in shared memory
 constexpr int kGroups = 8;       // warps per block = interleaved angle groups
+constexpr int kChunk = 32;       // angles per staged chunk
+constexpr uint32_t kWaitLimit = 1u << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit)
+{
+    const uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ float2 lds64(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// Issue the window copies of one chunk (warp 0; lane i handles angles i, i+32...).
+// Window of angle k: WL pairs of dy row k starting at ws (even, so the copy is
+// 16-byte aligned), covering every bin the tile's pixels project onto.
+__device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, int k0, int cnt, int wl,
+                                            float xmin, float xmax, float ymin, float ymax,
+                                            float2* buf, int* ws_out, uint64_t* bar)
+{
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) {
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                     "r"((uint32_t)(cnt * wl * sizeof(float2)))
+                     : "memory");
+    }
+    __syncwarp();
+    const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
+    for (int i = lane; i < cnt; i += 32) {
+        const BpAngle T = a.ang[k0 + i];
+        const float cs = T.cos_hi, sn = T.sin_hi;
+        const float b1 = fminf(xmin * cs, xmax * cs) + fminf(ymin * sn, ymax * sn) + offb;
+        int ws = ((int)floorf(b1) - 2) & ~1;
+        ws = max(0, min(ws, a.Pb - wl));
+        ws_out[i] = ws;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(buf + (size_t)i * wl)),
+            "l"(dys + (size_t)(k0 + i) * a.Pb + ws), "r"((uint32_t)(wl * sizeof(float2))), "r"(smem_u32(bar))
+            : "memory");
+    }
+}
 
 template <int PJ>
 __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 {
-    __shared__ BpAngle s_ang[kAngChunk];
-    __shared__ float s_red[kGroups][PJ][32];
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    int* s_ws = reinterpret_cast<int*>(smem + 64);                          // [2][kChunk]
+    BpAngle* s_ang = reinterpret_cast<BpAngle*>(smem + 64 + 2 * kChunk * sizeof(int));   // [2][kChunk]
+    float2* s_win = reinterpret_cast<float2*>(smem + 64 + 2 * kChunk * (sizeof(int) + sizeof(BpAngle)));
+    const int wl = a.wl;
     const int n = a.n;
     const int slot = blockIdx.z;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -42,18 +115,45 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     const float Y0 = (float)r0 - h;                // exact
     const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
     const float2* dys = a.dy + slot * a.dy_stride;
+    // tile extent in centred coordinates (columns past the image are clamped)
+    const float xmin = (float)(blockIdx.x * 32) - h, xmax = (float)min(blockIdx.x * 32 + 31, n - 1) - h;
+    const float ymin = Y0, ymax = Y0 + (float)(PJ - 1);
+    const int nck = (a.na + kChunk - 1) / kChunk;
+
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (g == 0)
+        issue_chunk(a, dys, 0, min(kChunk, a.na), wl, xmin, xmax, ymin, ymax, s_win, s_ws, &full[0]);
 
     float acc[PJ];
 #pragma unroll
     for (int j = 0; j < PJ; ++j) acc[j] = 0.0f;
 
-    for (int k0 = 0; k0 < a.na; k0 += kAngChunk) {
-        const int cnt = min(kAngChunk, a.na - k0);
+    for (int ch = 0; ch < nck; ++ch) {
+        const int buf = ch & 1;
+        const int k0 = ch * kChunk;
+        const int cnt = min(kChunk, a.na - k0);
+        // angle table of this chunk, and the next chunk's windows in flight
+        for (int i = threadIdx.x; i < cnt; i += 256) s_ang[buf * kChunk + i] = a.ang[k0 + i];
+        if (g == 0 && ch + 1 < nck)
+            issue_chunk(a, dys, k0 + kChunk, min(kChunk, a.na - k0 - kChunk), wl, xmin, xmax, ymin, ymax,
+                        s_win + (size_t)(buf ^ 1) * kChunk * wl, s_ws + (buf ^ 1) * kChunk, &full[buf ^ 1]);
         __syncthreads();
-        for (int i = threadIdx.x; i < cnt; i += 256) s_ang[i] = a.ang[k0 + i];
-        __syncthreads();
+        if (!mbar_wait(&full[buf], (uint32_t)((ch >> 1) & 1), kWaitLimit)) {
+            // a copy never landed: report, then give the other stage a bounded chance to land
+            if (threadIdx.x == 0) {
+                atomicExch(a.err, kErrTimeout);
+                mbar_wait(&full[buf ^ 1], (uint32_t)(((ch + 1) >> 1) & 1), 1u << 16);
+            }
+            return;
+        }
+        const uint32_t wbase = smem_u32(s_win + (size_t)buf * kChunk * wl) - ((uint32_t)kMagicBits << 3);
         for (int i = g; i < cnt; i += kGroups) {
-            const BpAngle T = s_ang[i];
+            const BpAngle T = s_ang[buf * kChunk + i];
             float ah, al, bh, bl, s, e, s2, e2;
             mul_df(X, T.cos_hi, T.cos_lo, ah, al);
             mul_df(Y0, T.sin_hi, T.sin_lo, bh, bl);
@@ -62,29 +162,34 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
             int bi;
             float frac;
             split_int_frac(s2, (al + bl) + (e + e2), bi, frac);
-            const float2* row = dys + (size_t)(k0 + i) * a.Pb + bi;
-            const float m = T.m, om = 1.0f - T.m;
+            const uint32_t row = wbase + ((uint32_t)(i * wl + bi - s_ws[buf * kChunk + i]) << 3);
+            const float m = T.m, om = 1.0f - T.m, sn = T.sin_hi;
 #pragma unroll
-            for (int j = 0; j < PJ; ++j) {
-                const float beta = fmaf((float)j, T.sin_hi, frac);
-                int fi;
-                const float fb = floor_magic(beta, fi);
-                const float d = beta - fb;
-                const float h0 = __saturatef(fmaf(-d, m, 1.0f));
-                const float h1 = __saturatef(fmaf(d, m, om));
-                const float2 yy = __ldg(row + fi);
-                acc[j] = fmaf(h0, yy.x, fmaf(h1, yy.y, acc[j]));
+            for (int j = 0; j < PJ; j += 2) {
+                const float2 b2 = __ffma2_rn(make_float2((float)j, (float)(j + 1)), make_float2(sn, sn),
+                                             make_float2(frac, frac));
+                const float2 t2 = __fadd2_rd(b2, make_float2(kMagic, kMagic));
+                const float2 fb2 = __fadd2_rn(t2, make_float2(-kMagic, -kMagic));
+                const float2 d2 = __ffma2_rn(fb2, make_float2(-1.0f, -1.0f), b2);
+                const float2 y0 = lds64(row + ((uint32_t)__float_as_int(t2.x) << 3));
+                const float2 y1 = lds64(row + ((uint32_t)__float_as_int(t2.y) << 3));
+                acc[j] = fmaf(__saturatef(fmaf(-d2.x, m, 1.0f)), y0.x,
+                              fmaf(__saturatef(fmaf(d2.x, m, om)), y0.y, acc[j]));
+                acc[j + 1] = fmaf(__saturatef(fmaf(-d2.y, m, 1.0f)), y1.x,
+                                  fmaf(__saturatef(fmaf(d2.y, m, om)), y1.y, acc[j + 1]));
             }
         }
+        __syncthreads();
     }
-    // fixed-order sum of the eight angle groups
+    // fixed-order sum of the eight angle groups (reusing the window buffers)
+    float* s_red = reinterpret_cast<float*>(s_win);                         // [kGroups][PJ][32]
 #pragma unroll
-    for (int j = 0; j < PJ; ++j) s_red[g][j][lane] = acc[j];
+    for (int j = 0; j < PJ; ++j) s_red[(g * PJ + j) * 32 + lane] = acc[j];
     __syncthreads();
     for (int j = g; j < PJ; j += kGroups) {
         float v = 0.0f;
 #pragma unroll
-        for (int q = 0; q < kGroups; ++q) v += s_red[q][j][lane];
+        for (int q = 0; q < kGroups; ++q) v += s_red[(q * PJ + j) * 32 + lane];
         const int r = r0 + j;
         if (c < n && r < n) a.out[(size_t)slot * n * n + (size_t)r * n + c] = v;
     }
@@ -92,13 +197,38 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 
 }  // namespace
 
-cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s)
+int backproject_window(int pj) { return ((int)std::ceil(std::sqrt(31.0 * 31.0 + (pj - 1.0) * (pj - 1.0))) + 7) & ~1; }
+
+size_t backproject_smem_bytes(int pj)
 {
+    const size_t win = 2 * (size_t)kChunk * backproject_window(pj) * sizeof(float2);
+    const size_t red = (size_t)kGroups * pj * 32 * sizeof(float);
+    return 64 + 2 * kChunk * (sizeof(int) + sizeof(BpAngle)) + std::max(win, red);
+}
+
+cudaError_t backproject_prepare()
+{
+    cudaError_t e = cudaSuccess;
+    for (int pj : {4, 8, 16}) {
+        const int bytes = (int)backproject_smem_bytes(pj);
+        if (e == cudaSuccess && pj == 4) e = cudaFuncSetAttribute(k_backproject<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess && pj == 8) e = cudaFuncSetAttribute(k_backproject<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e == cudaSuccess && pj == 16) e = cudaFuncSetAttribute(k_backproject<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    }
+    return e;
+}
+
+cudaError_t launch_backproject(const BpArgs& a_in, cudaStream_t s)
+{
+    BpArgs a = a_in;
+    a.wl = backproject_window(a.pj);
+    if (a.wl > a.Pb) return cudaErrorInvalidValue;
     const dim3 grid((a.n + 31) / 32, (a.n + a.pj - 1) / a.pj, a.n_slots);
+    const size_t smem = backproject_smem_bytes(a.pj);
     switch (a.pj) {
-    case 4: k_backproject<4><<<grid, 256, 0, s>>>(a); break;
-    case 8: k_backproject<8><<<grid, 256, 0, s>>>(a); break;
-    case 16: k_backproject<16><<<grid, 256, 0, s>>>(a); break;
+    case 4: k_backproject<4><<<grid, 256, smem, s>>>(a); break;
+    case 8: k_backproject<8><<<grid, 256, smem, s>>>(a); break;
+    case 16: k_backproject<16><<<grid, 256, smem, s>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -107,15 +107,24 @@ template <int LC, bool CLAMP>
 __device__ __forceinline__ float sample_lines(uint32_t ray_base, float fr, float t, const float* mj,
                                               float wlo, float whi, int lines, float acc)
 {
+    // two lines per step: position, floor and fraction in paired FP32 ops
 #pragma unroll
-    for (int j = 0; j < LC; ++j) {
+    for (int j = 0; j < LC; j += 2) {
         if (CLAMP && j >= lines) break;
-        float w = fmaf(-(float)j, t, fr);
-        if (CLAMP) w = fminf(fmaxf(w, wlo), whi);
-        const float t1 = __fadd_rd(w, mj[j]);
-        const float f = w - (t1 - mj[j]);
-        const float2 v = lds64(ray_base + ((uint32_t)__float_as_int(t1) << 3));
-        acc += fmaf(f, v.y, v.x);
+        float2 w2 = __ffma2_rn(make_float2(-(float)j, -(float)(j + 1)), make_float2(t, t),
+                               make_float2(fr, fr));
+        if (CLAMP) {
+            w2.x = fminf(fmaxf(w2.x, wlo), whi);
+            w2.y = fminf(fmaxf(w2.y, wlo), whi);
+        }
+        const float2 t2 = __fadd2_rd(w2, make_float2(mj[j], mj[j + 1]));
+        const float2 d2 = __fadd2_rn(t2, make_float2(-mj[j], -mj[j + 1]));     // floor(w), exact
+        const float2 f2 = __ffma2_rn(d2, make_float2(-1.0f, -1.0f), w2);       // w - floor(w), exact
+        const float2 v0 = lds64(ray_base + ((uint32_t)__float_as_int(t2.x) << 3));
+        acc += fmaf(f2.x, v0.y, v0.x);
+        if (CLAMP && j + 1 >= lines) break;
+        const float2 v1 = lds64(ray_base + ((uint32_t)__float_as_int(t2.y) << 3));
+        acc += fmaf(f2.y, v1.y, v1.x);
     }
     return acc;
 }
@@ -134,8 +143,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kStages;
     int* s_flag = reinterpret_cast<int*>(smem + 96);
-    GroupState* s_grp = reinterpret_cast<GroupState*>(smem + 128);          // [kConsumers][RPT]
-    float2* stage0 = reinterpret_cast<float2*>(smem + 128 + sizeof(GroupState) * kConsumers * RPT);
+    __shared__ GroupState s_grp[kConsumers * RPT];
+    float2* stage0 = reinterpret_cast<float2*>(smem + 128);
     const size_t stage_pairs = (size_t)LC * a.P;
 
     const int slot = blockIdx.y;
@@ -250,8 +259,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         for (int ch = 0; ch < nch; ++ch) {
             const int g = it * nch + ch;
             const int st = g % kStages;
-            if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), kWaitLimit) ||
-                *(volatile int*)s_flag) {
+            if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), kWaitLimit)) {
                 atomicExch(s_flag, 1);
                 atomicExch(a.err, kErrTimeout);
                 return;
@@ -313,10 +321,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 
 int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
 
-size_t forward_smem_bytes(int lc, int P)
-{
-    return 128 + sizeof(GroupState) * kConsumers * 8 + kStages * (size_t)lc * P * sizeof(float2);
-}
+size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }
 
 #define MC_FWD_INSTANCES(X) \
     X(2, 2) X(4, 2) X(8, 2) X(2, 4) X(4, 4) X(8, 4) X(2, 8) X(4, 8) X(8, 8)

@@ -318,7 +318,7 @@ mc_status backproject(mc_ctx* c, int n_slots, float* out)
     BpArgs a{};
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
     a.ang = c->d_bang; a.n = c->n; a.na = c->na; a.nb = c->nb; a.n_slots = n_slots;
-    a.pj = c->pj; a.out = out;
+    a.pj = c->pj; a.out = out; a.err = c->d_err;
     return launch(c, C_BP, "backproject", [&] { return launch_backproject(a, c->stream); });
 }
 
@@ -862,9 +862,11 @@ mc_status mc_create(const mc_geometry* geom, int32_t n_gates, const mc_motion* m
     if (st == MC_OK) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        const size_t need = forward_smem_bytes(c->lc, c->P);
+        const size_t static_smem = 8192;   // the forward's static group tables
+        const size_t need = forward_smem_bytes(c->lc, c->P) + static_smem;
         if ((size_t)optin < need) st = fail(c, MC_EDEVICE, "forward needs %zu B shared memory", need);
-        else if (forward_prepare(optin) != cudaSuccess) st = fail(c, MC_ECUDA, "cudaFuncSetAttribute failed");
+        else if (forward_prepare(optin - (int)static_smem) != cudaSuccess || backproject_prepare() != cudaSuccess)
+            st = fail(c, MC_ECUDA, "cudaFuncSetAttribute failed");
     }
     if (st == MC_OK) st = alloc_state(c);
     if (st == MC_OK) st = build_motion(c, motion);

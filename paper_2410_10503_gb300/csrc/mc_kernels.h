@@ -107,8 +107,11 @@ struct BpArgs {
     int n_slots;
     int pj;                    // pixels per thread along a column (4, 8 or 16)
     float* out;                // slot stride n*n
+    int* err;
+    int wl;                    // staged window length (pairs), set by the launcher
 };
 cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
+cudaError_t backproject_prepare();
 
 // ---- misc -------------------------------------------------------------------
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
