@@ -197,6 +197,30 @@ mc_status mc_iteration(mc_ctx* ctx, uint64_t* out);
 /* Library version string. */
 const char* mc_version(void);
 
+/* Allocation-free forward operator, for callers that must not allocate
+ * device memory (code running inside an allocator hook, a plugin with a
+ * fixed memory budget, or a host whose GPU memory is already owned by its
+ * own pool).  The paper has no counterpart: this is a deployment variant of
+ * mc_forward for a single motion state, with no context.
+ *   out = A D x, where D is the rigid map rigid = {phi, tx, ty} (as in
+ *   mc_motion) or the identity when rigid is NULL; geometry as mc_create.
+ *   x (n x n) and out (n_angles x n_bins) are DEVICE arrays of the current
+ *   device, owned by the caller; host arrays are rejected (MC_EINVAL).
+ * All scratch (tables, the warped image's line layouts, an error word) lives
+ * in one fixed 24 MiB device array built into the library, which every device
+ * that loads the library holds until the process exits; the call makes no
+ * cudaMalloc, cudaFree or other allocation.  Sizes whose scratch exceeds the
+ * array (about n > 1150 at 720 angles) return MC_EINVAL.  The first call on
+ * each device sets up (looks up the array's device address, sets kernel
+ * attributes); make that first call before any stream capture.  Every call
+ * shares the array: calls that overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  Work
+ * is ordered on cuda_stream (NULL = legacy default stream) and the call
+ * returns before it completes.  err (nullable, err_cap bytes) receives a
+ * message on failure. */
+mc_status mc_forward_static(const mc_geometry* geom, const double* rigid, const float* x,
+                            float* out, void* cuda_stream, char* err, int32_t err_cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -54,6 +54,7 @@ SIGNATURES = {
     "mc_profile_reset": (_I32, [_VP]),
     "mc_iteration": (_I32, [_VP, _VP]),
     "mc_version": (ctypes.c_char_p, []),
+    "mc_forward_static": (_I32, [ctypes.POINTER(mc_geometry), _VP, _VP, _VP, _VP, ctypes.c_char_p, _I32]),
 }
 
 _lib = None
