@@ -50,7 +50,7 @@ def workload_config(W):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """nvidia-smi sampled every 200 ms while the timed region runs."""
+    """nvidia-smi sampled every 100 ms while the timed region runs."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -65,7 +65,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -146,6 +146,33 @@ def algorithmic_units(W):
     return S_cnt
 
 
+def reduce_over_ranks(tot_ms: float, units: float, dist, device):
+    """Whole-job timing over ranks: the slowest rank's time and the sum of
+    the units every rank processed (replicas, no data-path collective)."""
+    if dist is None:
+        return tot_ms, units
+    import torch
+    t = torch.tensor([tot_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/ncu_traffic.json, or
+    None when the kernel's source changed since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        return rec["dram_bytes_per_launch"] if digest == rec["source_sha256_16"] else None
+    except Exception:
+        return None
+
+
 def run_ours(args, W):
     import torch
 
@@ -187,13 +214,9 @@ def run_ours(args, W):
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
         step_ms = [a.elapsed_time(b) for a, b in evs]
-        tot_ms = float(sum(step_ms))
+        tot_ms, pairs = reduce_over_ranks(float(sum(step_ms)), float(args.steps * N), dist, "cuda")
         if dist:
-            t = torch.tensor([tot_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_ms = float(t.item())
             dist.barrier()
-    pairs = args.steps * N * world
     value = pairs / (tot_ms / 1e3)
 
     # ---- per-kernel durations: same steps, per-launch CUDA events on the
@@ -235,7 +258,7 @@ def run_ours(args, W):
     peak = float(args.l1_peak_gbs)
     achieved = alg_bytes / avg_s / 1e9
     roof = {"bound": "l1", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": None,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom),
             "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
             "peak_source": "152 SMs x 128 B/clk shared/L1 load x 2.07 GHz (derived)"}
     hbm_peak = None
@@ -342,8 +365,8 @@ def run_reference(args, W):
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(S.WORKLOADS))
     ap.add_argument("--cpu-pairs", type=int, default=3)
