@@ -278,6 +278,8 @@ def run_ours(args, W):
         "norms2_max": float(np.max(norms[:N])), "kappa_spdhg": ctx.steps()["kappa"],
         "hbm_peak_gbs_measured": hbm_peak, "wall_s": round(wall, 3),
     }
+    if args.convergence_epochs > 0:
+        out["time_to_1e-3"] = convergence_legs(ctx, stream, d, W, norms, sd, args.convergence_epochs)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
     ctx.close()
@@ -313,6 +315,62 @@ def run_ncu_case(args, W):
     torch.cuda.synchronize()
     ctx.close()
     print(json.dumps({"ncu_case": W.name, "epochs": args.warmup + args.steps}))
+
+
+def time_to_tol(ctx, stream, which, tol, max_epochs, seed, graph=True):
+    """Epochs (SPDHG: N iterations; PDHG: 1 iteration) from a zero start until
+    ||x - x*|| / ||x*|| <= tol, timed with CUDA events per epoch (trace
+    reductions included); returns a dict with epochs (None if not reached),
+    seconds to the crossing (or to max_epochs) and the last relative error."""
+    import torch
+    ctx.reset()
+    ctx.set_option(1, 1 if graph else 0)
+    tot = 0.0
+    rel = float("nan")
+    with torch.cuda.stream(stream):
+        for e in range(1, max_epochs + 1):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if which == "spdhg":
+                _, tr = ctx.spdhg_run(1, seed=seed, x_out=False, trace=True)
+            else:
+                _, tr = ctx.pdhg_run(1, x_out=False, trace=True)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b) / 1e3
+            rel = float(tr[0, 0])
+            if rel <= tol:
+                ctx.set_option(1, 1)
+                return {"epochs": e, "seconds": round(tot, 6), "rel_err": rel}
+    ctx.set_option(1, 1)
+    return {"epochs": None, "seconds_for_max_epochs": round(tot, 6), "max_epochs": max_epochs,
+            "rel_err": rel}
+
+
+def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs):
+    """Time to 1e-3 relative distance to x* for graph-replayed SPDHG, SPDHG
+    with plain launches and PDHG, in the paper's regime (alpha such that
+    ||A||^2 / alpha = 70, Sec. III) and at the workload's own alpha."""
+    import torch
+    out = {}
+    nA = float(np.max(norms[:W.n_gates]))
+    for label, alpha, cg_iters in [("paper_regime_kappa70", nA / 70.0, 400), ("workload_alpha", W.alpha, 300)]:
+        ctx.set_data(d, alpha)
+        ctx.set_norms(norms)
+        x_star = torch.empty((W.n, W.n), dtype=torch.float32, device="cuda")
+        _, iters, rel = ctx.solve_normal(max_iter=cg_iters, tol=1e-6, x_out=x_star)
+        ctx.set_reference(x_star)
+        leg = {"alpha": alpha, "kappa": nA / alpha,
+               "kappa_spdhg": ctx.steps()["kappa"], "kappa_pdhg": ctx.steps(pdhg=True)["kappa"],
+               "x_star_cg": {"iterations": iters, "rel_residual": rel}}
+        leg["spdhg_graph"] = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], True)
+        leg["spdhg_plain"] = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], False)
+        leg["pdhg_graph"] = time_to_tol(ctx, stream, "pdhg", 1e-3, max_epochs, sd["gates"], True)
+        out[label] = leg
+    ctx.set_data(d, W.alpha)
+    ctx.set_norms(norms)
+    return out
 
 
 def _oracle_pair_setup(W):
@@ -371,6 +429,8 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(S.WORKLOADS))
     ap.add_argument("--cpu-pairs", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--convergence-epochs", type=int, default=100,
+                    help="epoch cap of the time-to-1e-3 legs (0 skips them)")
     ap.add_argument("--l1-peak-gbs", type=float, default=152 * 128 * 2.07)
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling driver: set up the workload, then only warm-up + timed "

@@ -145,6 +145,14 @@ mc_status mc_get_steps(mc_ctx* ctx, int32_t pdhg, double* out);
  * is derived from it.  Call after mc_set_data.  NULL clears it. */
 mc_status mc_set_reference(mc_ctx* ctx, const float* x_star);
 
+/* Reference solution by conjugate gradients on the optimality condition of
+ * O (Sec. II-A): (alpha I + N^-1 sum_i A_i^T A_i) x = N^-1 sum_i A_i^T d_i, with
+ * float32 operators (all gates per iteration) and float64 inner products.
+ * Stops after max_iter iterations or once ||r|| <= tol ||b|| (checked every
+ * 10 iterations).  x_out (n x n, host or device) receives x; info (nullable,
+ * host, 2 doubles) receives {iterations, ||r||/||b||}.  Needs mc_set_data. */
+mc_status mc_solve_normal(mc_ctx* ctx, int32_t max_iter, double tol, float* x_out, double* info);
+
 /* Zero the solver state (x = z = zbar = 0, y = 0) and the iteration count. */
 mc_status mc_reset(mc_ctx* ctx);
 

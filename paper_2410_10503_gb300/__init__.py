@@ -221,6 +221,18 @@ class Context:
     def reset(self):
         self._check(self._L.mc_reset(self._h))
 
+    def solve_normal(self, max_iter: int = 500, tol: float = 1e-6, x_out=None, like=None):
+        """x* of (alpha I + N^-1 sum A_i^T A_i) x = N^-1 sum A_i^T d_i by CG;
+        returns (x, iterations, relative residual)."""
+        if x_out is None:
+            x_out = _empty_like_kind(like, (self.n, self.n)) if like is not None else \
+                np.empty((self.n, self.n), np.float32)
+        px = _arg(x_out, np.float32, self.img_count, "x_out")[0]
+        info = np.zeros(2)
+        self._call(self._L.mc_solve_normal, int(max_iter), float(tol), px, info.ctypes.data,
+                   cuda_args=(x_out,))
+        return x_out, int(info[0]), float(info[1])
+
     def _run(self, which, epochs, seed, stream, x_out, trace, like):
         if x_out is None:
             x_out = _empty_like_kind(like, (self.n, self.n)) if like is not None else \

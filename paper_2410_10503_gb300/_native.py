@@ -45,6 +45,7 @@ SIGNATURES = {
     "mc_get_steps": (_I32, [_VP, _I32, _VP]),
     "mc_set_reference": (_I32, [_VP, _VP]),
     "mc_reset": (_I32, [_VP]),
+    "mc_solve_normal": (_I32, [_VP, _I32, _D, _VP, _VP]),
     "mc_spdhg_run": (_I32, [_VP, _I32, ctypes.POINTER(mc_sampling), _VP, _VP]),
     "mc_pdhg_run": (_I32, [_VP, _I32, _VP, _VP]),
     "mc_draw_gates": (_I32, [_VP, ctypes.POINTER(mc_sampling), _U64, _I32, _VP]),

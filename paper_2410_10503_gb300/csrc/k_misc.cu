@@ -110,6 +110,28 @@ __global__ void k_objective_combine(const double* xx, const double* res, int n_r
     *out = alpha * (*xx) + s / (double)N;
 }
 
+// Conjugate-gradient updates with the scalars kept on the device (float64):
+// step 1: a = rr / pq, x += a p, r -= a q;  step 2: beta = rr_new / rr, p = r + beta p.
+__global__ void k_cg_step1(float* x, float* r, const float* p, const float* q, size_t len,
+                           const double* rr, const double* pq)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double den = *pq;
+    const float a = den != 0.0 ? (float)(*rr / den) : 0.0f;
+    if (i < len) {
+        x[i] = fmaf(a, p[i], x[i]);
+        r[i] = fmaf(-a, q[i], r[i]);
+    }
+}
+
+__global__ void k_cg_step2(float* p, const float* r, size_t len, const double* rr_new, const double* rr_old)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double den = *rr_old;
+    const float beta = den != 0.0 ? (float)(*rr_new / den) : 0.0f;
+    if (i < len) p[i] = fmaf(beta, p[i], r[i]);
+}
+
 __global__ void k_fill_nan(double* p, int count)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,6 +189,20 @@ cudaError_t launch_objective_combine(const double* xx, const double* res, int n_
                                      double alpha, int N, double* out, cudaStream_t s)
 {
     k_objective_combine<<<1, 1, 0, s>>>(xx, res, n_res, alpha, N, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_step1(float* x, float* r, const float* p, const float* q, size_t len,
+                            const double* rr, const double* pq, cudaStream_t s)
+{
+    k_cg_step1<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(x, r, p, q, len, rr, pq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_step2(float* p, const float* r, size_t len, const double* rr_new,
+                            const double* rr_old, cudaStream_t s)
+{
+    k_cg_step2<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(p, r, len, rr_new, rr_old);
     return cudaGetLastError();
 }
 

@@ -122,6 +122,9 @@ struct mc_ctx {
     Steps sS, sP;
     bool steps_ok = false;
 
+    // conjugate-gradient vectors (x, r, p, q), allocated on first use
+    float* d_cg = nullptr;
+
     // reference
     float* d_xstar = nullptr;
     float* d_ystar = nullptr;
@@ -143,7 +146,8 @@ struct mc_ctx {
 };
 
 // scalar slots in d_s
-enum { S_DX2 = 0, S_XS2 = 1, S_DY2 = 2, S_XX = 3, S_TMP = 4, S_LAM = 5, S_NRM = 6, S_RES = 16 };
+enum { S_DX2 = 0, S_XS2 = 1, S_DY2 = 2, S_XX = 3, S_TMP = 4, S_LAM = 5, S_NRM = 6,
+       S_RR0 = 7, S_RR1 = 8, S_PQ = 9, S_BB = 10, S_RES = 16 };
 
 namespace {
 
@@ -1113,6 +1117,66 @@ mc_status mc_set_reference(mc_ctx* c, const float* x_star)
         return launch_axpby(s, c->d_ystar, -s, c->d_d, c->d_ystar, (size_t)c->N * ns, c->stream);
     }));
     c->have_ref = true;
+    CK(cudaStreamSynchronize(c->stream));
+    return finish(c);
+}
+
+// (alpha I + N^-1 sum_i A_i^T A_i) v into out (all gates at once)
+static mc_status apply_normal(mc_ctx* c, const float* v, float* out)
+{
+    const GateSel all{nullptr, -1};
+    const size_t n2 = (size_t)c->n * c->n;
+    TRY(warp_into_layouts(c, v, all, c->N, false));
+    TRY(project_store(c, all, c->N, c->d_sinoN));
+    TRY(pad_sinos(c, c->d_sinoN, c->N));
+    TRY(adjoint_from_dy(c, all, c->N, out));
+    const float inv_n = (float)(1.0 / c->N);
+    const float al = (float)c->alpha;
+    return launch(c, C_MISC, "axpby", [&] { return launch_axpby(al, v, inv_n, out, out, n2, c->stream); });
+}
+
+mc_status mc_solve_normal(mc_ctx* c, int32_t max_iter, double tol, float* x_out, double* info)
+{
+    if (!c) return MC_EINVAL;
+    if (!c->have_data) return fail(c, MC_ESTATE, "mc_solve_normal needs mc_set_data first");
+    if (max_iter < 1 || !(tol >= 0)) return fail(c, MC_EINVAL, "max_iter >= 1 and tol >= 0 required");
+    TRY(check_ptr(c, x_out, "x_out"));
+    const size_t n2 = (size_t)c->n * c->n;
+    if (!c->d_cg) TRY(dalloc(c, &c->d_cg, 4 * n2));
+    float *x = c->d_cg, *r = x + n2, *p = r + n2, *q = p + n2;
+    CK(cudaMemsetAsync(x, 0, n2 * sizeof(float), c->stream));
+    // r = p = b = N^-1 sum_i A_i^* d_i
+    TRY(pad_sinos(c, c->d_d, c->N));
+    TRY(adjoint_from_dy(c, GateSel{nullptr, -1}, c->N, r));
+    const float inv_n = (float)(1.0 / c->N);
+    TRY(launch(c, C_MISC, "axpby", [&] { return launch_axpby(inv_n, r, 0.0f, nullptr, r, n2, c->stream); }));
+    CK(cudaMemcpyAsync(p, r, n2 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    TRY(reduce(c, r, nullptr, n2, kRedSumSq, c->d_s + S_BB));
+    TRY(reduce(c, r, nullptr, n2, kRedSumSq, c->d_s + S_RR0));
+    double bb = 0;
+    CK(cudaMemcpyAsync(&bb, c->d_s + S_BB, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    int it = 0;
+    double rel = bb > 0 ? 1.0 : 0.0;
+    double* rr = c->d_s + S_RR0;
+    double* rr_new = c->d_s + S_RR1;
+    while (it < max_iter && rel > tol) {
+        TRY(apply_normal(c, p, q));
+        TRY(reduce(c, p, q, n2, kRedDot, c->d_s + S_PQ));
+        TRY(launch(c, C_MISC, "cg", [&] { return launch_cg_step1(x, r, p, q, n2, rr, c->d_s + S_PQ, c->stream); }));
+        TRY(reduce(c, r, nullptr, n2, kRedSumSq, rr_new));
+        TRY(launch(c, C_MISC, "cg", [&] { return launch_cg_step2(p, r, n2, rr_new, rr, c->stream); }));
+        std::swap(rr, rr_new);
+        ++it;
+        if (it % 10 == 0 || it == max_iter) {
+            double h = 0;
+            CK(cudaMemcpyAsync(&h, rr, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            rel = bb > 0 ? std::sqrt(std::max(h, 0.0) / bb) : 0.0;
+        }
+    }
+    TRY(stage_out(c, x_out, x, n2));
+    if (info) { info[0] = it; info[1] = rel; }
     CK(cudaStreamSynchronize(c->stream));
     return finish(c);
 }

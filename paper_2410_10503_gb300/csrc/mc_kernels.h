@@ -137,5 +137,10 @@ cudaError_t launch_trace_combine(const double* dx2, const double* xs2, const dou
 cudaError_t launch_objective_combine(const double* xx, const double* res, int n_res,
                                      double alpha, int N, double* out, cudaStream_t s);
 cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s);
+// conjugate gradients with device-side float64 scalars
+cudaError_t launch_cg_step1(float* x, float* r, const float* p, const float* q, size_t len,
+                            const double* rr, const double* pq, cudaStream_t s);
+cudaError_t launch_cg_step2(float* p, const float* r, size_t len, const double* rr_new,
+                            const double* rr_old, cudaStream_t s);
 
 }  // namespace mcg

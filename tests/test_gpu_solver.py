@@ -191,3 +191,19 @@ def test_device_and_host_outputs_agree(mc, rigid128):
     ctx.reset()
     xh, _ = ctx.spdhg_run(2, seed=sd["gates"])
     np.testing.assert_array_equal(xd.cpu().numpy(), xh)
+
+
+def test_solve_normal_matches_oracle_xstar(mc):
+    """GPU conjugate gradients (float32 operators, float64 inner products)
+    reach the oracle's x* on a 48^2 problem in the paper's regime (kappa = 70)."""
+    n, N = 48, 4
+    W = S.WORKLOADS["rigid128"].scaled(n=n, n_angles=72, n_bins=71, n_gates=N, n_ellipses=6,
+                                       axis_lo=3.0, axis_hi=14.0)
+    P, sd = problem(W)
+    nA = O.power_norm2(lambda v: O.At(O.A(v, P.geom), P.geom), (n, n))
+    P.alpha = nA / 70.0
+    xs = O.solve_xstar(P, tol=1e-13)
+    ctx = context(mc, P)
+    x, iters, rel = ctx.solve_normal(max_iter=400, tol=1e-6)
+    assert rel <= 1e-6 and iters < 400
+    assert rel_l2(x, xs) <= 1e-5
