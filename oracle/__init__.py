@@ -56,6 +56,8 @@ def _L():
                                 ctypes.c_double, fp, dp, dp]
         lib.or_warp_adj.argtypes = lib.or_warp.argtypes
         lib.or_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        lib.or_warp_field_vjp.argtypes = [ctypes.c_int, fp, dp, dp, dp]
+        lib.or_warp_field_vjp.restype = None
         lib.or_draw_gates.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                       ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(ctypes.c_uint64),
@@ -139,6 +141,24 @@ class Problem:
     @property
     def N(self) -> int:
         return self.motion.n_gates
+
+
+def warp_field_vjp(x, g, field_i, n: int) -> np.ndarray:
+    """(2, n, n): g(p) times the derivative of the pull-back warp (D_u x)(p)
+    with respect to u_x(p) and u_y(p) (dense field of one gate, float32)."""
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(n, n)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(n, n)
+    f = np.ascontiguousarray(field_i, dtype=np.float32).reshape(2, n, n)
+    out = np.empty((2, n, n))
+    _L().or_warp_field_vjp(n, f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _dp(x), _dp(g), _dp(out))
+    return out
+
+
+def loss_field_grad(x, P: Problem, i: int) -> np.ndarray:
+    """Gradient of N^-1 ||A D_{u_i} x - d_i||^2 with respect to the field u_i
+    (the differentiated data term of Sec. II-A)."""
+    r = (2.0 / P.N) * (Ai(x, P, i) - P.d[i])
+    return warp_field_vjp(x, At(r, P.geom), P.motion.fields[i], P.geom.n)
 
 
 def Ai(x, P: Problem, i: int) -> np.ndarray:

@@ -230,3 +230,32 @@ void or_draw_gates(uint64_t seed, uint32_t stream, uint64_t k0, int count, int n
         }
     }
 }
+
+/* Vector-Jacobian product of the dense-field warp: for (D_u x)(p) =
+ * bilinear(x)(p + u(p)), out[0][p] = g(p) d(D_u x)(p)/du_x(p) and
+ * out[1][p] = g(p) d(D_u x)(p)/du_y(p).  The derivative is that of the
+ * bilinear interpolant inside the cell holding q(p) (taps outside the image
+ * are zero), i.e. one-sided on the cell's lower edges. */
+void or_warp_field_vjp(int n, const float* field, const double* x, const double* g, double* out)
+{
+    const size_t n2 = (size_t)n * n;
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            const size_t p = (size_t)r * n + c;
+            const double cq = (double)c + (double)field[p];
+            const double rq = (double)r + (double)field[n2 + p];
+            const double r0 = floor(rq), c0 = floor(cq);
+            const double fr = rq - r0, fc = cq - c0;
+            const int i0 = (int)r0, j0 = (int)c0;
+            double v[2][2];
+            for (int di = 0; di < 2; ++di)
+                for (int dj = 0; dj < 2; ++dj) {
+                    const int i = i0 + di, j = j0 + dj;
+                    v[di][dj] = (i >= 0 && i < n && j >= 0 && j < n) ? x[(size_t)i * n + j] : 0.0;
+                }
+            const double dcol = (1.0 - fr) * (v[0][1] - v[0][0]) + fr * (v[1][1] - v[1][0]);
+            const double drow = (1.0 - fc) * (v[1][0] - v[0][0]) + fc * (v[1][1] - v[0][1]);
+            out[p] = g[p] * dcol;
+            out[n2 + p] = g[p] * drow;
+        }
+}

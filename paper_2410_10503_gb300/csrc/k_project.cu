@@ -90,13 +90,6 @@ __device__ __forceinline__ int gate_of(const GateSel& s, int slot)
     return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
 }
 
-__device__ __forceinline__ float2 lds64(uint32_t addr)
-{
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
-    return v;
-}
-
 // Samples of one ray over the LC lines of a staged chunk.  The magic
 // constant of line j is kMagic + j * P: adding it with round-down leaves
 // floor(w) + j * P in the low mantissa bits, so the shared address of the pair
@@ -104,10 +97,12 @@ __device__ __forceinline__ float2 lds64(uint32_t addr)
 // confines positions to [-ui, P - 2 - ui], i.e. into the zero guard cells,
 // and skips lines j >= lines of a short last chunk (warp-uniform).
 template <int LC, bool CLAMP>
-__device__ __forceinline__ float sample_lines(uint32_t ray_base, float fr, float t, const float* mj,
+__device__ __forceinline__ float sample_lines(const float2* stage, int ibase, float fr, float t, const float* mj,
                                               float wlo, float whi, int lines, float acc)
 {
-    // two lines per step: position, floor and fraction in paired FP32 ops
+    // two lines per step: position, floor and fraction in paired FP32 ops; the
+    // round-down sum's bits are kMagicBits + floor(w) + j * P, so the pair's
+    // index is ibase + bits with ibase = ui - kMagicBits
 #pragma unroll
     for (int j = 0; j < LC; j += 2) {
         if (CLAMP && j >= lines) break;
@@ -120,10 +115,10 @@ __device__ __forceinline__ float sample_lines(uint32_t ray_base, float fr, float
         const float2 t2 = __fadd2_rd(w2, make_float2(mj[j], mj[j + 1]));
         const float2 d2 = __fadd2_rn(t2, make_float2(-mj[j], -mj[j + 1]));     // floor(w), exact
         const float2 f2 = __ffma2_rn(d2, make_float2(-1.0f, -1.0f), w2);       // w - floor(w), exact
-        const float2 v0 = lds64(ray_base + ((uint32_t)__float_as_int(t2.x) << 3));
+        const float2 v0 = stage[ibase + __float_as_int(t2.x)];
         acc += fmaf(f2.x, v0.y, v0.x);
         if (CLAMP && j + 1 >= lines) break;
-        const float2 v1 = lds64(ray_base + ((uint32_t)__float_as_int(t2.y) << 3));
+        const float2 v1 = stage[ibase + __float_as_int(t2.y)];
         acc += fmaf(f2.y, v1.y, v1.x);
     }
     return acc;
@@ -195,7 +190,6 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     float mj[LC];
 #pragma unroll
     for (int j = 0; j < LC; ++j) mj[j] = kMagic + (float)(j * a.P);
-    const uint32_t magic_off = (uint32_t)kMagicBits << 3;
     GroupState* my = s_grp + warp * RPT;
 
     for (int it = 0; it < n_it; ++it) {
@@ -264,19 +258,19 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 atomicExch(a.err, kErrTimeout);
                 return;
             }
-            const uint32_t sb = smem_u32(stage0 + st * stage_pairs) - magic_off;
+            const float2* sp = stage0 + st * stage_pairs;
             const int lines = min(LC, n - ch * LC);
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
                 if (m >= ns) break;
                 const GroupState gs = my[m];
                 if (ch < gs.c_lo || ch > gs.c_hi) continue;
-                const uint32_t rb = sb + ((uint32_t)ui[m] << 3);
+                const int ib = ui[m] - kMagicBits;
                 if (ch >= gs.in_lo && ch <= gs.in_hi) {
-                    acc[m] = sample_lines<LC, false>(rb, frac[m], gs.t, mj, 0.0f, 0.0f, LC, acc[m]);
+                    acc[m] = sample_lines<LC, false>(sp, ib, frac[m], gs.t, mj, 0.0f, 0.0f, LC, acc[m]);
                 } else {
                     const float wlo = -(float)ui[m], whi = (float)(a.P - 2 - ui[m]);
-                    acc[m] = sample_lines<LC, true>(rb, frac[m], gs.t, mj, wlo, whi, lines, acc[m]);
+                    acc[m] = sample_lines<LC, true>(sp, ib, frac[m], gs.t, mj, wlo, whi, lines, acc[m]);
                 }
                 // advance to the first line of the next chunk: u -= LC * t
                 float nf = frac[m] - gs.step_frac;

@@ -228,3 +228,63 @@ def test_gate_draw_nonuniform():
     g = O.draw_gates(99, 3, 0, K, 4, p=p)
     freq = np.bincount(g, minlength=4) / K
     np.testing.assert_allclose(freq, p, atol=5e-3)
+
+
+# ---------------------------------------------------------------- field derivative
+H = 2.0 ** -10          # finite-difference step (~1e-3), exact in float32
+
+
+def _field_away_from_grid(n, seed, amp=2.0):
+    """Dense field on a 2^-12 grid whose sample positions stay >= 0.05 px from
+    grid lines, so that f +- H is exact in float32 and stays in one bilinear
+    cell (where the central difference is exact)."""
+    rng = np.random.default_rng(seed)
+    f = rng.uniform(-amp, amp, size=(2, n, n))
+    frac = f - np.floor(f)
+    f = np.where(frac < 0.05, f + 0.05, f)
+    f = np.where(frac > 0.95, f - 0.05, f)
+    return (np.round(f * 4096.0) / 4096.0).astype(np.float32)
+
+
+def test_field_vjp_matches_central_differences():
+    """<g, d(D_u x)/du . e> against central differences of <g, D_u x>."""
+    n = 12
+    x = S.random_image(n, 31)
+    g = S.random_image(n, 32) - 0.5
+    f = _field_away_from_grid(n, 33)
+    vjp = O.warp_field_vjp(x, g, f, n)
+    rng = np.random.default_rng(34)
+    for _ in range(16):
+        ch, r, c = rng.integers(0, 2), rng.integers(0, n), rng.integers(0, n)
+        fp, fm = f.copy(), f.copy()
+        fp[ch, r, c] += H
+        fm[ch, r, c] -= H
+        lp = float(np.sum(g * O.D(x, O.Motion(fields=fp[None]), 0, n)))
+        lm = float(np.sum(g * O.D(x, O.Motion(fields=fm[None]), 0, n)))
+        assert abs((lp - lm) / (2 * H) - vjp[ch, r, c]) <= 1e-9 * (1 + abs(vjp[ch, r, c]))
+
+
+def test_loss_field_gradient_directional_derivatives():
+    """Gradient of N^-1 ||A D_u x - d||^2 w.r.t. u along random directions,
+    against central differences (step 1e-3) of the oracle's loss."""
+    n, N = 16, 2
+    g = O.Geometry(n, 20, 23)
+    f = np.stack([np.zeros((2, n, n), np.float32), _field_away_from_grid(n, 35, amp=1.5)])
+    P = O.Problem(g, O.Motion(fields=f), S.random_sinogram(20, 23, 36)[None].repeat(N, 0), 1.0)
+    x = S.random_image(n, 37)
+    grad = O.loss_field_grad(x, P, 1)
+    rng = np.random.default_rng(38)
+    def loss(fi):
+        Pq = O.Problem(g, O.Motion(fields=np.stack([f[0], fi])), P.d, 1.0)
+        r = O.Ai(x, Pq, 1) - P.d[1]
+        return float(np.sum(r * r)) / N
+    for _ in range(6):
+        # sign directions on a sparse support: f +- H e is exact in float32 and
+        # stays in every cell; moving one component per pixel keeps the warped
+        # image linear and the loss quadratic in H, so the central difference
+        # equals the directional derivative
+        e = rng.choice([-1.0, 1.0], size=(2, n, n)) * (rng.uniform(size=(2, n, n)) < 0.3)
+        e[1][e[0] != 0] = 0.0      # one component per pixel: no bilinear cross term
+        fd = (loss((f[1] + H * e).astype(np.float32)) - loss((f[1] - H * e).astype(np.float32))) / (2 * H)
+        an = float(np.sum(grad * e))
+        assert abs(fd - an) <= 1e-7 * (abs(an) + 1.0)
