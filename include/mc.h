@@ -121,6 +121,29 @@ mc_status mc_backproject(mc_ctx* ctx, const float* y, float* out);
 mc_status mc_warp(mc_ctx* ctx, int32_t gate, const float* x, float* out);
 mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out);
 
+/* Replace the dense displacement field of one gate (Sec. II-A: D_i is the
+ * pull-back warp by u_i).  field: 2 x n x n {ux (column), uy (row)} in px,
+ * host or device, copied; values must be finite with |u| <= 1e5.  Rebuilds
+ * that gate's D_i^T CSR in place, without allocating (every gate owns a
+ * fixed slice of 4 n^2 entries, the most its taps can need).  A_i changes, so the
+ * squared norms, the step sizes and x* are dropped: call mc_norms or
+ * mc_set_norms (and mc_set_reference) again before the next run.  The
+ * iterates are kept (a warm start).  MC_ESTATE for rigid-motion contexts. */
+mc_status mc_set_field(mc_ctx* ctx, int32_t gate, const float* field);
+
+/* Vector-Jacobian product of (x, u_i) -> A D_{u_i} x at cotangent r
+ * (n_angles x n_bins): with b = A^T r,
+ *   grad_x     = D_i^T b = A_i^* r                      (n x n),
+ *   grad_field = b(p) * d x(q)/dq at q = p + u_i(p)     (2 x n x n, {ux, uy}),
+ * the second being the derivative of the bilinear sample inside the cell
+ * that floor(q) selects (zero-padded like D_i).  The data term
+ * N^-1 ||A_i x - d_i||^2 of Sec. II-A has gradient mc_vjp at
+ * r = (2/N)(A_i x - d_i).  Either output may be NULL (not both); grad_field
+ * needs a dense-field context (MC_ESTATE otherwise) and x, the image the
+ * forward map was applied to.  One backprojection serves both outputs. */
+mc_status mc_vjp(mc_ctx* ctx, int32_t gate, const float* x, const float* r, float* grad_x,
+                 float* grad_field);
+
 /* Power iteration (Theorem, Sec. II-B) with float32 operators and float64
  * reductions.  out (host or device, N+1 doubles): ||A_0||^2 .. ||A_{N-1}||^2,
  * then ||(A_0; ...; A_{N-1})||^2 = lambda_max(sum_i A_i^T A_i).  Stops per

@@ -23,7 +23,7 @@ import numpy as np
 
 from . import _native as N
 
-__all__ = ["Context", "MCError", "lib", "version"]
+__all__ = ["Context", "MCError", "lib", "version", "project_gate"]
 
 try:  # torch is plumbing here (device memory, streams); optional for host arrays
     import torch
@@ -106,6 +106,7 @@ class Context:
             raise MCError(st, L.mc_last_error(None).decode())
         self._h = out.value
         self.kind = "rigid" if rigid is not None else "field"
+        self._field_version = {}
 
     # -- plumbing --------------------------------------------------------------
     def _check(self, st: int):
@@ -191,6 +192,32 @@ class Context:
     def warp_adjoint(self, gate: int, v, out=None):
         """D_i^T v."""
         return self._op(self._L.mc_warp_adjoint, (gate,), v, self.img_count, out, (self.n, self.n))
+
+    # -- differentiation -------------------------------------------------------
+    def set_field(self, gate: int, field):
+        """Replace gate `gate`'s dense displacement field (2 x n x n); drops
+        the norms, step sizes and reference (mc_set_field)."""
+        p, k = _arg(field, np.float32, 2 * self.img_count, "field")
+        self._call(self._L.mc_set_field, gate, p, cuda_args=(field,))
+        self._field_version[gate] = self._field_version.get(gate, 0) + 1
+
+    def field_version(self, gate: int) -> int:
+        """How many times set_field replaced this gate's field."""
+        return self._field_version.get(gate, 0)
+
+    def vjp(self, gate: int, x, r, grad_x=True, grad_field=True):
+        """(A_i^* r, b * grad of the warp sample w.r.t. u_i) with b = A^T r
+        (mc_vjp); either part may be skipped (None is returned for it)."""
+        pr, kr = _arg(r, np.float32, self.sino_count, "r")
+        px = None
+        if grad_field:
+            px, kx = _arg(x, np.float32, self.img_count, "x")
+        gx = _empty_like_kind(r, (self.n, self.n)) if grad_x else None
+        gf = _empty_like_kind(r, (2, self.n, self.n)) if grad_field else None
+        pgx = _arg(gx, np.float32, self.img_count, "grad_x")[0] if grad_x else None
+        pgf = _arg(gf, np.float32, 2 * self.img_count, "grad_field")[0] if grad_field else None
+        self._call(self._L.mc_vjp, gate, px, pr, pgx, pgf, cuda_args=(x, r, gx, gf))
+        return gx, gf
 
     # -- problem ------------------------------------------------------------------
     def set_data(self, d, alpha: float):
@@ -292,3 +319,13 @@ class Context:
         out = ctypes.c_uint64()
         self._check(self._L.mc_iteration(self._h, ctypes.addressof(out)))
         return out.value
+
+
+def project_gate(ctx: Context, gate: int, x, field=None):
+    """Differentiable A_i x = A D_{u_i} x on CUDA tensors (torch autograd).
+
+    `field` (2 x n x n, dense-field contexts) replaces the gate's field first
+    when given; gradients flow to x (A_i^* of the output gradient) and to the
+    field (mc_vjp).  See autograd.GateProjection."""
+    from .autograd import GateProjection
+    return GateProjection.apply(ctx, gate, x, field)

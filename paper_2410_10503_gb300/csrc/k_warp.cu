@@ -264,6 +264,47 @@ cudaError_t launch_exclusive_scan(const int* in, int* out_rowptr, int len, int* 
     return cudaGetLastError();
 }
 
+// ---- field VJP ---------------------------------------------------------------
+// out0(p) = g(p) d(D_u x)(p)/du_x(p), out1(p) = g(p) d(D_u x)(p)/du_y(p): the
+// derivative of the bilinear pull-back sample at q(p) = p + u(p) inside the
+// cell that the floor split of q(p) selects (taps outside the image are
+// zero).  With g = A^T r this is the gradient of <A D_u x, r> with respect
+// to the dense displacement field u of one gate (Sec. II-A).
+__global__ void __launch_bounds__(256) k_field_vjp(int n, const float* __restrict__ field,
+                                                   const float* __restrict__ x,
+                                                   const float* __restrict__ g,
+                                                   float* __restrict__ out0,
+                                                   float* __restrict__ out1)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n * n) return;
+    const int r = p / n, c = p - r * n;
+    int r0, c0;
+    float fr, fc;
+    warp_taps(nullptr, field, n, r, c, r0, c0, fr, fc);
+    float v[2][2];
+#pragma unroll
+    for (int di = 0; di < 2; ++di)
+#pragma unroll
+        for (int dj = 0; dj < 2; ++dj) {
+            const int i = r0 + di, j = c0 + dj;
+            v[di][dj] = (i >= 0 && i < n && j >= 0 && j < n) ? __ldg(x + (size_t)i * n + j) : 0.0f;
+        }
+    const float dcol = fmaf(fr, v[1][1] - v[1][0], __fmul_rn(1.0f - fr, v[0][1] - v[0][0]));
+    const float drow = fmaf(fc, v[1][1] - v[0][1], __fmul_rn(1.0f - fc, v[1][0] - v[0][0]));
+    const float gp = __ldg(g + p);
+    out0[p] = gp * dcol;
+    out1[p] = gp * drow;
+}
+
+cudaError_t launch_field_vjp(int n, const float* field, const float* x, const float* g,
+                             float* out0, float* out1, cudaStream_t s)
+{
+    const int tot = n * n;
+    k_field_vjp<<<(tot + 255) / 256, 256, 0, s>>>(n, field, x, g, out0, out1);
+    return cudaGetLastError();
+}
+
 // ---- K5 (+K7) -------------------------------------------------------------
 template <bool UPDATE>
 __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)

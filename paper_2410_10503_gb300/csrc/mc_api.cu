@@ -84,7 +84,8 @@ struct mc_ctx {
     int* d_rowptr = nullptr;
     int2* d_ent = nullptr;
     long long* d_ent_off = nullptr;
-    long long nnz_total = 0;
+    int* d_csr_cnt = nullptr;     // per-row counters and scan scratch of a CSR rebuild
+    int* d_csr_scan = nullptr;
 
     // data and iterates
     float* d_d = nullptr;
@@ -685,6 +686,31 @@ mc_status build_tables(mc_ctx* c)
     return MC_OK;
 }
 
+// Copy the dense field of gate g (2 x n x n floats at src + off, host or
+// device) into the context and reject non-finite or absurd displacements
+// (sample positions must stay below 2^22).
+mc_status load_field(mc_ctx* c, int g, const float* src, size_t off)
+{
+    const size_t cnt = (size_t)2 * c->n * c->n;
+    const int pk = ptr_kind(c, src);
+    if (pk < 0) return fail(c, MC_EINVAL, "motion field lives on another device");
+    std::vector<float> hf(cnt);
+    if (pk == 1) {
+        CK(cudaMemcpyAsync(hf.data(), src + off, cnt * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    } else {
+        std::memcpy(hf.data(), src + off, cnt * sizeof(float));
+    }
+    for (size_t i = 0; i < cnt; ++i)
+        if (!std::isfinite(hf[i]) || std::fabs(hf[i]) > 1.0e5f)
+            return fail(c, MC_EINVAL, "motion field of gate %d, value %zu, is not finite or |u| > 1e5",
+                        g, i);
+    CK(cudaMemcpyAsync(c->d_field + (size_t)g * cnt, hf.data(), cnt * sizeof(float),
+                       cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MC_OK;
+}
+
 mc_status build_motion(mc_ctx* c, const mc_motion* m)
 {
     const int n = c->n, N = c->N;
@@ -707,20 +733,28 @@ mc_status build_motion(mc_ctx* c, const mc_motion* m)
         CK(cudaMemcpyAsync(c->d_rigid, rg.data(), N * sizeof(RigidGate), cudaMemcpyHostToDevice, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     } else {
-        const size_t cnt = (size_t)N * 2 * n * n;
-        TRY(dalloc(c, &c->d_field, cnt));
-        const int pk = ptr_kind(c, m->field);
-        if (pk < 0) return fail(c, MC_EINVAL, "motion field lives on another device");
-        CK(cudaMemcpyAsync(c->d_field, m->field, cnt * sizeof(float),
-                           pk == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        // reject non-finite or absurd displacements (positions must stay < 2^22)
-        std::vector<float> hf(cnt);
-        CK(cudaMemcpy(hf.data(), c->d_field, cnt * sizeof(float), cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < cnt; ++i)
-            if (!std::isfinite(hf[i]) || std::fabs(hf[i]) > 1.0e5f)
-                return fail(c, MC_EINVAL, "motion field value %zu is not finite or |u| > 1e5", i);
+        TRY(dalloc(c, &c->d_field, (size_t)N * 2 * n * n));
+        for (int g = 0; g < N; ++g) TRY(load_field(c, g, m->field, (size_t)g * 2 * n * n));
     }
+    return MC_OK;
+}
+
+// CSR of D_g^T rebuilt in place.  Every pixel has at most four taps, so gate
+// g owns a fixed slice of 4 n^2 entries (ent_off[g] = 4 n^2 g) and a rebuild
+// after mc_set_field allocates nothing and moves no pointer.
+mc_status build_gate_csr(mc_ctx* c, int g)
+{
+    const int n = c->n, n2 = n * n;
+    const RigidGate* rg = c->d_rigid ? c->d_rigid + g : nullptr;
+    const float* fl = c->d_field ? c->d_field + (size_t)g * 2 * n2 : nullptr;
+    int* rp = c->d_rowptr + (size_t)g * (n2 + 1);
+    int2* ent = c->d_ent + (size_t)g * 4 * n2;
+    CK(cudaMemsetAsync(c->d_csr_cnt, 0, n2 * sizeof(int), c->stream));
+    CK(launch_csr_count(n, rg, fl, c->d_csr_cnt, c->stream));
+    CK(launch_exclusive_scan(c->d_csr_cnt, rp, n2, c->d_csr_scan, scan_scratch_len(n2), c->stream));
+    CK(cudaMemsetAsync(c->d_csr_cnt, 0, n2 * sizeof(int), c->stream));
+    CK(launch_csr_fill(n, rg, fl, rp, c->d_csr_cnt, ent, c->stream));
+    CK(launch_csr_sort(n, rp, ent, c->stream));
     return MC_OK;
 }
 
@@ -728,37 +762,15 @@ mc_status build_csr(mc_ctx* c)
 {
     const int n = c->n, N = c->N, n2 = n * n;
     TRY(dalloc(c, &c->d_rowptr, (size_t)N * (n2 + 1)));
-    int* cnt = nullptr;
-    const int sl = scan_scratch_len(n2);
-    int* scratch = nullptr;
-    TRY(dalloc(c, &cnt, n2));
-    TRY(dalloc(c, &scratch, sl));
-    std::vector<long long> off(N + 1, 0);
-    for (int g = 0; g < N; ++g) {
-        const RigidGate* rg = c->d_rigid ? c->d_rigid + g : nullptr;
-        const float* fl = c->d_field ? c->d_field + (size_t)g * 2 * n2 : nullptr;
-        int* rp = c->d_rowptr + (size_t)g * (n2 + 1);
-        CK(cudaMemsetAsync(cnt, 0, n2 * sizeof(int), c->stream));
-        CK(launch_csr_count(n, rg, fl, cnt, c->stream));
-        CK(launch_exclusive_scan(cnt, rp, n2, scratch, sl, c->stream));
-        int tot = 0;
-        CK(cudaMemcpyAsync(&tot, rp + n2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        CK(cudaStreamSynchronize(c->stream));
-        off[g + 1] = off[g] + tot;
-    }
-    c->nnz_total = off[N];
-    TRY(dalloc(c, &c->d_ent, (size_t)std::max<long long>(off[N], 1)));
+    TRY(dalloc(c, &c->d_ent, (size_t)N * 4 * n2));
     TRY(dalloc(c, &c->d_ent_off, N + 1));
+    TRY(dalloc(c, &c->d_csr_cnt, n2));
+    TRY(dalloc(c, &c->d_csr_scan, scan_scratch_len(n2)));
+    std::vector<long long> off(N + 1);
+    for (int g = 0; g <= N; ++g) off[g] = (long long)g * 4 * n2;
     CK(cudaMemcpyAsync(c->d_ent_off, off.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice,
                        c->stream));
-    for (int g = 0; g < N; ++g) {
-        const RigidGate* rg = c->d_rigid ? c->d_rigid + g : nullptr;
-        const float* fl = c->d_field ? c->d_field + (size_t)g * 2 * n2 : nullptr;
-        int* rp = c->d_rowptr + (size_t)g * (n2 + 1);
-        CK(cudaMemsetAsync(cnt, 0, n2 * sizeof(int), c->stream));
-        CK(launch_csr_fill(n, rg, fl, rp, cnt, c->d_ent + off[g], c->stream));
-        CK(launch_csr_sort(n, rp, c->d_ent + off[g], c->stream));
-    }
+    for (int g = 0; g < N; ++g) TRY(build_gate_csr(c, g));
     CK(cudaStreamSynchronize(c->stream));
     return MC_OK;
 }
@@ -1013,6 +1025,66 @@ mc_status mc_warp_adjoint(mc_ctx* c, int32_t gate, const float* v, float* out)
     a.out = o;
     TRY(launch(c, C_WADJ, "warp_adjoint", [&] { return launch_warp_adjoint_store(a, c->stream); }));
     TRY(stage_out(c, out, o, (size_t)c->n * c->n));
+    return finish(c);
+}
+
+mc_status mc_set_field(mc_ctx* c, int32_t gate, const float* field)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_gate(c, gate));
+    if (c->kind != MC_MOTION_FIELD)
+        return fail(c, MC_ESTATE, "mc_set_field needs a context created with dense-field motion");
+    if (!field) return fail(c, MC_EINVAL, "field is NULL");
+    TRY(load_field(c, gate, field, 0));
+    TRY(build_gate_csr(c, gate));
+    // A_gate changed: its norm, the step sizes and x* are stale
+    c->have_norms = false;
+    c->have_ref = false;
+    TRY(update_steps(c));
+    CK(cudaStreamSynchronize(c->stream));
+    return finish(c);
+}
+
+mc_status mc_vjp(mc_ctx* c, int32_t gate, const float* x, const float* r, float* grad_x,
+                 float* grad_field)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_gate(c, gate));
+    TRY(check_ptr(c, r, "r"));
+    if (!grad_x && !grad_field) return fail(c, MC_EINVAL, "grad_x and grad_field are both NULL");
+    if (grad_field) {
+        if (c->kind != MC_MOTION_FIELD)
+            return fail(c, MC_ESTATE, "grad_field needs a context created with dense-field motion");
+        TRY(check_ptr(c, x, "x"));
+        TRY(check_ptr(c, grad_field, "grad_field"));
+    }
+    if (grad_x) TRY(check_ptr(c, grad_x, "grad_x"));
+    const size_t n2 = (size_t)c->n * c->n;
+    const float* rd;
+    TRY(stage_in(c, r, c->d_sino_io, (size_t)c->na * c->nb, &rd));
+    TRY(pad_sinos(c, rd, 1));
+    TRY(backproject(c, 1, c->d_b));                       // b = A^T r
+    if (grad_x) {
+        const bool dev = ptr_kind(c, grad_x) == 1;
+        float* o = dev ? grad_x : c->d_img[1];
+        WarpAdjArgs a = wadj_args(c, GateSel{nullptr, gate}, 1, c->d_b);
+        a.out = o;
+        TRY(launch(c, C_WADJ, "warp_adjoint", [&] { return launch_warp_adjoint_store(a, c->stream); }));
+        TRY(stage_out(c, grad_x, o, n2));
+    }
+    if (grad_field) {
+        const float* xd;
+        TRY(stage_in(c, x, c->d_img[0], n2, &xd));
+        const bool dev = ptr_kind(c, grad_field) == 1;
+        float* o0 = dev ? grad_field : c->d_img[2];
+        float* o1 = dev ? grad_field + n2 : c->d_img[3];
+        const float* fl = c->d_field + (size_t)gate * 2 * n2;
+        TRY(launch(c, C_WARP, "field_vjp", [&] {
+            return launch_field_vjp(c->n, fl, xd, c->d_b, o0, o1, c->stream);
+        }));
+        TRY(stage_out(c, grad_field, o0, n2));
+        TRY(stage_out(c, grad_field + n2, o1, n2));
+    }
     return finish(c);
 }
 

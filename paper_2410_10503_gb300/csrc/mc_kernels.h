@@ -43,6 +43,10 @@ cudaError_t launch_csr_fill(int n, const RigidGate* rg, const float* field,
                             const int* rowptr, int* cursor, int2* ent, cudaStream_t s);
 cudaError_t launch_csr_sort(int n, const int* rowptr, int2* ent, cudaStream_t s);
 
+// ---- field VJP: out0/out1 = g * d(D_u x)/du_x, d(D_u x)/du_y (one gate) -----
+cudaError_t launch_field_vjp(int n, const float* field, const float* x, const float* g,
+                             float* out0, float* out1, cudaStream_t s);
+
 // ---- K5 (+K7): v = sum_slots D_gate^T b_slot, then store or update ----------
 struct WarpAdjArgs {
     int n;
