@@ -320,8 +320,8 @@ def _trace_entry(x, y, x_star, y_star):
 
 
 def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None,
-          x_star=None, y_star=None, literal: bool = False) -> RunResult:
-    """Algorithm 1 (SPDHG) with serial sampling of one gate per iteration.
+          x_star=None, y_star=None, literal: bool = False, subsets: int = 1) -> RunResult:
+    """Algorithm 1 (SPDHG) with serial sampling of one block per iteration.
 
     Standard reading (default):
       (i)   x^{k+1} = prox_{tau g}(x^k - tau zbar^k)
@@ -330,28 +330,72 @@ def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None
             zbar^{k+1} = z^{k+1} + (theta/p_i) A_i^*(y_i^{k+1} - y_i^k)
     ``literal=True`` runs the text as printed (step (i) with z^k, zbar
     accumulated on zbar^k); it is kept only as a negative test.
+
+    ``subsets = S > 1`` samples gates and angle subsets together (the
+    extension of Sec. IV): the blocks are j = 0 .. N S - 1 with gate j // S
+    and angle subset j % S, operator A_{i,s} (subset_op) and data term
+    N^-1 ||A_{i,s} x - d_{i,s}||^2, so the objective is unchanged; the draw
+    is uniform over the N S blocks (p_j = 1/(N S)) and an epoch is N S
+    iterations.  ``st`` then comes from step_sizes(max_j ||A_j||^2, alpha,
+    N, N S).  ``gates`` holds the drawn block indices.
     """
-    g, N = P.geom, P.N
-    probs = np.full(N, 1.0 / N) if p is None else np.asarray(p, dtype=np.float64) / np.sum(p)
-    K = epochs * N
-    gates = draw_gates(seed, stream, 0, K, N, p)
+    g, N, S = P.geom, P.N, int(subsets)
+    nblk = N * S
+    if S > 1 and p is not None:
+        raise ValueError("non-uniform sampling is defined over gates only")
+    probs = np.full(nblk, 1.0 / nblk) if p is None else np.asarray(p, dtype=np.float64) / np.sum(p)
+    K = epochs * nblk
+    blocks = draw_gates(seed, stream, 0, K, nblk, p)
     x = np.zeros((g.n, g.n)); z = np.zeros_like(x); zbar = np.zeros_like(x)
     y = np.zeros((N, g.na, g.nb))
-    res = RunResult(x, y, z, gates)
+    res = RunResult(x, y, z, blocks)
     res.trace.append(_trace_entry(x, y, x_star, y_star))
     for k in range(K):
         x = prox_g(x - st.tau * (z if literal else zbar), st.tau, P.alpha)      # (i)
-        i = int(gates[k])                                                        # (ii)
-        y_new = prox_fstar(y[i] + st.sigma[i] * Ai(x, P, i), st.sigma[i], P.d[i], N)
-        dz = Ait(y_new - y[i], P, i)
-        y[i] = y_new
+        j = int(blocks[k])                                                       # (ii)
+        i, s = divmod(j, S)
+        rows = subset_angles(g.na, S, s)
+        y_new = prox_fstar(y[i][rows] + st.sigma[i] * subset_op(x, P, i, S, s), st.sigma[i],
+                           P.d[i][rows], N)
+        dz = subset_adj(y_new - y[i][rows], P, i, S, s)
+        y[i][rows] = y_new
         z = z + dz                                                               # (iii)
-        zbar = (zbar + (1.0 + st.theta / probs[i]) * dz) if literal \
-            else (z + (st.theta / probs[i]) * dz)
-        if (k + 1) % N == 0:
+        zbar = (zbar + (1.0 + st.theta / probs[j]) * dz) if literal \
+            else (z + (st.theta / probs[j]) * dz)
+        if (k + 1) % nblk == 0:
             res.trace.append(_trace_entry(x, y, x_star, y_star))
     res.x, res.y, res.z = x, y, z
     return res
+
+
+# ------------------------------------------------------------ angle subsets
+def subset_angles(na: int, S: int, s: int) -> np.ndarray:
+    """Angle indices of subset s of S: k = s, s + S, s + 2S, ... (< na)."""
+    return np.arange(s, na, S)
+
+
+def subset_op(x, P: Problem, i: int, S: int, s: int) -> np.ndarray:
+    """A_{i,s} x: the rows of A_i x at the angles of subset s."""
+    return Ai(x, P, i)[subset_angles(P.geom.na, S, s)]
+
+
+def subset_adj(ys, P: Problem, i: int, S: int, s: int) -> np.ndarray:
+    """A_{i,s}^* ys = A_i^* (ys in the subset's rows, zero elsewhere)."""
+    full = np.zeros((P.geom.na, P.geom.nb))
+    full[subset_angles(P.geom.na, S, s)] = ys
+    return Ait(full, P, i)
+
+
+def block_norms2(P: Problem, S: int, iters: int = 200, tol: float = 1e-12) -> np.ndarray:
+    """[||A_{0,0}||^2, ||A_{0,1}||^2, ..., ||A_{N-1,S-1}||^2, ||(A_1; ...; A_N)||^2]:
+    block j = i S + s, then the stacked norm (unchanged by the split)."""
+    n = P.geom.n
+    out = [power_norm2(lambda v, i=i, s=s: subset_adj(subset_op(v, P, i, S, s), P, i, S, s),
+                       (n, n), iters, tol)
+           for i in range(P.N) for s in range(S)]
+    out.append(power_norm2(lambda v: sum(Ait(Ai(v, P, i), P, i) for i in range(P.N)),
+                           (n, n), iters, tol))
+    return np.array(out)
 
 
 def pdhg(P: Problem, epochs: int, st: Steps, x_star=None, y_star=None) -> RunResult:
