@@ -121,6 +121,22 @@ mc_status mc_backproject(mc_ctx* ctx, const float* y, float* out);
 mc_status mc_warp(mc_ctx* ctx, int32_t gate, const float* x, float* out);
 mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out);
 
+/* Sample gates and angle subsets together (the extension named in Sec. IV):
+ * split the angles into `subsets` = S interleaved subsets (subset s holds
+ * the angles k = s, s + S, s + 2S, ...; 1 <= S <= n_angles, S = 1 restores
+ * gate sampling).  SPDHG then works on the N S blocks j = i S + s with
+ * A_j = R_s A D_i (R_s keeps the rows of subset s) and data terms
+ * N^-1 ||A_j x - d_{i,s}||^2, so the objective O is unchanged; each iteration
+ * draws one block uniformly (p_j = 1/(N S), Philox as in mc_spdhg_run with
+ * i replaced by j in [0, N S)) and an epoch is N S iterations, the same
+ * operator work as N gate iterations.  After this call: mc_norms and
+ * mc_set_norms use N S + 1 values {||A_0||^2 .. ||A_{N S - 1}||^2, stacked
+ * norm}, SPDHG step sizes take kappa = max_j ||A_j||^2/(alpha N) and n = N S,
+ * and mc_draw_gates returns block indices.  The norms and step sizes are
+ * dropped (call mc_norms or mc_set_norms again); iterates are kept.  PDHG,
+ * the operators (mc_forward ...) and mc_objective are unaffected. */
+mc_status mc_set_subsets(mc_ctx* ctx, int32_t subsets);
+
 /* Replace the dense displacement field of one gate (Sec. II-A: D_i is the
  * pull-back warp by u_i).  field: 2 x n x n {ux (column), uy (row)} in px,
  * host or device, copied; values must be finite with |u| <= 1e5.  Rebuilds
@@ -148,11 +164,13 @@ mc_status mc_vjp(mc_ctx* ctx, int32_t gate, const float* x, const float* r, floa
  * reductions.  out (host or device, N+1 doubles): ||A_0||^2 .. ||A_{N-1}||^2,
  * then ||(A_0; ...; A_{N-1})||^2 = lambda_max(sum_i A_i^T A_i).  Stops per
  * norm after max_iter iterations or when the Rayleigh quotient changes by
- * less than tol (relative).  The result also sets the step sizes. */
+ * less than tol (relative).  The result also sets the step sizes.  After
+ * mc_set_subsets(S > 1) the first N S values are the block norms ||A_j||^2,
+ * j = i S + s, and out holds N S + 1 doubles. */
 mc_status mc_norms(mc_ctx* ctx, int32_t max_iter, double tol, double* out);
 
-/* Use these squared norms (N+1 doubles, same layout as mc_norms) for the
- * step sizes instead of running mc_norms. */
+/* Use these squared norms (same layout as mc_norms: N+1 doubles, or N S + 1
+ * with angle subsets) for the step sizes instead of running mc_norms. */
 mc_status mc_set_norms(mc_ctx* ctx, const double* norms2);
 
 /* Step sizes in use (host out, 5 doubles): {sigma, tau, theta, kappa, omega}

@@ -107,6 +107,7 @@ class Context:
         self._h = out.value
         self.kind = "rigid" if rigid is not None else "field"
         self._field_version = {}
+        self.subsets = 1
 
     # -- plumbing --------------------------------------------------------------
     def _check(self, st: int):
@@ -224,13 +225,25 @@ class Context:
         p, k = _arg(d, np.float32, self.n_gates * self.sino_count, "d")
         self._call(self._L.mc_set_data, p, float(alpha), cuda_args=(d,))
 
+    @property
+    def n_blocks(self) -> int:
+        """Sampled blocks: gates, or gates x angle subsets after set_subsets."""
+        return self.n_gates * self.subsets
+
+    def set_subsets(self, subsets: int):
+        """Sample gates x `subsets` interleaved angle subsets (mc_set_subsets);
+        drops the norms and step sizes."""
+        self._check(self._L.mc_set_subsets(self._h, int(subsets)))
+        self.subsets = int(subsets)
+
     def norms(self, max_iter: int = 200, tol: float = 1e-6) -> np.ndarray:
-        out = np.empty(self.n_gates + 1)
+        """[||A_j||^2 per block, stacked ||(A_1; ...; A_N)||^2] (mc_norms)."""
+        out = np.empty(self.n_blocks + 1)
         self._check(self._L.mc_norms(self._h, max_iter, tol, out.ctypes.data))
         return out
 
     def set_norms(self, norms2):
-        p, k = _arg(norms2, np.float64, self.n_gates + 1, "norms2")
+        p, k = _arg(norms2, np.float64, self.n_blocks + 1, "norms2")
         self._check(self._L.mc_set_norms(self._h, p))
 
     def steps(self, pdhg: bool = False) -> dict:

@@ -40,6 +40,7 @@ SIGNATURES = {
     "mc_backproject": (_I32, [_VP, _VP, _VP]),
     "mc_warp": (_I32, [_VP, _I32, _VP, _VP]),
     "mc_warp_adjoint": (_I32, [_VP, _I32, _VP, _VP]),
+    "mc_set_subsets": (_I32, [_VP, _I32]),
     "mc_set_field": (_I32, [_VP, _I32, _VP]),
     "mc_vjp": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP]),
     "mc_norms": (_I32, [_VP, _I32, _D, _VP]),

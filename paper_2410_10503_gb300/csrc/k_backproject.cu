@@ -66,8 +66,10 @@ __device__ __forceinline__ float2 lds64(uint32_t addr)
 
 // Issue the window copies of one chunk (warp 0; lane i handles angles i, i+32...).
 // Window of angle k: WL pairs of dy row k starting at ws (even, so the copy is
-// 16-byte aligned), covering every bin the tile's pixels project onto.
-__device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, int k0, int cnt, int wl,
+// 16-byte aligned), covering every bin the tile's pixels project onto.  The
+// chunk's angles are k = sub + (k0 + i) * S (one angle subset; S = 1: all).
+__device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, int sub, int S, int k0,
+                                            int cnt, int wl,
                                             float xmin, float xmax, float ymin, float ymax,
                                             float2* buf, int* ws_out, uint64_t* bar)
 {
@@ -80,7 +82,8 @@ __device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, 
     __syncwarp();
     const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
     for (int i = lane; i < cnt; i += 32) {
-        const BpAngle T = a.ang[k0 + i];
+        const int k = sub + (k0 + i) * S;
+        const BpAngle T = a.ang[k];
         const float cs = T.cos_hi, sn = T.sin_hi;
         const float b1 = fminf(xmin * cs, xmax * cs) + fminf(ymin * sn, ymax * sn) + offb;
         int ws = ((int)floorf(b1) - 2) & ~1;
@@ -90,7 +93,7 @@ __device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, 
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(buf + (size_t)i * wl)),
-            "l"(dys + (size_t)(k0 + i) * a.Pb + ws), "r"((uint32_t)(wl * sizeof(float2))), "r"(smem_u32(bar))
+            "l"(dys + (size_t)k * a.Pb + ws), "r"((uint32_t)(wl * sizeof(float2))), "r"(smem_u32(bar))
             : "memory");
     }
 }
@@ -118,7 +121,11 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     // tile extent in centred coordinates (columns past the image are clamped)
     const float xmin = (float)(blockIdx.x * 32) - h, xmax = (float)min(blockIdx.x * 32 + 31, n - 1) - h;
     const float ymin = Y0, ymax = Y0 + (float)(PJ - 1);
-    const int nck = (a.na + kChunk - 1) / kChunk;
+    // angles of this launch: one angle subset of the drawn block, or all
+    const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;
+    const int sub = sel_subset(a.sel, slot);
+    const int na_s = (a.na - sub + S - 1) / S;
+    const int nck = (na_s + kChunk - 1) / kChunk;
 
     if (threadIdx.x == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[0])) : "memory");
@@ -127,7 +134,8 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     }
     __syncthreads();
     if (g == 0)
-        issue_chunk(a, dys, 0, min(kChunk, a.na), wl, xmin, xmax, ymin, ymax, s_win, s_ws, &full[0]);
+        issue_chunk(a, dys, sub, S, 0, min(kChunk, na_s), wl, xmin, xmax, ymin, ymax, s_win, s_ws,
+                    &full[0]);
 
     float acc[PJ];
 #pragma unroll
@@ -136,12 +144,13 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     for (int ch = 0; ch < nck; ++ch) {
         const int buf = ch & 1;
         const int k0 = ch * kChunk;
-        const int cnt = min(kChunk, a.na - k0);
+        const int cnt = min(kChunk, na_s - k0);
         // angle table of this chunk, and the next chunk's windows in flight
-        for (int i = threadIdx.x; i < cnt; i += 256) s_ang[buf * kChunk + i] = a.ang[k0 + i];
+        for (int i = threadIdx.x; i < cnt; i += 256) s_ang[buf * kChunk + i] = a.ang[sub + (k0 + i) * S];
         if (g == 0 && ch + 1 < nck)
-            issue_chunk(a, dys, k0 + kChunk, min(kChunk, a.na - k0 - kChunk), wl, xmin, xmax, ymin, ymax,
-                        s_win + (size_t)(buf ^ 1) * kChunk * wl, s_ws + (buf ^ 1) * kChunk, &full[buf ^ 1]);
+            issue_chunk(a, dys, sub, S, k0 + kChunk, min(kChunk, na_s - k0 - kChunk), wl, xmin, xmax, ymin,
+                        ymax, s_win + (size_t)(buf ^ 1) * kChunk * wl, s_ws + (buf ^ 1) * kChunk,
+                        &full[buf ^ 1]);
         __syncthreads();
         if (!mbar_wait(&full[buf], (uint32_t)((ch >> 1) & 1), kWaitLimit)) {
             // a copy never landed: report, then give the other stage a bounded chance to land

@@ -85,11 +85,6 @@ constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
 constexpr int kBlock = kThreads + 32;        // plus one producer warp
 constexpr int kStages = 5;
 
-__device__ __forceinline__ int gate_of(const GateSel& s, int slot)
-{
-    return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
-}
-
 // Samples of one ray over the LC lines of a staged chunk.  The magic
 // constant of line j is kMagic + j * P: adding it with round-down leaves
 // floor(w) + j * P in the low mantissa bits, so the shared address of the pair
@@ -145,8 +140,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     const int slot = blockIdx.y;
     const int n = a.n, nb = a.nb;
     const int nch = (n + LC - 1) / LC;
+    // this launch's item table: all angles, or the drawn block's angle subset
+    const int sub = sel_subset(a.sel, slot);
+    const RayItem* items = a.sub_off ? a.items + a.sub_off[sub] : a.items;
+    const int n_items = a.sub_off ? a.sub_off[sub + 1] - a.sub_off[sub] : a.n_items;
     const int it0 = blockIdx.x * a.ipb;
-    const int n_it = min(a.ipb, a.n_items - it0);
+    const int n_it = min(a.ipb, n_items - it0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -164,7 +163,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         if (lane == 0) {
             for (int g = 0; g < n_it * nch; ++g) {
                 const int it = g / nch, c = g - it * nch;
-                const float2* src = (a.items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
+                const float2* src = (items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
                 const int st = g % kStages;
                 if (g >= kStages &&
                     !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), kWaitLimit)) {
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     }
 
     // ---- consumers ------------------------------------------------------------
-    const int gate = gate_of(a.sel, slot);
+    const int gate = sel_gate(a.sel, slot);
     const float h = 0.5f * (float)(n - 1);
     const float hb = 0.5f * (float)(nb - 1);
     const float off = h + (float)kGuard;
@@ -193,7 +192,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     GroupState* my = s_grp + warp * RPT;
 
     for (int it = 0; it < n_it; ++it) {
-        const RayItem item = a.items[it0 + it];
+        const RayItem item = items[it0 + it];
         // this warp's groups: item.begin + warp + m * kConsumers
         const int ns = max(0, min(RPT, (item.end - item.begin - warp + kConsumers - 1) / kConsumers));
         float frac[RPT], acc[RPT];

@@ -5,11 +5,6 @@
 
 namespace mcg {
 
-__device__ __forceinline__ int gate_of(const GateSel& s, int slot)
-{
-    return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
-}
-
 // Bilinear pull-back sample (D x)(r, c); weights are the products
 // (1-fr or fr) * (1-fc or fc), rounded once, exactly as stored in the CSR.
 __device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
@@ -42,7 +37,7 @@ __global__ void __launch_bounds__(256) k_warp_layouts(WarpArgs a)
 {
     __shared__ float w_s[33][34];
     const int slot = blockIdx.z;
-    const int gate = gate_of(a.sel, slot);
+    const int gate = sel_gate(a.sel, slot);
     const int n = a.n;
     const RigidGate* rg = a.rigid ? a.rigid + gate : nullptr;
     const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
@@ -87,7 +82,7 @@ __global__ void __launch_bounds__(256) k_warp_layouts(WarpArgs a)
 __global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
 {
     const int slot = blockIdx.z;
-    const int gate = gate_of(a.sel, slot);
+    const int gate = sel_gate(a.sel, slot);
     const int n = a.n;
     const RigidGate* rg = a.rigid ? a.rigid + gate : nullptr;
     const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
@@ -314,7 +309,7 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
     if (q >= n2) return;
     float v = 0.0f;
     for (int s = 0; s < a.n_slots; ++s) {
-        const int gate = gate_of(a.sel, s);
+        const int gate = sel_gate(a.sel, s);
         const int* rp = a.rowptr + (size_t)gate * (n2 + 1);
         const int2* ent = a.ent + a.ent_off[gate];
         const float* b = a.b + (size_t)s * n2;

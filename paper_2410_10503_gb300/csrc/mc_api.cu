@@ -6,6 +6,7 @@
 // CUDA graphs.  No computation of the method runs on the host: every step
 // is one of the kernels in k_*.cu.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -76,6 +77,15 @@ struct mc_ctx {
     RayItem* d_items = nullptr;
     int n_items = 0, ipb = 1, rpt = 1, lc = 1, P = 0, Gb = 0, Pb = 0, pj = 4;
     size_t layout_stride = 0, dy_stride = 0;
+    std::vector<int> order;           // angles, rows-driven first
+    std::vector<double> inv_k, t_k;   // per angle: 1/|sin| or 1/|cos|, and the slope
+
+    // sampling over gates x angle subsets: S subsets, blocks j = gate * S + s
+    int S = 1;
+    int2* d_sgroups = nullptr;
+    RayItem* d_sitems = nullptr;
+    int* d_soff = nullptr;
+    int s_nitems = 0, s_ipb = 1, s_rpt = 2;
 
     // motion and D_i^T
     int kind = 0;
@@ -108,6 +118,7 @@ struct mc_ctx {
     // control and reductions
     unsigned long long* d_k = nullptr;
     int* d_gates = nullptr;
+    int gates_cap = 0;
     int* d_err = nullptr;
     int* d_draw_out = nullptr;
     int draw_cap = 0;
@@ -196,6 +207,19 @@ mc_status dalloc(mc_ctx* c, T** p, size_t count)
     if (e != cudaSuccess) return fail(c, MC_ECUDA, "cudaMemsetAsync failed: %s", cudaGetErrorString(e));
     *p = static_cast<T*>(q);
     return MC_OK;
+}
+
+// free one dalloc'd buffer early (stream work using it must have finished)
+template <class T>
+void dfree(mc_ctx* c, T** p)
+{
+    if (!*p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), (void*)*p);
+    if (it != c->allocs.end()) {
+        cudaFree(*it);
+        c->allocs.erase(it);
+    }
+    *p = nullptr;
 }
 
 // 1 = device memory of this context's device, 0 = host, -1 = other device
@@ -305,6 +329,10 @@ FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
     a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
     a.ang = c->d_fang; a.groups = c->d_groups; a.items = c->d_items; a.n_items = c->n_items;
     a.ipb = c->ipb; a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
+    if (sel.subsets > 1) {            // the drawn block's angle subset
+        a.groups = c->d_sgroups; a.items = c->d_sitems; a.sub_off = c->d_soff;
+        a.n_items = c->s_nitems; a.ipb = c->s_ipb; a.rpt = c->s_rpt;
+    }
     a.sel = sel; a.n_slots = n_slots;
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
     a.err = c->d_err;
@@ -318,9 +346,10 @@ mc_status project_store(mc_ctx* c, GateSel sel, int n_slots, float* out)
     return launch(c, C_PROJ, "project", [&] { return launch_forward(a, c->stream); });
 }
 
-mc_status backproject(mc_ctx* c, int n_slots, float* out)
+mc_status backproject(mc_ctx* c, GateSel sel, int n_slots, float* out)
 {
     BpArgs a{};
+    a.sel = sel;
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
     a.ang = c->d_bang; a.n = c->n; a.na = c->na; a.nb = c->nb; a.n_slots = n_slots;
     a.pj = c->pj; a.out = out; a.err = c->d_err;
@@ -357,7 +386,7 @@ mc_status reduce(mc_ctx* c, const float* a, const float* b, size_t len, int mode
 // A_i^* applied to N_slots sinograms (already padded in d_dy), summed, into out
 mc_status adjoint_from_dy(mc_ctx* c, GateSel sel, int n_slots, float* out)
 {
-    TRY(backproject(c, n_slots, c->d_b));
+    TRY(backproject(c, sel, n_slots, c->d_b));
     WarpAdjArgs a = wadj_args(c, sel, n_slots, c->d_b);
     a.out = out;
     return launch(c, C_WADJ, "warp_adjoint", [&] { return launch_warp_adjoint_store(a, c->stream); });
@@ -366,24 +395,24 @@ mc_status adjoint_from_dy(mc_ctx* c, GateSel sel, int n_slots, float* out)
 // ---- one epoch --------------------------------------------------------------
 mc_status enqueue_spdhg_epoch(mc_ctx* c, uint64_t seed, uint32_t stream)
 {
-    const int N = c->N;
+    const int N = c->N, nblk = N * c->S;     // blocks: gates, or gates x angle subsets
     TRY(launch(c, C_DRAW, "draw_gates", [&] {
-        return launch_draw_gates(seed, stream, c->d_k, 0, N, N, c->d_gates, c->stream);
+        return launch_draw_gates(seed, stream, c->d_k, 0, nblk, nblk, c->d_gates, c->stream);
     }));
     const float sigma = (float)c->sS.sigma;
     const float inv_den = (float)(1.0 / (1.0 + c->sS.sigma * N / 2.0));
-    for (int j = 0; j < N; ++j) {
-        const GateSel sel{c->d_gates + j, -1};
+    for (int j = 0; j < nblk; ++j) {
+        const GateSel sel{c->d_gates + j, -1, c->S};
         float* xin = c->d_x[c->cur];
         float* xout = c->d_x[c->cur ^ 1];
         TRY(warp_into_layouts(c, xin, sel, 1, false));
         FwdArgs fa = fwd_args(c, sel, 1);
         fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y; fa.sigma = sigma; fa.inv_den = inv_den;
         TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
-        TRY(backproject(c, 1, c->d_b));
+        TRY(backproject(c, sel, 1, c->d_b));
         WarpAdjArgs wa = wadj_args(c, sel, 1, c->d_b);
         wa.z = c->d_z; wa.x_in = xin; wa.x_out = xout;
-        wa.coef = (float)(c->sS.theta * N);               // theta / p_i, p_i = 1/N
+        wa.coef = (float)(c->sS.theta * nblk);            // theta / p_j, p_j = 1/(N S)
         wa.tau = (float)c->sS.tau;
         wa.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sS.tau * c->alpha));
         TRY(launch(c, C_WADJ, "warp_adjoint_update", [&] {
@@ -406,7 +435,7 @@ mc_status enqueue_pdhg_iter(mc_ctx* c)
     fa.sigma = (float)c->sP.sigma;
     fa.inv_den = (float)(1.0 / (1.0 + c->sP.sigma * N / 2.0));
     TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
-    TRY(backproject(c, N, c->d_b));
+    TRY(backproject(c, sel, N, c->d_b));
     WarpAdjArgs wa = wadj_args(c, sel, N, c->d_b);
     wa.z = c->d_z; wa.x_in = xin; wa.x_out = xout;
     wa.coef = (float)c->sP.theta;                          // p_i = 1
@@ -423,7 +452,7 @@ mc_status run_epoch(mc_ctx* c, int which, uint64_t seed, uint32_t stream)
     auto enqueue = [&]() -> mc_status {
         return which == 0 ? enqueue_spdhg_epoch(c, seed, stream) : enqueue_pdhg_iter(c);
     };
-    const int flips = (which == 0) ? (c->N & 1) : 1;
+    const int flips = (which == 0) ? ((c->N * c->S) & 1) : 1;
     if (!c->graph_on || c->prof_on) return enqueue();
     const int par = c->cur;
     if (which == 0 && c->gexec[0][par] && (c->g_seed[0] != seed || c->g_stream[0] != stream)) {
@@ -490,15 +519,16 @@ mc_status update_steps(mc_ctx* c)
         drop_graphs(c);
         return MC_OK;
     }
+    const int nblk = c->N * c->S;
     double mx = 0;
-    for (int i = 0; i < c->N; ++i) mx = std::max(mx, c->norms2[i]);
-    if (!(mx > 0) || !(c->norms2[c->N] > 0)) {
+    for (int i = 0; i < nblk; ++i) mx = std::max(mx, c->norms2[i]);
+    if (!(mx > 0) || !(c->norms2[nblk] > 0)) {
         c->steps_ok = false;
         drop_graphs(c);
         return fail(c, MC_EINVAL, "operator norms must be positive");
     }
-    const Steps s = make_steps(mx, c->alpha, c->N, c->N);
-    const Steps p = make_steps(c->norms2[c->N], c->alpha, c->N, 1);
+    const Steps s = make_steps(mx, c->alpha, c->N, nblk);
+    const Steps p = make_steps(c->norms2[nblk], c->alpha, c->N, 1);
     // captured epochs bake the steps into their kernel arguments
     auto same = [](const Steps& a, const Steps& b) {
         return a.sigma == b.sigma && a.tau == b.tau && a.theta == b.theta;
@@ -561,6 +591,87 @@ long long ray_samples(int n, double hb, double inv, double t, int b)
     return hi >= lo ? hi - lo + 1 : 0;
 }
 
+// Ray groups of the forward projector (up to 32 consecutive bins of one
+// angle) for S interleaved angle subsets: subset s holds the angles k = s
+// (mod S), rows-driven angles first; its groups are sets[s] = {first,
+// first columns-driven, end}.  cum holds running sample weights (a fixed
+// setup cost per group plus its in-image samples).
+struct GroupTable {
+    std::vector<int2> groups;
+    std::vector<long long> cum;
+    std::vector<std::array<long long, 3>> sets;
+};
+
+void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vector<double>& inv_k,
+                  const std::vector<double>& t_k, int S, GroupTable& gt)
+{
+    const int n = c->n, na = c->na, nb = c->nb;
+    const double hb = 0.5 * (nb - 1);
+    const int gpa = (nb + 31) / 32;                        // groups per angle
+    gt.groups.clear();
+    gt.cum.assign(1, 0);
+    gt.sets.clear();
+    gt.groups.reserve((size_t)na * gpa);
+    gt.cum.reserve((size_t)na * gpa + 1);
+    for (int sub = 0; sub < S; ++sub) {
+        std::array<long long, 3> set{(long long)gt.groups.size(), -1, 0};
+        for (int k : order) {
+            if (k % S != sub) continue;
+            const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
+            if (xd && set[1] < 0) set[1] = (long long)gt.groups.size();
+            for (int g = 0; g < gpa; ++g) {
+                long long w = 64;
+                for (int b = g * 32; b < std::min(nb, g * 32 + 32); ++b)
+                    w += ray_samples(n, hb, inv_k[k], t_k[k], b);
+                gt.groups.push_back(make_int2(k, g * 32));
+                gt.cum.push_back(gt.cum.back() + w);
+            }
+        }
+        set[2] = (long long)gt.groups.size();
+        if (set[1] < 0) set[1] = set[2];
+        gt.sets.push_back(set);
+    }
+}
+
+// Cut every set into about ipb * sms items of equal weight (each driving-axis
+// class separately: an item streams one line layout); the smallest ipb whose
+// items hold at most kConsumers * rpt groups, rpt in {2, 4, 8}.  Items of set
+// s are items[set_off[s] .. set_off[s+1]).
+void partition_items(const GroupTable& gt, int sms, std::vector<RayItem>& items, std::vector<int>& set_off,
+                     int& ipb, int& rpt)
+{
+    const std::vector<long long>& cum = gt.cum;
+    for (ipb = 1;; ++ipb) {
+        const int target = ipb * sms;
+        items.clear();
+        set_off.assign(1, 0);
+        long long max_groups = 0;
+        for (const auto& set : gt.sets) {
+            const double total = (double)(cum[set[2]] - cum[set[0]]);
+            for (int cls = 0; cls < 2; ++cls) {
+                const long long b0 = cls == 0 ? set[0] : set[1], b1 = cls == 0 ? set[1] : set[2];
+                if (b1 <= b0) continue;
+                const double w = (double)(cum[b1] - cum[b0]);
+                const int cnt = std::max(1, (int)std::lround(target * w / total));
+                long long st = b0;
+                for (int i = 1; i <= cnt && st < b1; ++i) {
+                    const long long goal = cum[b0] + (long long)std::llround(w * i / cnt);
+                    long long e = std::lower_bound(cum.begin() + st + 1, cum.begin() + b1 + 1, goal) - cum.begin();
+                    e = std::min(std::max(e, st + 1), b1);
+                    if (i == cnt) e = b1;
+                    items.push_back(RayItem{(int)st, (int)e, cls, 0});
+                    max_groups = std::max(max_groups, e - st);
+                    st = e;
+                }
+            }
+            set_off.push_back((int)items.size());
+        }
+        rpt = 2;
+        while (rpt < 8 && forward_groups_per_block(rpt) < max_groups) rpt <<= 1;
+        if (forward_groups_per_block(rpt) >= max_groups) return;
+    }
+}
+
 mc_status build_tables(mc_ctx* c)
 {
     const int n = c->n, na = c->na, nb = c->nb;
@@ -612,50 +723,16 @@ mc_status build_tables(mc_ctx* c)
     // forward ray groups: up to 32 consecutive bins of one angle, rows-driven
     // angles first; work items cut each axis class into group ranges with
     // equal sample counts; one block per SM takes ipb consecutive items
-    const double hb = 0.5 * (nb - 1);
-    const int gpa = (nb + 31) / 32;                        // groups per angle
-    std::vector<int2> groups;
-    std::vector<long long> cum(1, 0);
-    groups.reserve((size_t)na * gpa);
-    cum.reserve((size_t)na * gpa + 1);
-    for (int o = 0; o < na; ++o) {
-        const int k = order[o];
-        for (int g = 0; g < gpa; ++g) {
-            long long w = 64;                              // per-group setup cost
-            for (int b = g * 32; b < std::min(nb, g * 32 + 32); ++b)
-                w += ray_samples(n, hb, inv_k[k], t_k[k], b);
-            groups.push_back(make_int2(k, g * 32));
-            cum.push_back(cum.back() + w);
-        }
-    }
-    const long long g_y = (long long)ny * gpa, g_all = (long long)na * gpa;
+    c->order = order;
+    c->inv_k = inv_k;
+    c->t_k = t_k;
+    GroupTable gt;
+    build_groups(c, order, inv_k, t_k, 1, gt);
     std::vector<RayItem> items;
+    std::vector<int> set_off;
     int rpt = 2, ipb = 1;
-    for (;; ++ipb) {
-        const int target = ipb * c->sms;
-        items.clear();
-        long long max_groups = 0;
-        const double total = (double)cum[g_all];
-        for (int cls = 0; cls < 2; ++cls) {
-            const long long b0 = cls == 0 ? 0 : g_y, b1 = cls == 0 ? g_y : g_all;
-            if (b1 <= b0) continue;
-            const double w = (double)(cum[b1] - cum[b0]);
-            const int cnt = std::max(1, (int)std::lround(target * w / total));
-            long long s = b0;
-            for (int i = 1; i <= cnt && s < b1; ++i) {
-                const long long goal = cum[b0] + (long long)std::llround(w * i / cnt);
-                long long e = std::lower_bound(cum.begin() + s + 1, cum.begin() + b1 + 1, goal) - cum.begin();
-                e = std::min(std::max(e, s + 1), b1);
-                if (i == cnt) e = b1;
-                items.push_back(RayItem{(int)s, (int)e, cls, 0});
-                max_groups = std::max(max_groups, e - s);
-                s = e;
-            }
-        }
-        rpt = 2;
-        while (rpt < 8 && forward_groups_per_block(rpt) < max_groups) rpt <<= 1;
-        if (forward_groups_per_block(rpt) >= max_groups) break;
-    }
+    partition_items(gt, c->sms, items, set_off, ipb, rpt);
+    const std::vector<int2>& groups = gt.groups;
     c->ipb = ipb;
     c->rpt = rpt;
     c->n_items = (int)items.size();
@@ -678,7 +755,7 @@ mc_status build_tables(mc_ctx* c)
         if (warps >= 24LL * c->sms) { c->pj = pj; break; }
     }
     // dual increment layout: guards wide enough for every pixel's two bins
-    const double h = 0.5 * (n - 1);
+    const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
     const int pj_max = 16;
     c->Gb = std::max(2, (int)std::ceil(std::sqrt(2.0) * (h + pj_max + 1) - hb) + 2);
     c->Pb = (nb + 2 * c->Gb + 2 + 3) / 4 * 4;
@@ -793,6 +870,7 @@ mc_status alloc_state(mc_ctx* c)
     TRY(dalloc(c, &c->d_sino_io, ns));
     TRY(dalloc(c, &c->d_k, 1));
     TRY(dalloc(c, &c->d_gates, std::max(N, 1)));
+    c->gates_cap = std::max(N, 1);
     TRY(dalloc(c, &c->d_err, 1));
     TRY(dalloc(c, &c->d_part, reduce_parts()));
     TRY(dalloc(c, &c->d_s, S_RES + N + 8));
@@ -988,7 +1066,7 @@ mc_status mc_backproject(mc_ctx* c, const float* y, float* out)
     TRY(pad_sinos(c, yd, 1));
     const bool dev_out = ptr_kind(c, out) == 1;
     float* o = dev_out ? out : c->d_img[1];
-    TRY(backproject(c, 1, o));
+    TRY(backproject(c, GateSel{nullptr, 0}, 1, o));
     TRY(stage_out(c, out, o, (size_t)c->n * c->n));
     return finish(c);
 }
@@ -1028,6 +1106,53 @@ mc_status mc_warp_adjoint(mc_ctx* c, int32_t gate, const float* v, float* out)
     return finish(c);
 }
 
+mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
+{
+    if (!c) return MC_EINVAL;
+    if (subsets < 1 || subsets > c->na)
+        return fail(c, MC_EINVAL, "subsets must be in [1, n_angles = %d], got %d", c->na, subsets);
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    dfree(c, &c->d_sgroups);
+    dfree(c, &c->d_sitems);
+    dfree(c, &c->d_soff);
+    c->S = 1;
+    c->have_norms = false;
+    if (subsets > 1) {
+        // forward work items per angle subset, one table, subset s at soff[s]
+        GroupTable gt;
+        build_groups(c, c->order, c->inv_k, c->t_k, subsets, gt);
+        std::vector<RayItem> items;
+        std::vector<int> off;
+        int ipb = 1, rpt = 2;
+        partition_items(gt, c->sms, items, off, ipb, rpt);
+        int most = 0;
+        for (int q = 0; q < subsets; ++q) most = std::max(most, off[q + 1] - off[q]);
+        TRY(dalloc(c, &c->d_sgroups, gt.groups.size()));
+        TRY(dalloc(c, &c->d_sitems, items.size()));
+        TRY(dalloc(c, &c->d_soff, off.size()));
+        CK(cudaMemcpyAsync(c->d_sgroups, gt.groups.data(), gt.groups.size() * sizeof(int2),
+                           cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->d_sitems, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
+                           c->stream));
+        CK(cudaMemcpyAsync(c->d_soff, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        c->s_nitems = most;
+        c->s_ipb = ipb;
+        c->s_rpt = rpt;
+    }
+    const int nblk = c->N * subsets;
+    if (nblk > c->gates_cap) {
+        dfree(c, &c->d_gates);
+        TRY(dalloc(c, &c->d_gates, nblk));
+        c->gates_cap = nblk;
+    }
+    c->S = subsets;
+    TRY(update_steps(c));
+    CK(cudaStreamSynchronize(c->stream));
+    return finish(c);
+}
+
 mc_status mc_set_field(mc_ctx* c, int32_t gate, const float* field)
 {
     if (!c) return MC_EINVAL;
@@ -1063,7 +1188,7 @@ mc_status mc_vjp(mc_ctx* c, int32_t gate, const float* x, const float* r, float*
     const float* rd;
     TRY(stage_in(c, r, c->d_sino_io, (size_t)c->na * c->nb, &rd));
     TRY(pad_sinos(c, rd, 1));
-    TRY(backproject(c, 1, c->d_b));                       // b = A^T r
+    TRY(backproject(c, GateSel{nullptr, gate}, 1, c->d_b));     // b = A^T r
     if (grad_x) {
         const bool dev = ptr_kind(c, grad_x) == 1;
         float* o = dev ? grad_x : c->d_img[1];
@@ -1096,11 +1221,12 @@ mc_status mc_norms(mc_ctx* c, int32_t max_iter, double tol, double* out)
     const size_t n2 = (size_t)c->n * c->n;
     float* v = c->d_img[2];
     float* w = c->d_img[3];
-    std::vector<double> res(c->N + 1, 0.0);
-    for (int which = 0; which <= c->N; ++which) {
-        const bool stacked = which == c->N;
+    const int nblk = c->N * c->S;
+    std::vector<double> res(nblk + 1, 0.0);
+    for (int which = 0; which <= nblk; ++which) {
+        const bool stacked = which == nblk;
         const int slots = stacked ? c->N : 1;
-        const GateSel sel = stacked ? GateSel{nullptr, -1} : GateSel{nullptr, which};
+        const GateSel sel = stacked ? GateSel{nullptr, -1} : GateSel{nullptr, which, c->S};
         // v = constant image of unit norm
         std::vector<float> ones(n2, (float)(1.0 / std::sqrt((double)n2)));
         CK(cudaMemcpyAsync(v, ones.data(), n2 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
@@ -1141,7 +1267,7 @@ mc_status mc_set_norms(mc_ctx* c, const double* norms2)
 {
     if (!c) return MC_EINVAL;
     if (!norms2) return fail(c, MC_EINVAL, "norms2 is NULL");
-    std::vector<double> v(c->N + 1);
+    std::vector<double> v(c->N * c->S + 1);
     if (ptr_kind(c, norms2) == 1) {
         CK(cudaMemcpy(v.data(), norms2, v.size() * sizeof(double), cudaMemcpyDeviceToHost));
     } else {
@@ -1271,7 +1397,7 @@ static mc_status run_common(mc_ctx* c, int which, int32_t epochs, const mc_sampl
     const uint32_t strm = smp ? smp->stream : 0;
     for (int e = 0; e < epochs; ++e) {
         TRY(run_epoch(c, which, seed, strm));
-        if (which == 0) c->k_host += (uint64_t)c->N;
+        if (which == 0) c->k_host += (uint64_t)c->N * c->S;
         if (trace) TRY(enqueue_trace(c, e));
     }
     if (x_out) TRY(stage_out(c, x_out, c->d_x[c->cur ^ 1], (size_t)c->n * c->n));
@@ -1319,7 +1445,7 @@ mc_status mc_draw_gates(mc_ctx* c, const mc_sampling* smp, uint64_t k0, int32_t 
         o = c->d_draw_out;
     }
     TRY(launch(c, C_DRAW, "draw_gates", [&] {
-        return launch_draw_gates(smp->seed, smp->stream, nullptr, k0, count, c->N, o, c->stream);
+        return launch_draw_gates(smp->seed, smp->stream, nullptr, k0, count, c->N * c->S, o, c->stream);
     }));
     if (!dev) {
         CK(cudaMemcpyAsync(out, o, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));

@@ -8,12 +8,31 @@
 
 namespace mcg {
 
-// Which gate a gate slot works on: list[slot] if list, else fixed if >= 0,
-// else the slot index itself (PDHG: slot i is gate i).
+// Which block a gate slot works on: list[slot] if list, else fixed if >= 0,
+// else the slot index itself (PDHG: slot i is gate i).  With subsets = S > 1
+// the value is a block j of the gate x angle-subset split: gate j / S, angle
+// subset j % S (angles k = j % S + m S); subsets <= 1 means plain gates.
 struct GateSel {
     const int* list;
     int fixed;
+    int subsets;
 };
+
+__device__ __forceinline__ int sel_block(const GateSel& s, int slot)
+{
+    return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
+}
+
+__device__ __forceinline__ int sel_gate(const GateSel& s, int slot)
+{
+    const int v = sel_block(s, slot);
+    return s.subsets > 1 ? v / s.subsets : v;
+}
+
+__device__ __forceinline__ int sel_subset(const GateSel& s, int slot)
+{
+    return s.subsets > 1 ? sel_block(s, slot) % s.subsets : 0;
+}
 
 // ---- K1: warp w = D_i x into the two line layouts (or a plain image) ------
 struct WarpArgs {
@@ -78,7 +97,9 @@ struct FwdArgs {
     const FwdAngle* ang;
     const int2* groups;        // ray groups {angle k, first bin}, rows-driven first
     const RayItem* items;      // group ranges
-    int n_items;
+    int n_items;               // items (the largest subset's count when sub_off is set)
+    const int* sub_off;        // angle-subset tables: items of subset s are
+                               // items[sub_off[s] .. sub_off[s+1]), or null
     int ipb;                   // items per block (one block per SM)
     int rpt;                   // group slots per consumer warp (2, 4, 8)
     int lc;                    // lines per staged chunk (2, 4, 8)
@@ -103,6 +124,7 @@ cudaError_t forward_prepare(int max_smem);
 
 // ---- K4: pixel-driven gather backprojection ---------------------------------
 struct BpArgs {
+    GateSel sel;               // only the angle subset is used (all angles if subsets <= 1)
     const float2* dy;          // pairs, slot stride dy_stride, pitch Pb, guard Gb
     size_t dy_stride;
     int Pb, Gb;
