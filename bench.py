@@ -308,13 +308,15 @@ def run_ncu_case(args, W):
     for i in range(W.n_gates):
         ctx.forward(i, x_t, out=d[i])
     ctx.set_data(d, W.alpha)
-    ctx.set_norms(np.full(W.n_gates + 1, 3.5e5))
+    if args.subsets > 1:
+        ctx.set_subsets(args.subsets)
+    ctx.set_norms(np.full(ctx.n_blocks + 1, 3.5e5 / args.subsets))
     ctx.set_option(1, 0)
     for _ in range(args.warmup + args.steps):
         ctx.spdhg_run(1, seed=sd["gates"], x_out=False)
     torch.cuda.synchronize()
     ctx.close()
-    print(json.dumps({"ncu_case": W.name, "epochs": args.warmup + args.steps}))
+    print(json.dumps({"ncu_case": W.name, "subsets": args.subsets, "epochs": args.warmup + args.steps}))
 
 
 def time_to_tol(ctx, stream, which, tol, max_epochs, seed, graph=True):
@@ -351,7 +353,8 @@ def time_to_tol(ctx, stream, which, tol, max_epochs, seed, graph=True):
 def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs):
     """Time to 1e-3 relative distance to x* for graph-replayed SPDHG, SPDHG
     with plain launches and PDHG, in the paper's regime (alpha such that
-    ||A||^2 / alpha = 70, Sec. III) and at the workload's own alpha."""
+    ||A||^2 / alpha = 70, Sec. III) and at the workload's own alpha; in the
+    paper's regime also SPDHG over gates x S angle subsets, S = 2, 4, 8."""
     import torch
     out = {}
     nA = float(np.max(norms[:W.n_gates]))
@@ -367,6 +370,19 @@ def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs):
         leg["spdhg_graph"] = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], True)
         leg["spdhg_plain"] = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], False)
         leg["pdhg_graph"] = time_to_tol(ctx, stream, "pdhg", 1e-3, max_epochs, sd["gates"], True)
+        if label == "paper_regime_kappa70":
+            # sampling over gates x angle subsets (Sec. IV): same objective and x*,
+            # blocks of 1/S of the angles, N S iterations per epoch
+            subs = {}
+            for n_sub in (2, 4, 8):
+                ctx.set_subsets(n_sub)
+                ctx.norms(max_iter=100, tol=1e-7)
+                r = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], True)
+                r["kappa_spdhg"] = ctx.steps()["kappa"]
+                subs[f"S={n_sub}"] = r
+            ctx.set_subsets(1)
+            ctx.set_norms(norms)
+            leg["spdhg_angle_subsets_graph"] = subs
         out[label] = leg
     ctx.set_data(d, W.alpha)
     ctx.set_norms(norms)
@@ -435,6 +451,8 @@ def main():
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling driver: set up the workload, then only warm-up + timed "
                          "epochs as plain launches (no norms, e2e, profile or CPU legs)")
+    ap.add_argument("--subsets", type=int, default=1,
+                    help="--ncu-case only: sample gates x this many angle subsets")
     args = ap.parse_args()
     W = S.WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -98,7 +98,7 @@ __device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, 
     }
 }
 
-template <int PJ>
+template <int PJ, bool SUB>
 __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -122,9 +122,9 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     const float xmin = (float)(blockIdx.x * 32) - h, xmax = (float)min(blockIdx.x * 32 + 31, n - 1) - h;
     const float ymin = Y0, ymax = Y0 + (float)(PJ - 1);
     // angles of this launch: one angle subset of the drawn block, or all
-    const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;
-    const int sub = sel_subset(a.sel, slot);
-    const int na_s = (a.na - sub + S - 1) / S;
+    const int S = SUB ? a.sel.subsets : 1;
+    const int sub = SUB ? sel_subset(a.sel, slot) : 0;
+    const int na_s = SUB ? (a.na - sub + S - 1) / S : a.na;
     const int nck = (na_s + kChunk - 1) / kChunk;
 
     if (threadIdx.x == 0) {
@@ -215,15 +215,17 @@ size_t backproject_smem_bytes(int pj)
     return 64 + 2 * kChunk * (sizeof(int) + sizeof(BpAngle)) + std::max(win, red);
 }
 
+#define MC_BP_INSTANCES(X) X(4, false) X(8, false) X(16, false) X(4, true) X(8, true) X(16, true)
+
 cudaError_t backproject_prepare()
 {
     cudaError_t e = cudaSuccess;
-    for (int pj : {4, 8, 16}) {
-        const int bytes = (int)backproject_smem_bytes(pj);
-        if (e == cudaSuccess && pj == 4) e = cudaFuncSetAttribute(k_backproject<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess && pj == 8) e = cudaFuncSetAttribute(k_backproject<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-        if (e == cudaSuccess && pj == 16) e = cudaFuncSetAttribute(k_backproject<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    }
+#define MC_BP_ATTR(P, B)                                                                   \
+    if (e == cudaSuccess)                                                                 \
+        e = cudaFuncSetAttribute(k_backproject<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)backproject_smem_bytes(P));
+    MC_BP_INSTANCES(MC_BP_ATTR)
+#undef MC_BP_ATTR
     return e;
 }
 
@@ -234,13 +236,15 @@ cudaError_t launch_backproject(const BpArgs& a_in, cudaStream_t s)
     if (a.wl > a.Pb) return cudaErrorInvalidValue;
     const dim3 grid((a.n + 31) / 32, (a.n + a.pj - 1) / a.pj, a.n_slots);
     const size_t smem = backproject_smem_bytes(a.pj);
-    switch (a.pj) {
-    case 4: k_backproject<4><<<grid, 256, smem, s>>>(a); break;
-    case 8: k_backproject<8><<<grid, 256, smem, s>>>(a); break;
-    case 16: k_backproject<16><<<grid, 256, smem, s>>>(a); break;
-    default: return cudaErrorInvalidValue;
+    const bool sub = a.sel.subsets > 1;      // one angle subset per launch
+#define MC_BP_LAUNCH(P, B)                                     \
+    if (a.pj == P && sub == B) {                               \
+        k_backproject<P, B><<<grid, 256, smem, s>>>(a);        \
+        return cudaGetLastError();                             \
     }
-    return cudaGetLastError();
+    MC_BP_INSTANCES(MC_BP_LAUNCH)
+#undef MC_BP_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace mcg

@@ -32,8 +32,10 @@ __device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
 // computed into shared memory, then written as (w, next - w) pairs into the
 // row-line and the column-line layouts (the halo supplies "next"; pixels past
 // the image edge are zero).  The pair just before each line's data,
-// (0, w[0]), is written by the tile that holds position 0.
-__global__ void __launch_bounds__(256) k_warp_layouts(WarpArgs a)
+// (0, w[0]), is written by the tile that holds position 0.  One thread per
+// tile pixel (1024 per block, so a 512^2 image fits in one wave), the 65 halo
+// samples taken by the first threads afterwards.
+__global__ void __launch_bounds__(1024) k_warp_layouts(WarpArgs a)
 {
     __shared__ float w_s[33][34];
     const int slot = blockIdx.z;
@@ -43,21 +45,23 @@ __global__ void __launch_bounds__(256) k_warp_layouts(WarpArgs a)
     const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
     const int r_t = blockIdx.y * 32, c_t = blockIdx.x * 32;
     const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int idx = tid; idx < 33 * 33; idx += 256) {
-        const int rr = idx / 33, cc = idx - rr * 33;
+    auto sample = [&](int rr, int cc) {
         const int r = r_t + rr, c = c_t + cc;
         float w = 0.0f;
         if (r < n && c < n)
             w = a.identity ? __ldg(a.x + (size_t)r * n + c) : warp_sample(a.x, n, rg, field, r, c);
         w_s[rr][cc] = w;
+    };
+    sample(threadIdx.y, threadIdx.x);
+    if (tid < 65) {                        // halo: column 32 (rows 0..32), row 32 (columns 0..31)
+        if (tid < 33) sample(tid, 32);
+        else sample(32, tid - 33);
     }
     __syncthreads();
     float2* lrow = a.lrow + slot * a.layout_stride;
     float2* lcol = a.lcol + slot * a.layout_stride;
-    // row lines: lanes along the columns of one row
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int rr = threadIdx.y + 8 * i, cc = threadIdx.x;
+    {   // row lines: lanes along the columns of one row
+        const int rr = threadIdx.y, cc = threadIdx.x;
         const int r = r_t + rr, c = c_t + cc;
         if (r < n && c < n) {
             const float v = w_s[rr][cc];
@@ -65,10 +69,8 @@ __global__ void __launch_bounds__(256) k_warp_layouts(WarpArgs a)
             if (c == 0) lrow[(size_t)r * a.P + kGuard - 1] = make_float2(0.0f, v);
         }
     }
-    // column lines: lanes along the rows of one column
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int cc = threadIdx.y + 8 * i, rr = threadIdx.x;
+    {   // column lines: lanes along the rows of one column
+        const int cc = threadIdx.y, rr = threadIdx.x;
         const int r = r_t + rr, c = c_t + cc;
         if (r < n && c < n) {
             const float v = w_s[rr][cc];
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
 
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
 {
-    dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 8);
+    dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 32);
     k_warp_layouts<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -314,7 +316,20 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
         const int2* ent = a.ent + a.ent_off[gate];
         const float* b = a.b + (size_t)s * n2;
         const int e0 = __ldg(rp + q), e1 = __ldg(rp + q + 1);
-        for (int e = e0; e < e1; ++e) {
+        int e = e0;
+        // four entries per step: their loads and gathers are independent,
+        // the accumulation keeps the row's (sorted) order
+        for (; e + 4 <= e1; e += 4) {
+            const int2 t0 = __ldg(ent + e), t1 = __ldg(ent + e + 1);
+            const int2 t2 = __ldg(ent + e + 2), t3 = __ldg(ent + e + 3);
+            const float b0 = __ldg(b + t0.x), b1 = __ldg(b + t1.x);
+            const float b2 = __ldg(b + t2.x), b3 = __ldg(b + t3.x);
+            v = fmaf(__int_as_float(t0.y), b0, v);
+            v = fmaf(__int_as_float(t1.y), b1, v);
+            v = fmaf(__int_as_float(t2.y), b2, v);
+            v = fmaf(__int_as_float(t3.y), b3, v);
+        }
+        for (; e < e1; ++e) {
             const int2 t = __ldg(ent + e);
             v = fmaf(__int_as_float(t.y), __ldg(b + t.x), v);
         }
