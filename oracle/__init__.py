@@ -320,7 +320,8 @@ def _trace_entry(x, y, x_star, y_star):
 
 
 def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None,
-          x_star=None, y_star=None, literal: bool = False, subsets: int = 1) -> RunResult:
+          x_star=None, y_star=None, literal: bool = False, subsets: int = 1,
+          store: Optional[str] = None) -> RunResult:
     """Algorithm 1 (SPDHG) with serial sampling of one block per iteration.
 
     Standard reading (default):
@@ -338,6 +339,11 @@ def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None
     is uniform over the N S blocks (p_j = 1/(N S)) and an epoch is N S
     iterations.  ``st`` then comes from step_sizes(max_j ||A_j||^2, alpha,
     N, N S).  ``gates`` holds the drawn block indices.
+
+    ``store`` ('f32', 'f16', 'bf16') keeps the data d and the dual y in that
+    storage type (round_storage): d is rounded once, each new y_i is rounded
+    when stored, and the increment applied to z is the difference of the
+    stored values, so z = sum_i A_i^* y_i holds for the stored y.
     """
     g, N, S = P.geom, P.N, int(subsets)
     nblk = N * S
@@ -346,6 +352,7 @@ def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None
     probs = np.full(nblk, 1.0 / nblk) if p is None else np.asarray(p, dtype=np.float64) / np.sum(p)
     K = epochs * nblk
     blocks = draw_gates(seed, stream, 0, K, nblk, p)
+    d = round_storage(P.d, store)
     x = np.zeros((g.n, g.n)); z = np.zeros_like(x); zbar = np.zeros_like(x)
     y = np.zeros((N, g.na, g.nb))
     res = RunResult(x, y, z, blocks)
@@ -355,8 +362,8 @@ def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None
         j = int(blocks[k])                                                       # (ii)
         i, s = divmod(j, S)
         rows = subset_angles(g.na, S, s)
-        y_new = prox_fstar(y[i][rows] + st.sigma[i] * subset_op(x, P, i, S, s), st.sigma[i],
-                           P.d[i][rows], N)
+        y_new = round_storage(prox_fstar(y[i][rows] + st.sigma[i] * subset_op(x, P, i, S, s),
+                                         st.sigma[i], d[i][rows], N), store)
         dz = subset_adj(y_new - y[i][rows], P, i, S, s)
         y[i][rows] = y_new
         z = z + dz                                                               # (iii)
@@ -366,6 +373,27 @@ def spdhg(P: Problem, epochs: int, st: Steps, seed: int, stream: int = 0, p=None
             res.trace.append(_trace_entry(x, y, x_star, y_star))
     res.x, res.y, res.z = x, y, z
     return res
+
+
+# ------------------------------------------------------------ storage types
+def round_storage(v, kind: Optional[str]):
+    """v as stored in `kind`, returned as float64: None keeps v; 'f32' is
+    IEEE binary32, 'f16' binary16, 'bf16' bfloat16 (the upper 16 bits of a
+    binary32: 8 exponent bits, 7 stored significand bits).  Each rounds to
+    nearest, ties to even, through binary32 first (the kernels compute in
+    float32 and convert on store)."""
+    if kind is None:
+        return v
+    v32 = np.asarray(v, dtype=np.float32)
+    if kind == "f32":
+        return v32.astype(np.float64)
+    if kind == "f16":
+        return v32.astype(np.float16).astype(np.float64)
+    if kind == "bf16":
+        u = v32.view(np.uint32).astype(np.uint64)
+        u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(f"unknown storage type {kind!r}")
 
 
 # ------------------------------------------------------------ angle subsets
@@ -398,9 +426,12 @@ def block_norms2(P: Problem, S: int, iters: int = 200, tol: float = 1e-12) -> np
     return np.array(out)
 
 
-def pdhg(P: Problem, epochs: int, st: Steps, x_star=None, y_star=None) -> RunResult:
-    """PDHG: Algorithm 1 with p_i = 1 and S = all gates (Sec. II-A)."""
+def pdhg(P: Problem, epochs: int, st: Steps, x_star=None, y_star=None,
+         store: Optional[str] = None) -> RunResult:
+    """PDHG: Algorithm 1 with p_i = 1 and S = all gates (Sec. II-A); ``store``
+    as for spdhg."""
     g, N = P.geom, P.N
+    d = round_storage(P.d, store)
     x = np.zeros((g.n, g.n)); z = np.zeros_like(x); zbar = np.zeros_like(x)
     y = np.zeros((N, g.na, g.nb))
     res = RunResult(x, y, z, np.arange(N, dtype=np.int32))
@@ -409,7 +440,8 @@ def pdhg(P: Problem, epochs: int, st: Steps, x_star=None, y_star=None) -> RunRes
         x = prox_g(x - st.tau * zbar, st.tau, P.alpha)
         dz = np.zeros_like(x)
         for i in range(N):
-            y_new = prox_fstar(y[i] + st.sigma[i] * Ai(x, P, i), st.sigma[i], P.d[i], N)
+            y_new = round_storage(prox_fstar(y[i] + st.sigma[i] * Ai(x, P, i), st.sigma[i], d[i], N),
+                                  store)
             dz += Ait(y_new - y[i], P, i)
             y[i] = y_new
         z = z + dz
