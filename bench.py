@@ -41,8 +41,10 @@ UNIT = "pairs/s"
 def workload_config(W):
     return {
         "workload": f"{W.name}: {W.n}x{W.n} image ({W.n_ellipses} ellipses), {W.n_angles} angles x "
-                    f"{W.n_bins} bins, N={W.n_gates} rigid gates (+-{W.max_rot_deg:g} deg, "
-                    f"+-{W.max_shift:g} px), alpha={W.alpha:g}, SPDHG",
+                    f"{W.n_bins} bins, N={W.n_gates} " + (
+                        f"rigid gates (+-{W.max_rot_deg:g} deg, +-{W.max_shift:g} px)" if W.motion == "rigid"
+                        else f"dense-field gates ({W.rbf_count} Gaussian bumps of sigma {W.rbf_width:g} px, "
+                             f"max |u| = {W.rbf_max_disp:g} px)") + f", alpha={W.alpha:g}, SPDHG",
         "step": f"one SPDHG epoch = {W.n_gates} iterations = {W.n_gates} A_i+A_i^* pairs",
         "l2": "flushed between steps (256 MB write outside the timed events)",
     }
@@ -280,6 +282,8 @@ def run_ours(args, W):
     }
     if args.convergence_epochs > 0:
         out["time_to_1e-3"] = convergence_legs(ctx, stream, d, W, norms, sd, args.convergence_epochs)
+    if args.storage_epochs > 0:
+        out["storage_rbf512"] = storage_legs(args.storage_epochs)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
     ctx.close()
@@ -389,6 +393,62 @@ def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs):
     return out
 
 
+def storage_legs(max_epochs, steps=20):
+    """The non-rigid workload rbf512 (512^2, 720 x 729, N = 20 Gaussian-bump
+    fields) with d and y stored as float32, binary16 and bfloat16 (float32
+    arithmetic): time to 1e-3 relative distance to the float32 problem's x*
+    in the paper's regime (||A_i||^2 / alpha = 70), the distance reached
+    after max_epochs (the storage floor), and pairs/s of graph-replayed
+    epochs without trace."""
+    import torch
+
+    import paper_2410_10503_gb300 as mc
+    W = S.WORKLOADS["rbf512"]
+    sd = S.seeds(W.cid)
+    fields = S.rbf_fields(W.n, W.n_gates, sd["motion"], W.rbf_count, W.rbf_width, W.rbf_max_disp)
+    xt = S.phantom(W.n, W.n_ellipses, sd["phantom"], W.axis_lo, W.axis_hi)
+    eps = S.noise(W.n_gates, W.n_angles, W.n_bins, sd["noise"])
+    stream = torch.cuda.Stream()
+    ctx = mc.Context(W.n, W.n_angles, W.n_bins, W.n_gates, fields=fields, stream=stream.cuda_stream)
+    x_t = torch.as_tensor(xt, dtype=torch.float32, device="cuda")
+    d = torch.empty((W.n_gates, W.n_angles, W.n_bins), dtype=torch.float32, device="cuda")
+    for i in range(W.n_gates):
+        ctx.forward(i, x_t, out=d[i])
+    torch.cuda.synchronize()
+    sigma = W.noise_level * float(d.max())
+    d += torch.as_tensor(eps * (sigma / math.sqrt(W.n_gates)), dtype=torch.float32, device="cuda")
+    ctx.set_data(d, W.alpha)
+    norms = ctx.norms(max_iter=40, tol=1e-7)
+    alpha = float(np.max(norms[:W.n_gates])) / 70.0
+    ctx.set_data(d, alpha)
+    ctx.set_norms(norms)
+    x_star = torch.empty((W.n, W.n), dtype=torch.float32, device="cuda")
+    _, iters, rel = ctx.solve_normal(max_iter=400, tol=1e-6, x_out=x_star)
+    ctx.set_reference(x_star)
+    out = {"workload": workload_config(W)["workload"], "alpha": alpha,
+           "kappa_spdhg": ctx.steps()["kappa"], "x_star_cg": {"iterations": iters, "rel_residual": rel}}
+    for store in ("f32", "f16", "bf16"):
+        ctx.set_storage(store)
+        leg = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], True)
+        ctx.reset()
+        with torch.cuda.stream(stream):
+            _, tr = ctx.spdhg_run(max_epochs, seed=sd["gates"], x_out=False, trace=True)
+        leg["rel_err_after_max_epochs"] = float(tr[-1, 0])
+        leg["max_epochs"] = max_epochs
+        with torch.cuda.stream(stream):
+            ctx.spdhg_run(2, seed=sd["gates"], x_out=False)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.spdhg_run(steps, seed=sd["gates"], x_out=False)
+            b.record(stream)
+            b.synchronize()
+        leg["pairs_per_s"] = round(steps * W.n_gates / (a.elapsed_time(b) / 1e3), 1)
+        out[store] = leg
+    ctx.close()
+    return out
+
+
 def _oracle_pair_setup(W):
     import oracle as O
     sd = S.seeds(W.cid)
@@ -447,6 +507,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--convergence-epochs", type=int, default=100,
                     help="epoch cap of the time-to-1e-3 legs (0 skips them)")
+    ap.add_argument("--storage-epochs", type=int, default=100,
+                    help="epoch cap of the rbf512 float32/binary16/bfloat16 storage legs (0 skips)")
     ap.add_argument("--l1-peak-gbs", type=float, default=152 * 128 * 2.07)
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling driver: set up the workload, then only warm-up + timed "

@@ -79,8 +79,22 @@ typedef struct {
 enum {
     MC_OPT_GRAPH = 1,            /* 1 (default): replay each epoch as a CUDA graph */
     MC_OPT_PROFILE = 2,          /* 1: time every launch with CUDA events (slower)  */
-    MC_OPT_TRACE_OBJECTIVE = 3   /* 1: trace also evaluates O(x) (N extra A_i x)    */
+    MC_OPT_TRACE_OBJECTIVE = 3,  /* 1: trace also evaluates O(x) (N extra A_i x)    */
+    MC_OPT_STORAGE = 4           /* storage type of the data d and the dual y read and
+                                    written by every iteration: MC_STORE_F32 (default),
+                                    MC_STORE_F16 (IEEE binary16) or MC_STORE_BF16
+                                    (bfloat16); arithmetic stays float32.  d is rounded
+                                    once, each new y_i is rounded (to nearest even) when
+                                    stored and y_i^{k+1} - y_i^k is taken from the stored
+                                    values, so z = sum_i A_i^* y_i holds.  The iterates
+                                    then settle near x* of the rounded data: relative
+                                    floors of ~2e-4 (f16) and ~2e-3 (bf16) were measured,
+                                    within ||d_h - d|| / (2 sqrt(alpha N)).  The float32 d
+                                    is kept for mc_objective, mc_set_reference and
+                                    mc_solve_normal.  Switching converts the current y. */
 };
+
+enum { MC_STORE_F32 = 0, MC_STORE_F16 = 1, MC_STORE_BF16 = 2 };
 
 /* Create a context on the current CUDA device (Sec. II-A: geometry of A,
  * N gates, motion of D_i).  Builds the angle tables, uploads the motion and

@@ -314,6 +314,12 @@ class Context:
     def set_option(self, option: int, value: int):
         self._check(self._L.mc_set_option(self._h, option, int(value)))
 
+    def set_storage(self, kind: str):
+        """Storage type of d and y in the iterations: 'f32', 'f16' or 'bf16'
+        (MC_OPT_STORAGE)."""
+        code = {"f32": N.MC_STORE_F32, "f16": N.MC_STORE_F16, "bf16": N.MC_STORE_BF16}[kind]
+        self.set_option(N.MC_OPT_STORAGE, code)
+
     def profile(self) -> dict:
         cap = 16
         names = (ctypes.c_char_p * cap)()

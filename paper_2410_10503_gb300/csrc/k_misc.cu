@@ -1,6 +1,7 @@
 // K8 device gate draw (Algorithm 1 step (ii), serial uniform sampling
 // p_i = 1/N), K9 float64 reductions (Theorem norms, objective O(x) of
 // Sec. II-A, saddle-point distance), and small vector kernels.
+#include <algorithm>
 #include <cmath>
 
 #include "mc_kernels.h"
@@ -210,6 +211,37 @@ cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     k_fill_nan<<<(count + 255) / 256, 256, 0, s>>>(p, count);
+    return cudaGetLastError();
+}
+
+// ---- storage conversions ------------------------------------------------------
+__global__ void k_to_store(const float* __restrict__ src, unsigned short* __restrict__ dst, size_t len,
+                           int store)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = to_store(src[i], store);
+}
+
+__global__ void k_from_store(const unsigned short* __restrict__ src, float* __restrict__ dst, size_t len,
+                             int store)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < len; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = load_store(src[i], store);
+}
+
+cudaError_t launch_to_store(const float* src, unsigned short* dst, size_t len, int store, cudaStream_t s)
+{
+    if (store != 1 && store != 2) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)std::min<size_t>((len + 255) / 256, 4096);
+    k_to_store<<<std::max(blocks, 1u), 256, 0, s>>>(src, dst, len, store);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_from_store(const unsigned short* src, float* dst, size_t len, int store, cudaStream_t s)
+{
+    if (store != 1 && store != 2) return cudaErrorInvalidValue;
+    const unsigned blocks = (unsigned)std::min<size_t>((len + 255) / 256, 4096);
+    k_from_store<<<std::max(blocks, 1u), 256, 0, s>>>(src, dst, len, store);
     return cudaGetLastError();
 }
 

@@ -296,9 +296,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 a.out[(size_t)slot * a.na * nb + idx] = val;
             } else {
                 const size_t gi = (size_t)gate * a.na * nb + idx;
-                const float yo = a.y[gi];
-                const float yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
-                a.y[gi] = yn;
+                float yo, yn;
+                if (a.store == 0) {
+                    yo = a.y[gi];
+                    yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
+                    a.y[gi] = yn;
+                } else {
+                    // reduced-precision d and y: arithmetic in float32, the new
+                    // y rounded on store and the increment taken from stored values
+                    yo = load_store(a.yh[gi], a.store);
+                    const float yf = (yo + a.sigma * (val - load_store(a.dh[gi], a.store))) * a.inv_den;
+                    const unsigned short q = to_store(yf, a.store);
+                    a.yh[gi] = q;
+                    yn = load_store(q, a.store);
+                }
                 // dy pairs scaled by the angle's step: (m dy[b], m dy[b+1])
                 const float v = delta * (yn - yo);
                 float* dyp = reinterpret_cast<float*>(a.dy + slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b);

@@ -100,6 +100,9 @@ struct mc_ctx {
     // data and iterates
     float* d_d = nullptr;
     float* d_y = nullptr;
+    int store = 0;                    // MC_OPT_STORAGE: 0 float32 y (and d), 1 binary16, 2 bfloat16
+    unsigned short* d_dh = nullptr;   // d and y in that storage type (d_d stays the float32 master)
+    unsigned short* d_yh = nullptr;
     float* d_x[2] = {nullptr, nullptr};
     float* d_z = nullptr;
     int cur = 0;
@@ -408,6 +411,7 @@ mc_status enqueue_spdhg_epoch(mc_ctx* c, uint64_t seed, uint32_t stream)
         TRY(warp_into_layouts(c, xin, sel, 1, false));
         FwdArgs fa = fwd_args(c, sel, 1);
         fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y; fa.sigma = sigma; fa.inv_den = inv_den;
+        fa.store = c->store; fa.dh = c->d_dh; fa.yh = c->d_yh;
         TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
         TRY(backproject(c, sel, 1, c->d_b));
         WarpAdjArgs wa = wadj_args(c, sel, 1, c->d_b);
@@ -432,6 +436,7 @@ mc_status enqueue_pdhg_iter(mc_ctx* c)
     TRY(warp_into_layouts(c, xin, sel, N, false));
     FwdArgs fa = fwd_args(c, sel, N);
     fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y;
+    fa.store = c->store; fa.dh = c->d_dh; fa.yh = c->d_yh;
     fa.sigma = (float)c->sP.sigma;
     fa.inv_den = (float)(1.0 / (1.0 + c->sP.sigma * N / 2.0));
     TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
@@ -486,8 +491,16 @@ mc_status enqueue_trace(mc_ctx* c, int e)
     const float* xk = c->d_x[c->cur ^ 1];
     const size_t n2 = (size_t)c->n * c->n;
     if (c->have_ref) {
+        const size_t cnt = (size_t)c->N * c->na * c->nb;
+        const float* yk = c->d_y;
+        if (c->store != 0) {           // the stored dual, widened to float32
+            TRY(launch(c, C_MISC, "from_store", [&] {
+                return launch_from_store(c->d_yh, c->d_sinoN, cnt, c->store, c->stream);
+            }));
+            yk = c->d_sinoN;
+        }
         TRY(reduce(c, xk, c->d_xstar, n2, kRedDiffSq, c->d_s + S_DX2));
-        TRY(reduce(c, c->d_y, c->d_ystar, (size_t)c->N * c->na * c->nb, kRedDiffSq, c->d_s + S_DY2));
+        TRY(reduce(c, yk, c->d_ystar, cnt, kRedDiffSq, c->d_s + S_DY2));
         TRY(launch(c, C_MISC, "trace", [&] {
             return launch_trace_combine(c->d_s + S_DX2, c->d_s + S_XS2, c->d_s + S_DY2, out, c->stream);
         }));
@@ -986,6 +999,7 @@ mc_status mc_reset(mc_ctx* c)
     CK(cudaMemsetAsync(c->d_x[1], 0, n2 * sizeof(float), c->stream));
     CK(cudaMemsetAsync(c->d_z, 0, n2 * sizeof(float), c->stream));
     CK(cudaMemsetAsync(c->d_y, 0, (size_t)c->N * ns * sizeof(float), c->stream));
+    if (c->d_yh) CK(cudaMemsetAsync(c->d_yh, 0, (size_t)c->N * ns * sizeof(unsigned short), c->stream));
     CK(cudaMemsetAsync(c->d_k, 0, sizeof(unsigned long long), c->stream));
     c->cur = 0;
     c->k_host = 0;
@@ -1000,6 +1014,8 @@ mc_status mc_set_data(mc_ctx* c, const float* d, double alpha)
     const size_t cnt = (size_t)c->N * c->na * c->nb;
     CK(cudaMemcpyAsync(c->d_d, d, cnt * sizeof(float),
                        ptr_kind(c, d) == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (c->store != 0)
+        TRY(launch(c, C_MISC, "to_store", [&] { return launch_to_store(c->d_d, c->d_dh, cnt, c->store, c->stream); }));
     c->alpha = alpha;
     c->have_data = true;
     c->have_ref = false;
@@ -1487,6 +1503,28 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
     case MC_OPT_GRAPH: c->graph_on = value != 0; if (!c->graph_on) drop_graphs(c); return MC_OK;
     case MC_OPT_PROFILE: c->prof_on = value != 0; return MC_OK;
     case MC_OPT_TRACE_OBJECTIVE: c->trace_obj = value != 0; return MC_OK;
+    case MC_OPT_STORAGE: {
+        if (value < 0 || value > 2) return fail(c, MC_EINVAL, "storage must be 0 (f32), 1 (f16) or 2 (bf16)");
+        const int v = (int)value;
+        if (v == c->store) return MC_OK;
+        const size_t cnt = (size_t)c->N * c->na * c->nb;
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        // carry the dual over: to float32 first, then to the new type
+        if (c->store != 0)
+            TRY(launch(c, C_MISC, "from_store", [&] {
+                return launch_from_store(c->d_yh, c->d_y, cnt, c->store, c->stream);
+            }));
+        if (v != 0) {
+            if (!c->d_yh) TRY(dalloc(c, &c->d_yh, cnt));
+            if (!c->d_dh) TRY(dalloc(c, &c->d_dh, cnt));
+            TRY(launch(c, C_MISC, "to_store", [&] { return launch_to_store(c->d_y, c->d_yh, cnt, v, c->stream); }));
+            TRY(launch(c, C_MISC, "to_store", [&] { return launch_to_store(c->d_d, c->d_dh, cnt, v, c->stream); }));
+        }
+        c->store = v;
+        CK(cudaStreamSynchronize(c->stream));
+        return finish(c);
+    }
     default: return fail(c, MC_EINVAL, "unknown option %d", option);
     }
 }

@@ -16,6 +16,8 @@
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 namespace mcg {
 
@@ -127,6 +129,17 @@ __device__ __forceinline__ void warp_taps(const RigidGate* rg, const float* fiel
         two_sum(s, rg->offy_hi, s2, e2);
         split_int_frac(s2, ((a_lo + b_lo) + (e + e2)) + rg->offy_lo, r0, fr);
     }
+}
+
+// ---- reduced-precision storage of d and y (1: binary16, 2: bfloat16) --------
+__device__ __forceinline__ float load_store(unsigned short v, int store)
+{
+    return store == 1 ? __half2float(__ushort_as_half(v)) : __bfloat162float(__ushort_as_bfloat16(v));
+}
+
+__device__ __forceinline__ unsigned short to_store(float v, int store)
+{
+    return store == 1 ? __half_as_ushort(__float2half_rn(v)) : __bfloat16_as_ushort(__float2bfloat16_rn(v));
 }
 
 // ---- Philox4x32-10 (Salmon et al., SC'11) ----------------------------------

@@ -115,6 +115,9 @@ struct FwdArgs {
     int Pb, Gb;
     float sigma;
     float inv_den;             // 1 / (1 + sigma N / 2)
+    int store;                 // mode 1: 0 d, y as float; 1 binary16; 2 bfloat16 (dh, yh)
+    const unsigned short* dh;  // mode 1, store != 0: data and dual, gate stride na*nb
+    unsigned short* yh;
     int* err;
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
@@ -163,6 +166,9 @@ cudaError_t launch_trace_combine(const double* dx2, const double* xs2, const dou
 cudaError_t launch_objective_combine(const double* xx, const double* res, int n_res,
                                      double alpha, int N, double* out, cudaStream_t s);
 cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s);
+// storage conversions (store 1 binary16, 2 bfloat16; round to nearest even)
+cudaError_t launch_to_store(const float* src, unsigned short* dst, size_t len, int store, cudaStream_t s);
+cudaError_t launch_from_store(const unsigned short* src, float* dst, size_t len, int store, cudaStream_t s);
 // conjugate gradients with device-side float64 scalars
 cudaError_t launch_cg_step1(float* x, float* r, const float* p, const float* q, size_t len,
                             const double* rr, const double* pq, cudaStream_t s);
