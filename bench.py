@@ -284,6 +284,8 @@ def run_ours(args, W):
         out["time_to_1e-3"] = convergence_legs(ctx, stream, d, W, norms, sd, args.convergence_epochs)
     if args.storage_epochs > 0:
         out["storage_rbf512"] = storage_legs(args.storage_epochs)
+    if args.batch_slices > 0:
+        out["batch_mixed_slices"] = batch_legs(args.batch_slices, args.batch_epochs)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
     ctx.close()
@@ -449,6 +451,60 @@ def storage_legs(max_epochs, steps=20):
     return out
 
 
+def batch_legs(count, epochs):
+    """Independent slices of mixed size (mc_synth.slice_batch: sides 256-1024,
+    angles 1.4 side, bins side + 17, 4-32 gates, rigid and dense-field
+    motion), each in its own context with autotuned launch shapes: `epochs`
+    SPDHG epochs per slice run one slice after another (graph replay) and as
+    one batched run (mc_batch_spdhg_run, all slices' streams at once);
+    throughput in A_i + A_i^* pairs per second of the whole batch."""
+    import torch
+
+    import paper_2410_10503_gb300 as mc
+    ws = S.slice_batch(count)
+    ctxs, seeds, tunes = [], [], []
+    for W in ws:
+        sd = S.seeds(W.cid)
+        if W.motion == "rigid":
+            kw = dict(rigid=S.rigid_motion(W.n_gates, W.max_rot_deg, W.max_shift, sd["motion"]))
+        else:
+            kw = dict(fields=S.rbf_fields(W.n, W.n_gates, sd["motion"], W.rbf_count, W.rbf_width,
+                                          W.rbf_max_disp))
+        ctx = mc.Context(W.n, W.n_angles, W.n_bins, W.n_gates, **kw)
+        xt = torch.as_tensor(S.phantom(W.n, W.n_ellipses, sd["phantom"], W.axis_lo, W.axis_hi),
+                             dtype=torch.float32, device="cuda")
+        d = torch.empty((W.n_gates, W.n_angles, W.n_bins), dtype=torch.float32, device="cuda")
+        for i in range(W.n_gates):
+            ctx.forward(i, xt, out=d[i])
+        torch.cuda.synchronize()
+        ctx.set_data(d, W.alpha)
+        ctx.set_norms(ctx.norms(max_iter=12, tol=1e-4) * 1.05)
+        tunes.append(ctx.autotune(reps=3))
+        ctxs.append(ctx)
+        seeds.append(sd["gates"])
+    pairs = epochs * sum(W.n_gates for W in ws)
+    for c, sdg in zip(ctxs, seeds):                 # capture every slice's epoch graph
+        c.spdhg_run(1, seed=sdg, x_out=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c, sdg in zip(ctxs, seeds):
+        c.spdhg_run(epochs, seed=sdg, x_out=False)
+        c.stream.synchronize()
+    seq_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mc.batch_spdhg_run(ctxs, epochs, seeds)
+    bat_s = time.perf_counter() - t0
+    out = {"slices": [f"{W.n}^2 {W.n_angles}x{W.n_bins} N={W.n_gates} {W.motion}" for W in ws],
+           "epochs_per_slice": epochs, "pairs": pairs,
+           "one_after_another_pairs_per_s": round(pairs / seq_s, 1),
+           "batched_pairs_per_s": round(pairs / bat_s, 1),
+           "autotuned": tunes}
+    for c in ctxs:
+        c.close()
+    return out
+
+
 def _oracle_pair_setup(W):
     import oracle as O
     sd = S.seeds(W.cid)
@@ -509,6 +565,9 @@ def main():
                     help="epoch cap of the time-to-1e-3 legs (0 skips them)")
     ap.add_argument("--storage-epochs", type=int, default=100,
                     help="epoch cap of the rbf512 float32/binary16/bfloat16 storage legs (0 skips)")
+    ap.add_argument("--batch-slices", type=int, default=10,
+                    help="independent mixed-size slices of the batched leg (0 skips)")
+    ap.add_argument("--batch-epochs", type=int, default=3)
     ap.add_argument("--l1-peak-gbs", type=float, default=152 * 128 * 2.07)
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling driver: set up the workload, then only warm-up + timed "

@@ -135,6 +135,19 @@ mc_status mc_backproject(mc_ctx* ctx, const float* y, float* out);
 mc_status mc_warp(mc_ctx* ctx, int32_t gate, const float* x, float* out);
 mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out);
 
+/* Tune the launch shapes of the two projectors for this context's geometry
+ * by timing them on the device (each candidate `reps` launches after one
+ * warm-up, CUDA events on the context's stream): the forward's lines per
+ * staged chunk (2, 4, 8, as shared memory allows), work items per block and
+ * ray-group slots per warp, and the backprojector's rows per thread (4, 8,
+ * 16).  The fastest setting is kept; results are unchanged bit for bit by
+ * the item split and change within float32 rounding with the chunk size and
+ * rows per thread.  out (nullable, host, 4 int32): {lines per chunk, items per
+ * block, group slots per warp, rows per thread}.  Captured epoch graphs are
+ * dropped.  The creation-time choice is a heuristic (largest chunk that
+ * fits, fewest items, rows per thread giving ~24 warps per SM). */
+mc_status mc_autotune(mc_ctx* ctx, int32_t reps, int32_t* out);
+
 /* Sample gates and angle subsets together (the extension named in Sec. IV):
  * split the angles into `subsets` = S interleaved subsets (subset s holds
  * the angles k = s, s + S, s + 2S, ...; 1 <= S <= n_angles, S = 1 restores
@@ -229,6 +242,19 @@ mc_status mc_reset(mc_ctx* ctx);
  * MC_ESTATE if data or step sizes are missing. */
 mc_status mc_spdhg_run(mc_ctx* ctx, int32_t epochs, const mc_sampling* sampling,
                        float* x_out, double* trace);
+
+/* Many independent slices (one context each, e.g. different sizes, gate
+ * counts and motion kinds): run `epochs` SPDHG epochs on every context,
+ * enqueuing epoch e of every slice before epoch e + 1 of any, each on its
+ * own context stream, so small slices' launches overlap with large ones.
+ * Per context the result equals `epochs` calls of mc_spdhg_run with
+ * sampling[i] (same gate draws, same iterates).  sampling: count entries.
+ * All contexts must live on one device and have data and step sizes.
+ * Returns after every slice has finished (its error word checked); on
+ * failure *failed (nullable) receives the index of the context whose
+ * mc_last_error holds the message. */
+mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
+                             const mc_sampling* sampling, int32_t* failed);
 
 /* Run `epochs` iterations of PDHG (p_i = 1, every gate each iteration,
  * zbar^{k+1} = z^{k+1} + theta sum_i A_i^*(y_i^{k+1} - y_i^k)), continuing from

@@ -24,7 +24,7 @@ from dataclasses import dataclass, replace
 import numpy as np
 
 __all__ = [
-    "Workload", "WORKLOADS", "phantom", "disc_area_image", "rigid_motion",
+    "Workload", "WORKLOADS", "SLICE_SIDES", "slice_batch", "phantom", "disc_area_image", "rigid_motion",
     "rbf_fields", "noise", "seeds", "random_image", "random_sinogram",
 ]
 
@@ -72,6 +72,29 @@ WORKLOADS = {
     "rbf256": Workload("rbf256", 4, 256, 360, 365, 8, "rbf",
                        n_ellipses=20, alpha=1e-3, epochs=50),
 }
+
+
+SLICE_SIDES = (256, 384, 512, 768, 1024)
+
+
+def slice_batch(count: int, seed: int = 5000, sides=SLICE_SIDES) -> list:
+    """Independent slices of mixed size for batched runs: side drawn from
+    `sides` (cycled, so every size appears), angles round(1.4 side), bins
+    side + 17, gate count U{4..32}, motion alternating rigid (+-8 deg, +-6 px)
+    and dense fields (16 bumps, sigma side/12.8, max |u| = 8 px), 10-40
+    ellipses scaled with the side, alpha = 1e-3.  Slice j has workload id
+    seed + j (its seeds() follow from it)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for j in range(count):
+        side = int(sides[j % len(sides)])
+        gates = int(rng.integers(4, 33))
+        kind = "rigid" if j % 2 == 0 else "rbf"
+        out.append(Workload(f"slice{j}_{side}", seed + j, side, int(round(1.4 * side)), side + 17, gates,
+                            kind, max_rot_deg=8.0, max_shift=6.0, rbf_width=side / 12.8,
+                            n_ellipses=max(10, side // 25), axis_lo=side / 100.0, axis_hi=side / 12.8,
+                            alpha=1e-3, epochs=100))
+    return out
 
 
 def seeds(cid: int, run: int = 0) -> dict:

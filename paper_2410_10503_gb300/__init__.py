@@ -23,7 +23,7 @@ import numpy as np
 
 from . import _native as N
 
-__all__ = ["Context", "MCError", "lib", "version", "project_gate"]
+__all__ = ["Context", "MCError", "lib", "version", "project_gate", "batch_spdhg_run"]
 
 try:  # torch is plumbing here (device memory, streams); optional for host arrays
     import torch
@@ -314,6 +314,14 @@ class Context:
     def set_option(self, option: int, value: int):
         self._check(self._L.mc_set_option(self._h, option, int(value)))
 
+    def autotune(self, reps: int = 5) -> dict:
+        """Time the projectors' launch shapes on this geometry and keep the
+        fastest (mc_autotune)."""
+        out = np.zeros(4, np.int32)
+        self._check(self._L.mc_autotune(self._h, int(reps), out.ctypes.data))
+        return dict(zip(("lines_per_chunk", "items_per_block", "group_slots", "rows_per_thread"),
+                        out.tolist()))
+
     def set_storage(self, kind: str):
         """Storage type of d and y in the iterations: 'f32', 'f16' or 'bf16'
         (MC_OPT_STORAGE)."""
@@ -348,3 +356,25 @@ def project_gate(ctx: Context, gate: int, x, field=None):
     field (mc_vjp).  See autograd.GateProjection."""
     from .autograd import GateProjection
     return GateProjection.apply(ctx, gate, x, field)
+
+
+def batch_spdhg_run(contexts, epochs: int, seeds, streams=None):
+    """SPDHG epochs on many independent slice contexts at once
+    (mc_batch_spdhg_run): per context identical to ctx.spdhg_run(epochs,
+    seed) but interleaved epoch by epoch across the contexts' streams."""
+    count = len(contexts)
+    if streams is None:
+        streams = [0] * count
+    arr = (ctypes.c_void_p * count)(*[c._h for c in contexts])
+    smp = (N.mc_sampling * count)(*[N.mc_sampling(int(s), int(t)) for s, t in zip(seeds, streams)])
+    failed = ctypes.c_int32(-1)
+    L = lib()
+    if torch is not None and torch.cuda.is_available():
+        cur = torch.cuda.current_stream()
+        for c in contexts:
+            if c._stream is not None and c._stream != cur:
+                c._stream.wait_stream(cur)
+    st = L.mc_batch_spdhg_run(arr, count, int(epochs), smp, ctypes.byref(failed))
+    if st != 0:
+        who = contexts[failed.value] if 0 <= failed.value < count else contexts[0]
+        raise MCError(st, L.mc_last_error(who._h).decode())

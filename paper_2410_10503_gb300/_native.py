@@ -42,6 +42,7 @@ SIGNATURES = {
     "mc_warp": (_I32, [_VP, _I32, _VP, _VP]),
     "mc_warp_adjoint": (_I32, [_VP, _I32, _VP, _VP]),
     "mc_set_subsets": (_I32, [_VP, _I32]),
+    "mc_autotune": (_I32, [_VP, _I32, _VP]),
     "mc_set_field": (_I32, [_VP, _I32, _VP]),
     "mc_vjp": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP]),
     "mc_norms": (_I32, [_VP, _I32, _D, _VP]),
@@ -52,6 +53,7 @@ SIGNATURES = {
     "mc_solve_normal": (_I32, [_VP, _I32, _D, _VP, _VP]),
     "mc_spdhg_run": (_I32, [_VP, _I32, ctypes.POINTER(mc_sampling), _VP, _VP]),
     "mc_pdhg_run": (_I32, [_VP, _I32, _VP, _VP]),
+    "mc_batch_spdhg_run": (_I32, [_VP, _I32, _I32, _VP, _VP]),
     "mc_draw_gates": (_I32, [_VP, ctypes.POINTER(mc_sampling), _U64, _I32, _VP]),
     "mc_objective": (_I32, [_VP, _VP, _VP]),
     "mc_set_option": (_I32, [_VP, _I32, _I64]),

@@ -604,6 +604,29 @@ long long ray_samples(int n, double hb, double inv, double t, int b)
     return hi >= lo ? hi - lo + 1 : 0;
 }
 
+// Forward angle table for chunks of lc lines: slope split into float pairs and
+// the exact integer/fraction split of the per-chunk advance lc * t.
+std::vector<FwdAngle> fwd_angles(const mc_ctx* c, int lc)
+{
+    std::vector<FwdAngle> fa(c->na);
+    for (int k = 0; k < c->na; ++k) {
+        const bool xd = (c->na <= 4 * k) && (4 * k <= 3 * c->na);
+        const double inv = c->inv_k[k], t = c->t_k[k];
+        FwdAngle f{};
+        split_f(inv, f.inv_hi, f.inv_lo);
+        split_f(t, f.t_hi, f.t_lo);
+        const double step = (double)lc * t;
+        const double si = std::floor(step);
+        f.step_int = (int)si;
+        f.step_frac = (float)(step - si);
+        if (f.step_frac >= 1.0f) { f.step_frac = 0.0f; f.step_int += 1; }
+        f.delta = (float)std::fabs(inv);
+        f.dir = xd ? 1 : 0;
+        fa[k] = f;
+    }
+    return fa;
+}
+
 // Ray groups of the forward projector (up to 32 consecutive bins of one
 // angle) for S interleaved angle subsets: subset s holds the angles k = s
 // (mod S), rows-driven angles first; its groups are sets[s] = {first,
@@ -650,11 +673,11 @@ void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vec
 // class separately: an item streams one line layout); the smallest ipb whose
 // items hold at most kConsumers * rpt groups, rpt in {2, 4, 8}.  Items of set
 // s are items[set_off[s] .. set_off[s+1]).
-void partition_items(const GroupTable& gt, int sms, std::vector<RayItem>& items, std::vector<int>& set_off,
-                     int& ipb, int& rpt)
+void partition_items(const GroupTable& gt, int sms, int ipb_start, std::vector<RayItem>& items,
+                     std::vector<int>& set_off, int& ipb, int& rpt)
 {
     const std::vector<long long>& cum = gt.cum;
-    for (ipb = 1;; ++ipb) {
+    for (ipb = std::max(ipb_start, 1);; ++ipb) {
         const int target = ipb * sms;
         items.clear();
         set_off.assign(1, 0);
@@ -705,27 +728,14 @@ mc_status build_tables(mc_ctx* c)
             if ((pass == 1) == xd) order.push_back(k);
         }
     std::vector<double> inv_k(na), t_k(na);
-    int ny = 0;
     for (int k = 0; k < na; ++k) {
         const double phi = (double)k * kPi / (double)na;
         const double cs = std::cos(phi), sn = std::sin(phi);
         const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
-        if (!xd) ++ny;
         const double inv = xd ? 1.0 / sn : 1.0 / cs;
         const double t = xd ? cs / sn : sn / cs;
         inv_k[k] = inv;
         t_k[k] = t;
-        FwdAngle f{};
-        split_f(inv, f.inv_hi, f.inv_lo);
-        split_f(t, f.t_hi, f.t_lo);
-        const double step = (double)c->lc * t;
-        const double si = std::floor(step);
-        f.step_int = (int)si;
-        f.step_frac = (float)(step - si);
-        if (f.step_frac >= 1.0f) { f.step_frac = 0.0f; f.step_int += 1; }
-        f.delta = (float)std::fabs(inv);
-        f.dir = xd ? 1 : 0;
-        fa[k] = f;
         BpAngle b{};
         split_f(cs, b.cos_hi, b.cos_lo);
         split_f(sn, b.sin_hi, b.sin_lo);
@@ -739,12 +749,13 @@ mc_status build_tables(mc_ctx* c)
     c->order = order;
     c->inv_k = inv_k;
     c->t_k = t_k;
+    fa = fwd_angles(c, c->lc);
     GroupTable gt;
     build_groups(c, order, inv_k, t_k, 1, gt);
     std::vector<RayItem> items;
     std::vector<int> set_off;
     int rpt = 2, ipb = 1;
-    partition_items(gt, c->sms, items, set_off, ipb, rpt);
+    partition_items(gt, c->sms, 1, items, set_off, ipb, rpt);
     const std::vector<int2>& groups = gt.groups;
     c->ipb = ipb;
     c->rpt = rpt;
@@ -1122,6 +1133,102 @@ mc_status mc_warp_adjoint(mc_ctx* c, int32_t gate, const float* v, float* out)
     return finish(c);
 }
 
+// Install the all-angle forward tables for chunks of lc lines and at least
+// ipb_start items per block (rpt = 0: the smallest that fits, else at least rpt).
+mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min)
+{
+    std::vector<FwdAngle> fa = fwd_angles(c, lc);
+    GroupTable gt;
+    build_groups(c, c->order, c->inv_k, c->t_k, 1, gt);
+    std::vector<RayItem> items;
+    std::vector<int> off;
+    int ipb = 1, rpt = 2;
+    partition_items(gt, c->sms, ipb_start, items, off, ipb, rpt);
+    while (rpt < rpt_min && rpt < 8) rpt <<= 1;
+    dfree(c, &c->d_items);
+    TRY(dalloc(c, &c->d_items, items.size()));
+    CK(cudaMemcpyAsync(c->d_fang, fa.data(), fa.size() * sizeof(FwdAngle), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->lc = lc;
+    c->ipb = ipb;
+    c->rpt = rpt;
+    c->n_items = (int)items.size();
+    return MC_OK;
+}
+
+mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
+{
+    if (!c) return MC_EINVAL;
+    if (reps < 1 || reps > 1000) return fail(c, MC_EINVAL, "reps must be in [1, 1000]");
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graphs(c);
+    const bool prof = c->prof_on;
+    c->prof_on = false;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto timed = [&](auto&& body, float& ms) -> mc_status {
+        TRY(body());                                   // warm-up
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < reps; ++r) TRY(body());
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        return MC_OK;
+    };
+    // the forward's work does not depend on the values: warp the current x of gate 0
+    mc_status st = warp_into_layouts(c, c->d_x[c->cur], GateSel{nullptr, 0}, 1, false);
+    // forward: chunk lines x items per block x group slots per warp
+    int best_lc = c->lc, best_ipb = c->ipb, best_rpt = c->rpt;
+    float best = 1e30f;
+    for (int lc : {2, 4, 8}) {
+        if (st != MC_OK) break;
+        if ((size_t)lc * c->P * sizeof(float2) > 34816) continue;
+        int ipb0 = 0;
+        for (int step = 0; step < 3 && st == MC_OK; ++step) {
+            const int ipb_try = ipb0 ? ipb0 + step : 1;
+            for (int rmul = 1; rmul <= 2 && st == MC_OK; rmul *= 2) {
+                st = install_forward_tables(c, lc, ipb_try, 0);
+                if (st != MC_OK) break;
+                if (!ipb0) ipb0 = c->ipb;
+                if (rmul == 2) {
+                    if (c->rpt >= 8) continue;
+                    st = install_forward_tables(c, lc, ipb_try, c->rpt * 2);
+                    if (st != MC_OK) break;
+                }
+                float ms = 0;
+                st = timed([&] { return project_store(c, GateSel{nullptr, 0}, 1, c->d_sinoN); }, ms);
+                if (st == MC_OK && ms < best) {
+                    best = ms; best_lc = c->lc; best_ipb = c->ipb; best_rpt = c->rpt;
+                }
+            }
+        }
+    }
+    if (st == MC_OK) st = install_forward_tables(c, best_lc, best_ipb, best_rpt);
+    // backprojection: rows per thread
+    int best_pj = c->pj;
+    float best_bp = 1e30f;
+    for (int pj : {4, 8, 16}) {
+        if (st != MC_OK) break;
+        c->pj = pj;
+        float ms = 0;
+        st = timed([&] { return backproject(c, GateSel{nullptr, 0}, 1, c->d_b); }, ms);
+        if (st == MC_OK && ms < best_bp) { best_bp = ms; best_pj = pj; }
+    }
+    c->pj = best_pj;
+    c->prof_on = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(st);
+    TRY(check_err_word(c));
+    if (out) {
+        out[0] = c->lc; out[1] = c->ipb; out[2] = c->rpt; out[3] = c->pj;
+    }
+    return finish(c);
+}
+
 mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
 {
     if (!c) return MC_EINVAL;
@@ -1141,7 +1248,7 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
         std::vector<RayItem> items;
         std::vector<int> off;
         int ipb = 1, rpt = 2;
-        partition_items(gt, c->sms, items, off, ipb, rpt);
+        partition_items(gt, c->sms, 1, items, off, ipb, rpt);
         int most = 0;
         for (int q = 0; q < subsets; ++q) most = std::max(most, off[q + 1] - off[q]);
         TRY(dalloc(c, &c->d_sgroups, gt.groups.size()));
@@ -1437,6 +1544,43 @@ mc_status mc_spdhg_run(mc_ctx* c, int32_t epochs, const mc_sampling* sampling, f
                        double* trace)
 {
     return run_common(c, 0, epochs, sampling, x_out, trace);
+}
+
+mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
+                             const mc_sampling* sampling, int32_t* failed)
+{
+    if (failed) *failed = -1;
+    if (!ctxs || count < 1) return MC_EINVAL;
+    if (!sampling) return fail(ctxs[0], MC_EINVAL, "sampling is NULL");
+    if (epochs < 0) return fail(ctxs[0], MC_EINVAL, "epochs must be >= 0");
+    int dev = -1;
+    for (int i = 0; i < count; ++i) {
+        mc_ctx* c = ctxs[i];
+        if (!c) { if (failed) *failed = i; return MC_EINVAL; }
+        if (i == 0) dev = c->dev;
+        if (c->dev != dev || !c->have_data || !c->steps_ok) {
+            if (failed) *failed = i;
+            return fail(c, c->dev != dev ? MC_EINVAL : MC_ESTATE,
+                        c->dev != dev ? "batch contexts must share one device"
+                                      : "runs need mc_set_data and mc_norms/mc_set_norms first");
+        }
+    }
+    // epoch by epoch, every slice in turn: each context's graph goes to its
+    // own stream, so the slices' kernels overlap on the device
+    for (int e = 0; e < epochs; ++e)
+        for (int i = 0; i < count; ++i) {
+            mc_ctx* c = ctxs[i];
+            const mc_status st = run_epoch(c, 0, sampling[i].seed, sampling[i].stream);
+            if (st != MC_OK) { if (failed) *failed = i; return st; }
+            c->k_host += (uint64_t)c->N * c->S;
+        }
+    for (int i = 0; i < count; ++i) {
+        mc_ctx* c = ctxs[i];
+        mc_status st = check_err_word(c);
+        if (st == MC_OK) st = finish(c);
+        if (st != MC_OK) { if (failed) *failed = i; return st; }
+    }
+    return MC_OK;
 }
 
 mc_status mc_pdhg_run(mc_ctx* c, int32_t epochs, float* x_out, double* trace)

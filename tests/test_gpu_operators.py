@@ -183,3 +183,24 @@ def test_invalid_gate_and_state_errors(mc):
     assert "MC_ESTATE" in str(e.value)
     with pytest.raises(mc.MCError):
         ctx.set_data(np.zeros(2 * 8 * 23, np.float32), alpha=-1.0)
+
+
+def test_autotune_keeps_parity(mc):
+    """mc_autotune picks launch shapes from its candidate sets; the tuned
+    operators still meet the FP64 oracle, and an item split alone changes no
+    bit of the forward."""
+    n, na, nb, N = 128, 180, 183, 3
+    rig = _rigid(N, 21)
+    ctx = mc.Context(n, na, nb, N, rigid=rig)
+    P = O.Problem(O.Geometry(n, na, nb), O.Motion(rigid=rig), np.zeros((N, na, nb)), 1.0)
+    x = S.phantom(n, 10, 22, 5, 40)
+    y = S.random_sinogram(na, nb, 23)
+    t = ctx.autotune(reps=2)
+    assert t["lines_per_chunk"] in (2, 4, 8) and t["rows_per_thread"] in (4, 8, 16)
+    assert t["group_slots"] in (2, 4, 8) and t["items_per_block"] >= 1
+    for i in range(N):
+        assert rel_l2(host(ctx.forward(i, cuda(x))), O.Ai(x, P, i)) <= TOL
+        assert rel_l2(host(ctx.adjoint(i, cuda(y))), O.Ait(y, P, i)) <= TOL
+    fresh = mc.Context(n, na, nb, N, rigid=rig)
+    if t["lines_per_chunk"] == 8:
+        np.testing.assert_array_equal(host(ctx.forward(1, cuda(x))), host(fresh.forward(1, cuda(x))))
