@@ -57,13 +57,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     return false;
 }
 
-__device__ __forceinline__ float2 lds64(uint32_t addr)
-{
-    float2 v;
-    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
-    return v;
-}
-
 // Issue the window copies of one chunk (warp 0; lane i handles angles i, i+32...).
 // Window of angle k: WL pairs of dy row k starting at ws (even, so the copy is
 // 16-byte aligned), covering every bin the tile's pixels project onto.  The
@@ -96,6 +89,41 @@ __device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, 
             "l"(dys + (size_t)k * a.Pb + ws), "r"((uint32_t)(wl * sizeof(float2))), "r"(smem_u32(bar))
             : "memory");
     }
+}
+
+
+__device__ __forceinline__ unsigned long long bp_pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// Two rows of one column, as PTX on packed pairs: beta = j sn + frac, its
+// floor through the round-down magic add (whose bits also give the window
+// index), the fraction d, then the two 8-byte shared loads of the rows' dy
+// pairs; jj = (j, j+1) and mm = (magic, magic) stay in registers.
+__device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long long sn2, unsigned long long fr2,
+                                            unsigned long long mm, uint32_t row, float& d0, float& d1,
+                                            float2& y0, float2& y1)
+{
+    asm volatile(
+        "{\n\t"
+        ".reg .b64 b2, t2, fb2, d2;\n\t"
+        ".reg .b32 q0, q1, a0, a1;\n\t"
+        "fma.rn.f32x2 b2, %6, %7, %8;\n\t"
+        "add.rm.f32x2 t2, b2, %9;\n\t"
+        "sub.rn.f32x2 fb2, t2, %9;\n\t"
+        "sub.rn.f32x2 d2, b2, fb2;\n\t"
+        "mov.b64 {q0, q1}, t2;\n\t"
+        "mov.b64 {%0, %1}, d2;\n\t"
+        "mad.lo.u32 a0, q0, 8, %10;\n\t"
+        "mad.lo.u32 a1, q1, 8, %10;\n\t"
+        "ld.shared.v2.f32 {%2, %3}, [a0];\n\t"
+        "ld.shared.v2.f32 {%4, %5}, [a1];\n\t"
+        "}"
+        : "=f"(d0), "=f"(d1), "=f"(y0.x), "=f"(y0.y), "=f"(y1.x), "=f"(y1.y)
+        : "l"(jj), "l"(sn2), "l"(fr2), "l"(mm), "r"(row));
 }
 
 template <int PJ, bool SUB>
@@ -140,6 +168,10 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     float acc[PJ];
 #pragma unroll
     for (int j = 0; j < PJ; ++j) acc[j] = 0.0f;
+    unsigned long long jj[PJ / 2];
+#pragma unroll
+    for (int j = 0; j < PJ; j += 2) jj[j / 2] = bp_pk2((float)j, (float)(j + 1));
+    const unsigned long long mm = bp_pk2(kMagic, kMagic);
 
     for (int ch = 0; ch < nck; ++ch) {
         const int buf = ch & 1;
@@ -173,19 +205,16 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
             split_int_frac(s2, (al + bl) + (e + e2), bi, frac);
             const uint32_t row = wbase + ((uint32_t)(i * wl + bi - s_ws[buf * kChunk + i]) << 3);
             const float m = T.m, om = 1.0f - T.m, sn = T.sin_hi;
+            const unsigned long long sn2 = bp_pk2(sn, sn), fr2 = bp_pk2(frac, frac);
 #pragma unroll
             for (int j = 0; j < PJ; j += 2) {
-                const float2 b2 = __ffma2_rn(make_float2((float)j, (float)(j + 1)), make_float2(sn, sn),
-                                             make_float2(frac, frac));
-                const float2 t2 = __fadd2_rd(b2, make_float2(kMagic, kMagic));
-                const float2 fb2 = __fadd2_rn(t2, make_float2(-kMagic, -kMagic));
-                const float2 d2 = __ffma2_rn(fb2, make_float2(-1.0f, -1.0f), b2);
-                const float2 y0 = lds64(row + ((uint32_t)__float_as_int(t2.x) << 3));
-                const float2 y1 = lds64(row + ((uint32_t)__float_as_int(t2.y) << 3));
-                acc[j] = fmaf(__saturatef(fmaf(-d2.x, m, 1.0f)), y0.x,
-                              fmaf(__saturatef(fmaf(d2.x, m, om)), y0.y, acc[j]));
-                acc[j + 1] = fmaf(__saturatef(fmaf(-d2.y, m, 1.0f)), y1.x,
-                                  fmaf(__saturatef(fmaf(d2.y, m, om)), y1.y, acc[j + 1]));
+                float dx, dy;
+                float2 y0, y1;
+                bp_two_rows(jj[j / 2], sn2, fr2, mm, row, dx, dy, y0, y1);
+                acc[j] = fmaf(__saturatef(fmaf(-dx, m, 1.0f)), y0.x,
+                              fmaf(__saturatef(fmaf(dx, m, om)), y0.y, acc[j]));
+                acc[j + 1] = fmaf(__saturatef(fmaf(-dy, m, 1.0f)), y1.x,
+                                  fmaf(__saturatef(fmaf(dy, m, om)), y1.y, acc[j + 1]));
             }
         }
         __syncthreads();

@@ -85,12 +85,13 @@ constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
 constexpr int kBlock = kThreads + 32;        // plus one producer warp
 constexpr int kStages = 5;
 
-// Samples of one ray over the LC lines of a staged chunk.  The magic
-// constant of line j is kMagic + j * P: adding it with round-down leaves
-// floor(w) + j * P in the low mantissa bits, so the shared address of the pair
-// is one shift-add away and the fraction needs one more subtraction.  CLAMP
-// confines positions to [-ui, P - 2 - ui], i.e. into the zero guard cells,
-// and skips lines j >= lines of a short last chunk (warp-uniform).
+// Samples of one ray over the LC lines of an edge chunk (some lane's ray
+// leaves the image inside it).  The magic constant of line j is
+// kMagic + j * P: adding it with round-down leaves floor(w) + j * P in the
+// low mantissa bits, so the shared address of the pair is one shift-add away
+// and the fraction needs one more subtraction.  CLAMP confines positions to
+// [-ui, P - 2 - ui], i.e. into the zero guard cells, and skips lines
+// j >= lines of a short last chunk (warp-uniform).
 template <int LC, bool CLAMP>
 __device__ __forceinline__ float sample_lines(const float2* stage, int ibase, float fr, float t, const float* mj,
                                               float wlo, float whi, int lines, float acc)
@@ -115,6 +116,52 @@ __device__ __forceinline__ float sample_lines(const float2* stage, int ibase, fl
         if (CLAMP && j + 1 >= lines) break;
         const float2 v1 = stage[ibase + __float_as_int(t2.y)];
         acc += fmaf(f2.y, v1.y, v1.x);
+    }
+    return acc;
+}
+
+// Two FP32 values as one 64-bit register pair (the operand form of the
+// f32x2 instructions).
+__device__ __forceinline__ unsigned long long pk2(float a, float b)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// The same samples for an interior chunk, written as PTX on packed pairs:
+// the line constants jj = (-j, -(j+1)) and mm = (magic_j, magic_{j+1}) stay
+// in registers for the whole kernel, tt = (t, t) and ff = (fr, fr) are
+// packed once per group and chunk, and gbase = shared address of the stage
+// + 8 (ui - kMagicBits), so a sample's address is one multiply-add of its
+// round-down bits.  Same arithmetic, bit for bit, as sample_lines.
+template <int LC>
+__device__ __forceinline__ float sample_interior(uint32_t gbase, unsigned long long tt, unsigned long long ff,
+                                                 const unsigned long long* jj, const unsigned long long* mm,
+                                                 float acc)
+{
+#pragma unroll
+    for (int q = 0; q < LC / 2; ++q) {
+        float f0, f1, v0x, v0y, v1x, v1y;
+        asm volatile(
+            "{\n\t"
+            ".reg .b64 w2, t2, d2, f2;\n\t"
+            ".reg .b32 b0, b1, a0, a1;\n\t"
+            "fma.rn.f32x2 w2, %6, %7, %8;\n\t"
+            "add.rm.f32x2 t2, w2, %9;\n\t"
+            "sub.rn.f32x2 d2, t2, %9;\n\t"
+            "sub.rn.f32x2 f2, w2, d2;\n\t"
+            "mov.b64 {b0, b1}, t2;\n\t"
+            "mov.b64 {%0, %1}, f2;\n\t"
+            "mad.lo.u32 a0, b0, 8, %10;\n\t"
+            "mad.lo.u32 a1, b1, 8, %10;\n\t"
+            "ld.shared.v2.f32 {%2, %3}, [a0];\n\t"
+            "ld.shared.v2.f32 {%4, %5}, [a1];\n\t"
+            "}"
+            : "=f"(f0), "=f"(f1), "=f"(v0x), "=f"(v0y), "=f"(v1x), "=f"(v1y)
+            : "l"(jj[q]), "l"(tt), "l"(ff), "l"(mm[q]), "r"(gbase));
+        acc += fmaf(f0, v0y, v0x);
+        acc += fmaf(f1, v1y, v1x);
     }
     return acc;
 }
@@ -190,6 +237,12 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 #pragma unroll
     for (int j = 0; j < LC; ++j) mj[j] = kMagic + (float)(j * a.P);
     GroupState* my = s_grp + warp * RPT;
+    unsigned long long jj[LC / 2], mm[LC / 2];
+#pragma unroll
+    for (int q = 0; q < LC / 2; ++q) {
+        jj[q] = pk2(-(float)(2 * q), -(float)(2 * q + 1));
+        mm[q] = pk2(mj[2 * q], mj[2 * q + 1]);
+    }
 
     for (int it = 0; it < n_it; ++it) {
         const RayItem item = items[it0 + it];
@@ -266,7 +319,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 if (ch < gs.c_lo || ch > gs.c_hi) continue;
                 const int ib = ui[m] - kMagicBits;
                 if (ch >= gs.in_lo && ch <= gs.in_hi) {
-                    acc[m] = sample_lines<LC, false>(sp, ib, frac[m], gs.t, mj, 0.0f, 0.0f, LC, acc[m]);
+                    const uint32_t gbase = (uint32_t)__cvta_generic_to_shared(sp) + ((uint32_t)ib << 3);
+                    acc[m] = sample_interior<LC>(gbase, pk2(gs.t, gs.t), pk2(frac[m], frac[m]), jj, mm, acc[m]);
                 } else {
                     const float wlo = -(float)ui[m], whi = (float)(a.P - 2 - ui[m]);
                     acc[m] = sample_lines<LC, true>(sp, ib, frac[m], gs.t, mj, wlo, whi, lines, acc[m]);
@@ -324,6 +378,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 }  // namespace
 
 int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
+
+int forward_static_smem() { return (int)(kConsumers * 8 * sizeof(GroupState)); }
 
 size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }
 

@@ -980,7 +980,7 @@ mc_status mc_create(const mc_geometry* geom, int32_t n_gates, const mc_motion* m
     if (st == MC_OK) {
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        const size_t static_smem = 8192;   // the forward's static group tables
+        const size_t static_smem = (size_t)forward_static_smem();   // per-warp group tables
         const size_t need = forward_smem_bytes(c->lc, c->P) + static_smem;
         if ((size_t)optin < need) st = fail(c, MC_EDEVICE, "forward needs %zu B shared memory", need);
         else if (forward_prepare(optin - (int)static_smem) != cudaSuccess || backproject_prepare() != cudaSuccess)

@@ -122,6 +122,7 @@ struct FwdArgs {
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 int forward_groups_per_block(int rpt);
+int forward_static_smem();           // static shared memory of the largest instance
 size_t forward_smem_bytes(int lc, int P);
 cudaError_t forward_prepare(int max_smem);
 

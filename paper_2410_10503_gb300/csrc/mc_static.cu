@@ -147,7 +147,7 @@ mc_status device_setup(int dev, void** ptr, int* sms, char* err, int cap)
         }
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        e = forward_prepare(optin - 8192);
+        e = forward_prepare(optin - forward_static_smem());
         if (e != cudaSuccess) {
             set_msg(err, cap, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(e));
             return MC_ECUDA;
