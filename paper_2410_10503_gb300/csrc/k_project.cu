@@ -173,7 +173,13 @@ struct GroupState {
     int c_lo, c_hi, in_lo, in_hi;     // chunk range and interior chunk range
 };
 
-template <int RPT, int LC>
+// BANDED (angle-subset launches): an item also names a band of chunks
+// [band * cpb, (band + 1) * cpb); its rays' partial sums over that band go to
+// a.part[band] and k_forward_combine adds the bands in order and runs the
+// epilogue.  Items then hold several times more ray groups and stream only
+// their band of the image, where an unbanded subset item would stream the
+// whole image for a few groups.
+template <int RPT, int LC, bool BANDED>
 __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -208,21 +214,47 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     // ---- producer warp: fill the ring, item after item ----------------------
     if (warp == kConsumers) {
         if (lane == 0) {
-            for (int g = 0; g < n_it * nch; ++g) {
-                const int it = g / nch, c = g - it * nch;
-                const float2* src = (items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
-                const int st = g % kStages;
-                if (g >= kStages &&
-                    !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), kWaitLimit)) {
-                    atomicExch(s_flag, 1);
-                    atomicExch(a.err, kErrTimeout);
-                    break;
+            if constexpr (BANDED) {
+                // running chunk count q over the items' bands
+                int q = 0;
+                bool stop = false;
+                for (int it = 0; it < n_it && !stop; ++it) {
+                    const RayItem item = items[it0 + it];
+                    const float2* src = (item.dir ? a.lcol : a.lrow) + slot * a.layout_stride;
+                    const int cb0 = item.band * a.cpb, cb1 = min(nch, cb0 + a.cpb);
+                    for (int c = cb0; c < cb1; ++c, ++q) {
+                        const int st = q % kStages;
+                        if (q >= kStages &&
+                            !mbar_wait(&empty[st], (uint32_t)((q / kStages - 1) & 1), kWaitLimit)) {
+                            atomicExch(s_flag, 1);
+                            atomicExch(a.err, kErrTimeout);
+                            stop = true;
+                            break;
+                        }
+                        if (*(volatile int*)s_flag) { stop = true; break; }
+                        const int l0 = c * LC;
+                        const int lines = min(LC, n - l0);
+                        bulk_load(stage0 + st * stage_pairs, src + (size_t)l0 * a.P,
+                                  (uint32_t)(lines * a.P * sizeof(float2)), &full[st]);
+                    }
                 }
-                if (*(volatile int*)s_flag) break;
-                const int l0 = c * LC;
-                const int lines = min(LC, n - l0);
-                bulk_load(stage0 + st * stage_pairs, src + (size_t)l0 * a.P,
-                          (uint32_t)(lines * a.P * sizeof(float2)), &full[st]);
+            } else {
+                for (int g = 0; g < n_it * nch; ++g) {
+                    const int it = g / nch, c = g - it * nch;
+                    const float2* src = (items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
+                    const int st = g % kStages;
+                    if (g >= kStages &&
+                        !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), kWaitLimit)) {
+                        atomicExch(s_flag, 1);
+                        atomicExch(a.err, kErrTimeout);
+                        break;
+                    }
+                    if (*(volatile int*)s_flag) break;
+                    const int l0 = c * LC;
+                    const int lines = min(LC, n - l0);
+                    bulk_load(stage0 + st * stage_pairs, src + (size_t)l0 * a.P,
+                              (uint32_t)(lines * a.P * sizeof(float2)), &full[st]);
+                }
             }
         }
         return;
@@ -244,8 +276,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         mm[q] = pk2(mj[2 * q], mj[2 * q + 1]);
     }
 
+    int q_run = 0;                        // BANDED: chunks consumed so far
     for (int it = 0; it < n_it; ++it) {
         const RayItem item = items[it0 + it];
+        const int cb0 = BANDED ? item.band * a.cpb : 0;
+        const int cb1 = BANDED ? min(nch, cb0 + a.cpb) : nch;
         // this warp's groups: item.begin + warp + m * kConsumers
         const int ns = max(0, min(RPT, (item.end - item.begin - warp + kConsumers - 1) / kConsumers));
         float frac[RPT], acc[RPT];
@@ -278,8 +313,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
             const int hi_max = __reduce_max_sync(0xffffffffu, hi);
             const int lo_max = __reduce_max_sync(0xffffffffu, lo);
             const int hi_min = __reduce_min_sync(0xffffffffu, hi);
-            const int c_lo = (hi_max >= lo_min) ? lo_min / LC : nch;
-            const int c_hi = (hi_max >= lo_min) ? hi_max / LC : -1;
+            const int c_lo = (hi_max >= lo_min) ? (BANDED ? max(lo_min / LC, cb0) : lo_min / LC) : nch;
+            const int c_hi = (hi_max >= lo_min) ? (BANDED ? min(hi_max / LC, cb1 - 1) : hi_max / LC) : -1;
             const int in_lo = (lo_max + LC - 1) / LC;
             const int in_hi = (hi_min + 1) / LC - 1;
             if (lane == 0) {
@@ -302,8 +337,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         }
         __syncwarp();
 
-        for (int ch = 0; ch < nch; ++ch) {
-            const int g = it * nch + ch;
+        for (int ch = cb0; ch < cb1; ++ch) {
+            const int g = BANDED ? q_run++ : it * nch + ch;
             const int st = g % kStages;
             if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), kWaitLimit)) {
                 atomicExch(s_flag, 1);
@@ -337,6 +372,17 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         }
 
         // ---- epilogue ---------------------------------------------------------
+        if constexpr (BANDED) {
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                if (m >= ns) break;
+                const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+                const int b = grp.y + lane;
+                if (b < nb) a.part[((size_t)item.band * a.na + grp.x) * nb + b] = acc[m];
+            }
+            __syncwarp();
+            continue;
+        }
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             if (m >= ns) break;
@@ -375,6 +421,49 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     }
 }
 
+// Sum of the bands' partial ray sums in band order, then the epilogue of
+// k_forward (store, or the dual update of Algorithm 1 (ii)); one thread per
+// ray of the launch's angle subset.
+__global__ void __launch_bounds__(256) k_forward_combine(FwdArgs a)
+{
+    const int slot = blockIdx.y;
+    const int nb = a.nb;
+    const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;
+    const int sub = sel_subset(a.sel, slot);
+    const int na_s = (a.na - sub + S - 1) / S;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= na_s * nb) return;
+    const int m = idx / nb, b = idx - m * nb;
+    const int k = sub + m * S;
+    float accv = 0.0f;
+    for (int band = 0; band < a.nbands; ++band) accv += a.part[((size_t)band * a.na + k) * nb + b];
+    const float delta = __ldg(&a.ang[k].delta);
+    const float val = delta * accv;
+    const size_t ki = (size_t)k * nb + b;
+    if (a.mode == 0) {
+        a.out[(size_t)slot * a.na * nb + ki] = val;
+        return;
+    }
+    const int gate = sel_gate(a.sel, slot);
+    const size_t gi = (size_t)gate * a.na * nb + ki;
+    float yo, yn;
+    if (a.store == 0) {
+        yo = a.y[gi];
+        yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
+        a.y[gi] = yn;
+    } else {
+        yo = load_store(a.yh[gi], a.store);
+        const float yf = (yo + a.sigma * (val - load_store(a.dh[gi], a.store))) * a.inv_den;
+        const unsigned short q = to_store(yf, a.store);
+        a.yh[gi] = q;
+        yn = load_store(q, a.store);
+    }
+    const float v = delta * (yn - yo);
+    float* dyp = reinterpret_cast<float*>(a.dy + slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b);
+    dyp[0] = v;
+    dyp[-1] = v;
+}
+
 }  // namespace
 
 int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
@@ -389,9 +478,12 @@ size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P
 cudaError_t forward_prepare(int max_smem)
 {
     cudaError_t e = cudaSuccess;
-#define MC_SET_ATTR(R, L)                                                                   \
-    if (e == cudaSuccess)                                                                  \
-        e = cudaFuncSetAttribute(k_forward<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+#define MC_SET_ATTR(R, L)                                                                          \
+    if (e == cudaSuccess)                                                                         \
+        e = cudaFuncSetAttribute(k_forward<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 max_smem);                                                       \
+    if (e == cudaSuccess)                                                                         \
+        e = cudaFuncSetAttribute(k_forward<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                  max_smem);
     MC_FWD_INSTANCES(MC_SET_ATTR)
 #undef MC_SET_ATTR
@@ -400,12 +492,20 @@ cudaError_t forward_prepare(int max_smem)
 
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
 {
+    if (a.nbands > 1 && (a.n_slots != 1 || !a.part)) return cudaErrorInvalidValue;   // one partial buffer
     const dim3 grid((a.n_items + a.ipb - 1) / a.ipb, a.n_slots);
     const size_t smem = forward_smem_bytes(a.lc, a.P);
-#define MC_LAUNCH(R, L)                                              \
-    if (a.rpt == R && a.lc == L) {                                   \
-        k_forward<R, L><<<grid, kBlock, smem, s>>>(a);               \
-        return cudaGetLastError();                                   \
+#define MC_LAUNCH(R, L)                                                                   \
+    if (a.rpt == R && a.lc == L) {                                                        \
+        if (a.nbands > 1) {                                                               \
+            k_forward<R, L, true><<<grid, kBlock, smem, s>>>(a);                          \
+            const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;                          \
+            const int rays = ((a.na + S - 1) / S) * a.nb;                                 \
+            k_forward_combine<<<dim3((rays + 255) / 256, a.n_slots), 256, 0, s>>>(a);     \
+        } else {                                                                          \
+            k_forward<R, L, false><<<grid, kBlock, smem, s>>>(a);                         \
+        }                                                                                 \
+        return cudaGetLastError();                                                        \
     }
     MC_FWD_INSTANCES(MC_LAUNCH)
 #undef MC_LAUNCH

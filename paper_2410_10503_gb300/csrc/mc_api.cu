@@ -86,6 +86,8 @@ struct mc_ctx {
     RayItem* d_sitems = nullptr;
     int* d_soff = nullptr;
     int s_nitems = 0, s_ipb = 1, s_rpt = 2;
+    int s_bands = 1;                  // line bands per subset item (partial sums in d_bandpart)
+    float* d_bandpart = nullptr;
 
     // motion and D_i^T
     int kind = 0;
@@ -335,6 +337,12 @@ FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
     if (sel.subsets > 1) {            // the drawn block's angle subset
         a.groups = c->d_sgroups; a.items = c->d_sitems; a.sub_off = c->d_soff;
         a.n_items = c->s_nitems; a.ipb = c->s_ipb; a.rpt = c->s_rpt;
+        if (c->s_bands > 1) {
+            const int nch = (c->n + c->lc - 1) / c->lc;
+            a.nbands = c->s_bands;
+            a.cpb = (nch + c->s_bands - 1) / c->s_bands;
+            a.part = c->d_bandpart;
+        }
     }
     a.sel = sel; a.n_slots = n_slots;
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
@@ -1239,18 +1247,36 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
     dfree(c, &c->d_sgroups);
     dfree(c, &c->d_sitems);
     dfree(c, &c->d_soff);
+    dfree(c, &c->d_bandpart);
     c->S = 1;
+    c->s_bands = 1;
     c->have_norms = false;
     if (subsets > 1) {
-        // forward work items per angle subset, one table, subset s at soff[s]
+        // forward work items per angle subset, one table, subset s at soff[s];
+        // with B = S / 2 line bands (at most 8) each subset's groups are cut
+        // into ~SMs / B ranges, each repeated for every band
+        const int bands = std::min(8, std::max(1, subsets / 2));
         GroupTable gt;
         build_groups(c, c->order, c->inv_k, c->t_k, subsets, gt);
-        std::vector<RayItem> items;
-        std::vector<int> off;
+        std::vector<RayItem> cut;
+        std::vector<int> cut_off;
         int ipb = 1, rpt = 2;
-        partition_items(gt, c->sms, 1, items, off, ipb, rpt);
+        partition_items(gt, std::max(1, c->sms / bands), 1, cut, cut_off, ipb, rpt);
+        std::vector<RayItem> items;
+        std::vector<int> off(1, 0);
+        for (int q = 0; q < subsets; ++q) {
+            for (int band = 0; band < bands; ++band)
+                for (int i = cut_off[q]; i < cut_off[q + 1]; ++i) {
+                    RayItem it = cut[i];
+                    it.band = band;
+                    items.push_back(it);
+                }
+            off.push_back((int)items.size());
+        }
         int most = 0;
         for (int q = 0; q < subsets; ++q) most = std::max(most, off[q + 1] - off[q]);
+        if (bands > 1) TRY(dalloc(c, &c->d_bandpart, (size_t)bands * c->na * c->nb));
+        c->s_bands = bands;
         TRY(dalloc(c, &c->d_sgroups, gt.groups.size()));
         TRY(dalloc(c, &c->d_sitems, items.size()));
         TRY(dalloc(c, &c->d_soff, off.size()));

@@ -60,7 +60,7 @@ struct RigidGate {
 // group table, all with the same driving axis.  A ray group is up to 32
 // consecutive bins of one angle (one warp).
 struct RayItem {
-    int begin, end, dir, pad;
+    int begin, end, dir, band;     // band: chunk band of a banded (angle-subset) item, else 0
 };
 
 // ---- exact little helpers ------------------------------------------------

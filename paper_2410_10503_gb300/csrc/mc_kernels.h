@@ -100,6 +100,9 @@ struct FwdArgs {
     int n_items;               // items (the largest subset's count when sub_off is set)
     const int* sub_off;        // angle-subset tables: items of subset s are
                                // items[sub_off[s] .. sub_off[s+1]), or null
+    int nbands;                // > 1: items carry a band of cpb chunks; partial ray
+    int cpb;                   //      sums go to part [nbands][na][nb] and a combine
+    float* part;               //      kernel adds them and runs the epilogue
     int ipb;                   // items per block (one block per SM)
     int rpt;                   // group slots per consumer warp (2, 4, 8)
     int lc;                    // lines per staged chunk (2, 4, 8)
