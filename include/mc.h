@@ -103,7 +103,11 @@ enum { MC_STORE_F32 = 0, MC_STORE_F16 = 1, MC_STORE_BF16 = 2 };
  * those of D_i).  cuda_stream: a cudaStream_t to order all work on, or NULL
  * for a stream the context creates.  On success *out owns all device memory
  * of the context; release it with mc_destroy.  Errors: MC_EINVAL,
- * MC_ENOMEM, MC_ECUDA, MC_EDEVICE (message: mc_last_error(NULL)). */
+ * MC_ENOMEM, MC_ECUDA, MC_EDEVICE (message: mc_last_error(NULL)); a failed
+ * create frees everything it allocated.  Fault injection for tests: with
+ * the environment variable MC_FAIL_ALLOC_AFTER=k set at creation, the
+ * context's (k+1)-th device allocation fails with MC_ENOMEM (at creation or
+ * in a later call that allocates). */
 mc_status mc_create(const mc_geometry* geom, int32_t n_gates, const mc_motion* motion,
                     void* cuda_stream, mc_ctx** out);
 
@@ -282,6 +286,20 @@ mc_status mc_profile_reset(mc_ctx* ctx);
 
 /* Iteration counter k of the next SPDHG iteration (host out). */
 mc_status mc_iteration(mc_ctx* ctx, uint64_t* out);
+
+/* Checkpoint and resume of the solver state (x^K, x^{K+1}, z, every y_i in
+ * the current storage type, and the iteration counter k that keys the
+ * Philox draw).  mc_state_size gives the bytes; mc_save_state writes them to
+ * a HOST buffer of capacity cap; mc_load_state restores them into a context
+ * with the same geometry, gate count, storage type (MC_OPT_STORAGE) and
+ * angle-subset count, after mc_set_data and the step sizes as at saving.  A
+ * run continued from a loaded state with the same sampling seed and stream
+ * is bit-identical to the uninterrupted run.  The data, the steps, the
+ * motion and the reference are not part of the state.  Errors: MC_EINVAL
+ * for a foreign, mismatched or truncated buffer. */
+mc_status mc_state_size(mc_ctx* ctx, uint64_t* bytes);
+mc_status mc_save_state(mc_ctx* ctx, void* buf, uint64_t cap);
+mc_status mc_load_state(mc_ctx* ctx, const void* buf, uint64_t size);
 
 /* Library version string. */
 const char* mc_version(void);

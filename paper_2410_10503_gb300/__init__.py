@@ -342,6 +342,19 @@ class Context:
     def profile_reset(self):
         self._check(self._L.mc_profile_reset(self._h))
 
+    def save_state(self) -> bytes:
+        """Checkpoint of the solver state (mc_save_state) as bytes."""
+        size = ctypes.c_uint64()
+        self._check(self._L.mc_state_size(self._h, ctypes.byref(size)))
+        buf = (ctypes.c_char * size.value)()
+        self._check(self._L.mc_save_state(self._h, buf, size.value))
+        return bytes(buf)
+
+    def load_state(self, state: bytes):
+        """Restore a checkpoint from save_state (mc_load_state)."""
+        buf = ctypes.create_string_buffer(state, len(state))
+        self._check(self._L.mc_load_state(self._h, buf, len(state)))
+
     def iteration(self) -> int:
         out = ctypes.c_uint64()
         self._check(self._L.mc_iteration(self._h, ctypes.addressof(out)))

@@ -60,6 +60,9 @@ SIGNATURES = {
     "mc_profile_read": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP]),
     "mc_profile_reset": (_I32, [_VP]),
     "mc_iteration": (_I32, [_VP, _VP]),
+    "mc_state_size": (_I32, [_VP, _VP]),
+    "mc_save_state": (_I32, [_VP, _VP, _U64]),
+    "mc_load_state": (_I32, [_VP, _VP, _U64]),
     "mc_version": (ctypes.c_char_p, []),
     "mc_forward_static": (_I32, [ctypes.POINTER(mc_geometry), _VP, _VP, _VP, _VP, ctypes.c_char_p, _I32]),
 }

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -69,6 +70,7 @@ struct mc_ctx {
     bool own_stream = false;
     std::string err;
     std::vector<void*> allocs;
+    long fail_alloc_at = -1;          // simulated failure of the (k+1)-th device allocation
 
     // geometry
     FwdAngle* d_fang = nullptr;
@@ -202,6 +204,9 @@ mc_status dalloc(mc_ctx* c, T** p, size_t count)
 {
     void* q = nullptr;
     const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (c->fail_alloc_at >= 0 && (long)c->allocs.size() >= c->fail_alloc_at)
+        return fail(c, MC_ENOMEM, "simulated allocation failure at device buffer %zu (MC_FAIL_ALLOC_AFTER)",
+                    c->allocs.size());
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -974,6 +979,7 @@ mc_status mc_create(const mc_geometry* geom, int32_t n_gates, const mc_motion* m
     if (!c) return fail(nullptr, MC_ENOMEM, "host allocation failed");
     c->dev = dev;
     c->sms = prop.multiProcessorCount;
+    if (const char* fa = std::getenv("MC_FAIL_ALLOC_AFTER")) c->fail_alloc_at = std::atol(fa);
     c->n = geom->n; c->na = geom->n_angles; c->nb = geom->n_bins; c->N = n_gates;
     if (cuda_stream) {
         c->stream = (cudaStream_t)cuda_stream;
@@ -1719,6 +1725,91 @@ mc_status mc_profile_reset(mc_ctx* c)
     TRY(prof_collect(c));
     for (int i = 0; i < kNumClasses; ++i) { c->prof_count[i] = 0; c->prof_ms[i] = 0; }
     return MC_OK;
+}
+
+// ---- checkpoint / resume -----------------------------------------------------
+// Layout: header (8 x uint64) | x^K | x^{K+1} | z (n^2 float32 each) | y
+// (N n_a n_b values of the current storage type: float32 or uint16).
+namespace {
+constexpr uint64_t kStateMagic = 0x3154535043474d4dULL;   // "MMGCPST1"
+constexpr int kStateWords = 8;
+
+size_t state_bytes(const mc_ctx* c)
+{
+    const size_t n2 = (size_t)c->n * c->n, ny = (size_t)c->N * c->na * c->nb;
+    return kStateWords * sizeof(uint64_t) + 3 * n2 * sizeof(float) +
+           ny * (c->store ? sizeof(unsigned short) : sizeof(float));
+}
+}  // namespace
+
+mc_status mc_state_size(mc_ctx* c, uint64_t* bytes)
+{
+    if (!c || !bytes) return MC_EINVAL;
+    *bytes = state_bytes(c);
+    return MC_OK;
+}
+
+mc_status mc_save_state(mc_ctx* c, void* buf, uint64_t cap)
+{
+    if (!c) return MC_EINVAL;
+    if (!buf) return fail(c, MC_EINVAL, "buf is NULL");
+    if (ptr_kind(c, buf) != 0) return fail(c, MC_EINVAL, "buf must be host memory");
+    const size_t need = state_bytes(c);
+    if (cap < need) return fail(c, MC_EINVAL, "state needs %zu bytes, buffer has %llu", need, (unsigned long long)cap);
+    const size_t n2 = (size_t)c->n * c->n, ny = (size_t)c->N * c->na * c->nb;
+    uint64_t hdr[kStateWords] = {kStateMagic, (uint64_t)c->n, (uint64_t)c->na, (uint64_t)c->nb,
+                                 (uint64_t)c->N, (uint64_t)c->store, (uint64_t)c->S, c->k_host};
+    unsigned char* p = static_cast<unsigned char*>(buf);
+    std::memcpy(p, hdr, sizeof hdr);
+    p += sizeof hdr;
+    CK(cudaMemcpyAsync(p, c->d_x[c->cur ^ 1], n2 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(p + n2 * sizeof(float), c->d_x[c->cur], n2 * sizeof(float), cudaMemcpyDeviceToHost,
+                       c->stream));
+    CK(cudaMemcpyAsync(p + 2 * n2 * sizeof(float), c->d_z, n2 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    unsigned char* py = p + 3 * n2 * sizeof(float);
+    if (c->store)
+        CK(cudaMemcpyAsync(py, c->d_yh, ny * sizeof(unsigned short), cudaMemcpyDeviceToHost, c->stream));
+    else
+        CK(cudaMemcpyAsync(py, c->d_y, ny * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return finish(c);
+}
+
+mc_status mc_load_state(mc_ctx* c, const void* buf, uint64_t size)
+{
+    if (!c) return MC_EINVAL;
+    if (!buf) return fail(c, MC_EINVAL, "buf is NULL");
+    if (ptr_kind(c, buf) != 0) return fail(c, MC_EINVAL, "buf must be host memory");
+    if (size < kStateWords * sizeof(uint64_t)) return fail(c, MC_EINVAL, "state too short");
+    uint64_t hdr[kStateWords];
+    std::memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != kStateMagic) return fail(c, MC_EINVAL, "not a saved solver state");
+    if (hdr[1] != (uint64_t)c->n || hdr[2] != (uint64_t)c->na || hdr[3] != (uint64_t)c->nb ||
+        hdr[4] != (uint64_t)c->N)
+        return fail(c, MC_EINVAL, "state is for geometry %llu x (%llu x %llu), %llu gates",
+                    (unsigned long long)hdr[1], (unsigned long long)hdr[2], (unsigned long long)hdr[3],
+                    (unsigned long long)hdr[4]);
+    if (hdr[5] != (uint64_t)c->store || hdr[6] != (uint64_t)c->S)
+        return fail(c, MC_EINVAL, "state was saved with storage %llu and %llu angle subsets (context: %d, %d)",
+                    (unsigned long long)hdr[5], (unsigned long long)hdr[6], c->store, c->S);
+    if (size < state_bytes(c)) return fail(c, MC_EINVAL, "state truncated");
+    const size_t n2 = (size_t)c->n * c->n, ny = (size_t)c->N * c->na * c->nb;
+    const unsigned char* p = static_cast<const unsigned char*>(buf) + kStateWords * sizeof(uint64_t);
+    CK(cudaStreamSynchronize(c->stream));
+    c->cur = 0;                                   // x^{K+1} in d_x[0], x^K in d_x[1]
+    CK(cudaMemcpyAsync(c->d_x[1], p, n2 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_x[0], p + n2 * sizeof(float), n2 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_z, p + 2 * n2 * sizeof(float), n2 * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    const unsigned char* py = p + 3 * n2 * sizeof(float);
+    if (c->store)
+        CK(cudaMemcpyAsync(c->d_yh, py, ny * sizeof(unsigned short), cudaMemcpyHostToDevice, c->stream));
+    else
+        CK(cudaMemcpyAsync(c->d_y, py, ny * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    const unsigned long long k = hdr[7];
+    CK(cudaMemcpyAsync(c->d_k, &k, sizeof k, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->k_host = k;
+    return finish(c);
 }
 
 mc_status mc_iteration(mc_ctx* c, uint64_t* out)

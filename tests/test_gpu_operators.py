@@ -69,6 +69,26 @@ def test_backproject_matches_oracle(mc, n, na, nb):
     assert rel_l2(x, O.At(y, g)) <= TOL
 
 
+# the limits of mc_create (n <= 2048, n_angles and n_bins <= 8192), each with
+# the other sizes small enough for the oracle: the largest image with a wide
+# ragged detector, the most angles, the most bins
+LIMIT_GEOMS = [(2048, 5, 2900), (16, 8192, 23), (64, 7, 8192)]
+
+
+@pytest.mark.parametrize("n,na,nb", LIMIT_GEOMS)
+def test_operators_at_size_limits(mc, n, na, nb):
+    g = O.Geometry(n, na, nb)
+    rig = _rigid(2, 31, rot=8.0, shift=6.0)
+    ctx = mc.Context(n, na, nb, 2, rigid=rig)
+    P = O.Problem(g, O.Motion(rigid=rig), np.zeros((2, na, nb)), 1.0)
+    x = S.phantom(n, 6, 32, n / 16 + 0.5, n / 4 + 1)
+    y = S.random_sinogram(na, nb, 33)
+    assert rel_l2(host(ctx.project(cuda(x))), O.A(x, g)) <= TOL
+    assert rel_l2(host(ctx.backproject(cuda(y))), O.At(y, g)) <= TOL
+    assert rel_l2(host(ctx.forward(1, cuda(x))), O.Ai(x, P, 1)) <= TOL
+    assert rel_l2(host(ctx.adjoint(1, cuda(y))), O.Ait(y, P, 1)) <= TOL
+
+
 @pytest.mark.parametrize("kind", ["rigid", "field"])
 @pytest.mark.parametrize("n", [16, 37, 128])
 def test_warp_and_transpose_match_oracle(mc, kind, n):
