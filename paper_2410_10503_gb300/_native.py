@@ -5,7 +5,7 @@ from __future__ import annotations
 import ctypes
 import os
 
-from .build import LIB
+from .build import CHECKED_LIB, LIB
 
 MC_OK, MC_EINVAL, MC_ENOMEM, MC_ECUDA, MC_ETIMEOUT, MC_ESTATE, MC_EDEVICE = 0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "MC_OK", -1: "MC_EINVAL", -2: "MC_ENOMEM", -3: "MC_ECUDA",
@@ -71,17 +71,19 @@ _lib = None
 
 
 def lib_path() -> str:
-    return LIB
+    """The library this process loads: the checked flavour under MC_CHECKED=1."""
+    return CHECKED_LIB if os.environ.get("MC_CHECKED") == "1" else LIB
 
 
 def load() -> ctypes.CDLL:
     """Load the in-tree libmc.so (built by __graft_entry__.build())."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB):
-            raise RuntimeError(f"libmc is not built ({LIB} missing): run "
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libmc is not built ({path} missing): run "
                                "`python -c 'import __graft_entry__ as g; g.build()'`")
-        lib = ctypes.CDLL(LIB)
+        lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(lib, name)
             f.restype = res

@@ -1,7 +1,11 @@
 """Build libmc.so in-tree for sm_103a with nvcc (no cmake, no torch extension).
 
 Each translation unit compiles in parallel; the shared library lands in
-paper_2410_10503_gb300/_build/libmc.so, which the binding loads.
+paper_2410_10503_gb300/_build/libmc.so, which the binding loads.  The checked
+flavour (-DMC_CHECKED: every shared-memory gather index bounds-checked, a
+failed check sets the device error word that calls turn into MC_EDEVICE)
+lands in _build/checked/libmc.so and is loaded instead when MC_CHECKED=1 is
+set in the environment.
 """
 from __future__ import annotations
 
@@ -16,6 +20,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libmc.so")
+CHECKED_DIR = os.path.join(OUT_DIR, "checked")
+CHECKED_LIB = os.path.join(CHECKED_DIR, "libmc.so")
 SOURCES = ["k_warp.cu", "k_project.cu", "k_backproject.cu", "k_misc.cu", "mc_api.cu", "mc_static.cu"]
 HEADERS = ["mc_device.cuh", "mc_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,14 +46,18 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every CUDA translation unit and link libmc.so; return its path."""
-    os.makedirs(OUT_DIR, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Compile every CUDA translation unit and link libmc.so (or its checked
+    flavour); return its path."""
+    out_dir, lib = (CHECKED_DIR, CHECKED_LIB) if checked else (OUT_DIR, LIB)
+    if checked:
+        extra_flags = (*extra_flags, "-DMC_CHECKED")
+    os.makedirs(out_dir, exist_ok=True)
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(INCLUDE, "mc.h")]
     objs, jobs = [], []
     for src in SOURCES:
         sp = os.path.join(CSRC, src)
-        op = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        op = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(op)
         if force or _stale(op, [sp] + hdrs):
             jobs.append([nvcc(), *_flags(extra_flags), "-c", sp, "-o", op])
@@ -59,16 +69,16 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
                 raise RuntimeError(f"nvcc failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
             if verbose and (r.stdout or r.stderr):
                 print(r.stdout, r.stderr)
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     import sys
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, checked="--checked" in sys.argv))

@@ -206,11 +206,32 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
             const uint32_t row = wbase + ((uint32_t)(i * wl + bi - s_ws[buf * kChunk + i]) << 3);
             const float m = T.m, om = 1.0f - T.m, sn = T.sin_hi;
             const unsigned long long sn2 = bp_pk2(sn, sn), fr2 = bp_pk2(frac, frac);
+#ifdef MC_CHECKED
+            const int wofs = bi - s_ws[buf * kChunk + i];     // window offset of beta's integer part
+#endif
 #pragma unroll
             for (int j = 0; j < PJ; j += 2) {
                 float dx, dy;
                 float2 y0, y1;
+#ifdef MC_CHECKED
+                // the same arithmetic in C++, each pair index checked against
+                // the angle's window (0 <= offset <= WL - 1)
+                const float2 b2 = __ffma2_rn(make_float2((float)j, (float)(j + 1)), make_float2(sn, sn),
+                                             make_float2(frac, frac));
+                const float2 t2 = __fadd2_rd(b2, make_float2(kMagic, kMagic));
+                const float2 fb2 = __fadd2_rn(t2, make_float2(-kMagic, -kMagic));
+                dx = b2.x - fb2.x;
+                dy = b2.y - fb2.y;
+                const int o0 = wofs + (__float_as_int(t2.x) - kMagicBits);
+                const int o1 = wofs + (__float_as_int(t2.y) - kMagicBits);
+                const float2* win = reinterpret_cast<const float2*>(s_win + (size_t)buf * kChunk * wl) + (size_t)i * wl;
+                y0 = make_float2(0.0f, 0.0f);
+                y1 = make_float2(0.0f, 0.0f);
+                if (o0 >= 0 && o0 <= wl - 1) y0 = win[o0]; else atomicExch(a.err, kErrBounds);
+                if (o1 >= 0 && o1 <= wl - 1) y1 = win[o1]; else atomicExch(a.err, kErrBounds);
+#else
                 bp_two_rows(jj[j / 2], sn2, fr2, mm, row, dx, dy, y0, y1);
+#endif
                 acc[j] = fmaf(__saturatef(fmaf(-dx, m, 1.0f)), y0.x,
                               fmaf(__saturatef(fmaf(dx, m, om)), y0.y, acc[j]));
                 acc[j + 1] = fmaf(__saturatef(fmaf(-dy, m, 1.0f)), y1.x,

@@ -92,9 +92,24 @@ constexpr int kStages = 5;
 // and the fraction needs one more subtraction.  CLAMP confines positions to
 // [-ui, P - 2 - ui], i.e. into the zero guard cells, and skips lines
 // j >= lines of a short last chunk (warp-uniform).
+// In MC_CHECKED builds every pair index is checked against its line
+// (0 <= ui + floor(w) <= P - 2); a failed check sets the error word and the
+// sample reads zero.
+__device__ __forceinline__ float2 load_pair(const float2* stage, int idx, int j, int P, int* err)
+{
+#ifdef MC_CHECKED
+    const int q = idx - j * P;
+    if (q < 0 || q > P - 2) {
+        atomicExch(err, kErrBounds);
+        return make_float2(0.0f, 0.0f);
+    }
+#endif
+    return stage[idx];
+}
+
 template <int LC, bool CLAMP>
 __device__ __forceinline__ float sample_lines(const float2* stage, int ibase, float fr, float t, const float* mj,
-                                              float wlo, float whi, int lines, float acc)
+                                              float wlo, float whi, int lines, float acc, int P, int* err)
 {
     // two lines per step: position, floor and fraction in paired FP32 ops; the
     // round-down sum's bits are kMagicBits + floor(w) + j * P, so the pair's
@@ -111,10 +126,10 @@ __device__ __forceinline__ float sample_lines(const float2* stage, int ibase, fl
         const float2 t2 = __fadd2_rd(w2, make_float2(mj[j], mj[j + 1]));
         const float2 d2 = __fadd2_rn(t2, make_float2(-mj[j], -mj[j + 1]));     // floor(w), exact
         const float2 f2 = __ffma2_rn(d2, make_float2(-1.0f, -1.0f), w2);       // w - floor(w), exact
-        const float2 v0 = stage[ibase + __float_as_int(t2.x)];
+        const float2 v0 = load_pair(stage, ibase + __float_as_int(t2.x), j, P, err);
         acc += fmaf(f2.x, v0.y, v0.x);
         if (CLAMP && j + 1 >= lines) break;
-        const float2 v1 = stage[ibase + __float_as_int(t2.y)];
+        const float2 v1 = load_pair(stage, ibase + __float_as_int(t2.y), j + 1, P, err);
         acc += fmaf(f2.y, v1.y, v1.x);
     }
     return acc;
@@ -354,11 +369,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 if (ch < gs.c_lo || ch > gs.c_hi) continue;
                 const int ib = ui[m] - kMagicBits;
                 if (ch >= gs.in_lo && ch <= gs.in_hi) {
+#ifdef MC_CHECKED
+                    acc[m] = sample_lines<LC, false>(sp, ib, frac[m], gs.t, mj, 0.0f, 0.0f, LC, acc[m], a.P, a.err);
+#else
                     const uint32_t gbase = (uint32_t)__cvta_generic_to_shared(sp) + ((uint32_t)ib << 3);
                     acc[m] = sample_interior<LC>(gbase, pk2(gs.t, gs.t), pk2(frac[m], frac[m]), jj, mm, acc[m]);
+#endif
                 } else {
                     const float wlo = -(float)ui[m], whi = (float)(a.P - 2 - ui[m]);
-                    acc[m] = sample_lines<LC, true>(sp, ib, frac[m], gs.t, mj, wlo, whi, lines, acc[m]);
+                    acc[m] = sample_lines<LC, true>(sp, ib, frac[m], gs.t, mj, wlo, whi, lines, acc[m], a.P, a.err);
                 }
                 // advance to the first line of the next chunk: u -= LC * t
                 float nf = frac[m] - gs.step_frac;

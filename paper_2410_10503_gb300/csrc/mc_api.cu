@@ -592,6 +592,9 @@ mc_status finish(mc_ctx* c)
 {
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(c, MC_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
+#ifdef MC_CHECKED
+    TRY(check_err_word(c));       // bounds checks of the checked build
+#endif
     if (c->prof_on) TRY(prof_collect(c));
     return MC_OK;
 }
