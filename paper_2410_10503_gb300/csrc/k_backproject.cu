@@ -32,7 +32,7 @@ namespace mcg {
 namespace {
 
 constexpr int kGroups = 8;       // warps per block = interleaved angle groups
-constexpr int kChunk = 32;       // angles per staged chunk
+constexpr int kChunk = 64;       // angles per staged chunk
 constexpr uint32_t kWaitLimit = 1u << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)

@@ -399,41 +399,40 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 const int b = grp.y + lane;
                 if (b < nb) a.part[((size_t)item.band * a.na + grp.x) * nb + b] = acc[m];
             }
-            __syncwarp();
-            continue;
-        }
+        } else {
 #pragma unroll
-        for (int m = 0; m < RPT; ++m) {
-            if (m >= ns) break;
-            const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
-            const int k = grp.x, b = grp.y + lane;
-            if (b >= nb) continue;
-            const float delta = __ldg(&a.ang[k].delta);
-            const float val = delta * acc[m];
-            const size_t idx = (size_t)k * nb + b;
-            if (a.mode == 0) {
-                a.out[(size_t)slot * a.na * nb + idx] = val;
-            } else {
-                const size_t gi = (size_t)gate * a.na * nb + idx;
-                float yo, yn;
-                if (a.store == 0) {
-                    yo = a.y[gi];
-                    yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
-                    a.y[gi] = yn;
+            for (int m = 0; m < RPT; ++m) {
+                if (m >= ns) break;
+                const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+                const int k = grp.x, b = grp.y + lane;
+                if (b >= nb) continue;
+                const float delta = __ldg(&a.ang[k].delta);
+                const float val = delta * acc[m];
+                const size_t idx = (size_t)k * nb + b;
+                if (a.mode == 0) {
+                    a.out[(size_t)slot * a.na * nb + idx] = val;
                 } else {
-                    // reduced-precision d and y: arithmetic in float32, the new
-                    // y rounded on store and the increment taken from stored values
-                    yo = load_store(a.yh[gi], a.store);
-                    const float yf = (yo + a.sigma * (val - load_store(a.dh[gi], a.store))) * a.inv_den;
-                    const unsigned short q = to_store(yf, a.store);
-                    a.yh[gi] = q;
-                    yn = load_store(q, a.store);
+                    const size_t gi = (size_t)gate * a.na * nb + idx;
+                    float yo, yn;
+                    if (a.store == 0) {
+                        yo = a.y[gi];
+                        yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
+                        a.y[gi] = yn;
+                    } else {
+                        // reduced-precision d and y: arithmetic in float32, the new
+                        // y rounded on store and the increment taken from stored values
+                        yo = load_store(a.yh[gi], a.store);
+                        const float yf = (yo + a.sigma * (val - load_store(a.dh[gi], a.store))) * a.inv_den;
+                        const unsigned short q = to_store(yf, a.store);
+                        a.yh[gi] = q;
+                        yn = load_store(q, a.store);
+                    }
+                    // dy pairs scaled by the angle's step: (m dy[b], m dy[b+1])
+                    const float v = delta * (yn - yo);
+                    float* dyp = reinterpret_cast<float*>(a.dy + slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b);
+                    dyp[0] = v;
+                    dyp[-1] = v;
                 }
-                // dy pairs scaled by the angle's step: (m dy[b], m dy[b+1])
-                const float v = delta * (yn - yo);
-                float* dyp = reinterpret_cast<float*>(a.dy + slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b);
-                dyp[0] = v;
-                dyp[-1] = v;
             }
         }
         __syncwarp();
