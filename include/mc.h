@@ -144,7 +144,7 @@ mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out)
  * warm-up, CUDA events on the context's stream): the forward's lines per
  * staged chunk (2, 4, 8, as shared memory allows), work items per block and
  * ray-group slots per warp, and the backprojector's rows per thread (4, 8,
- * 16).  The fastest setting is kept; results are unchanged bit for bit by
+ * 14, 16).  The fastest setting is kept; results are unchanged bit for bit by
  * the item split and change within float32 rounding with the chunk size and
  * rows per thread.  out (nullable, host, 4 int32): {lines per chunk, items per
  * block, group slots per warp, rows per thread}.  Captured epoch graphs are

@@ -13,14 +13,17 @@
 //
 // A block owns a tile of 32 columns x PJ rows; its 8 warps all cover that
 // tile, each for every 8th angle, and their partial sums are added in a fixed
-// order through shared memory at the end.  Angles are processed in chunks of
-// kChunk: for each angle one bulk TMA copy brings the window of dy pairs that
-// the tile projects onto (WL pairs) into shared memory, double-buffered and
-// completed on an mbarrier, so the gathers are shared-memory loads whose lanes
-// (consecutive columns, |cos| <= 1 bin apart) rarely share a bank.  A thread
-// owns PJ consecutive rows of one column: per angle it forms beta of its first
-// pixel in float-pair arithmetic (integer bin + fraction) and steps the
-// fraction by sin(phi) down the column, two rows at a time in paired FP32
+// order through shared memory at the end.  Each warp runs its own staging
+// pipeline: for a batch of kBatch of its angles, lanes 0..kBatch-1 each issue
+// one bulk TMA copy of the window of dy pairs that the tile projects onto (WL
+// pairs) into the warp's half of a two-batch ring, completed on the warp's
+// mbarrier, and store the angle's constants beside it.  The next batch is in
+// flight while the warp gathers from the current one, and no warp waits for
+// another until the final sum, so the gathers are shared-memory loads whose
+// lanes (consecutive columns, |cos| <= 1 bin apart) rarely share a bank.  A
+// thread owns PJ consecutive rows of one column: per angle it forms beta of
+// its first pixel in float-pair arithmetic (integer bin + fraction) and steps
+// the fraction by sin(phi) down the column, two rows at a time in paired FP32
 // arithmetic, so d is exact to ~1e-6 whatever the image size.
 #include <algorithm>
 #include <cmath>
@@ -32,8 +35,15 @@ namespace mcg {
 namespace {
 
 constexpr int kGroups = 8;       // warps per block = interleaved angle groups
-constexpr int kChunk = 64;       // angles per staged chunk
+constexpr int kBatch = 8;        // angles per staged batch of one warp
+constexpr int kRing = 2;         // batches per warp in shared memory
 constexpr uint32_t kWaitLimit = 1u << 24;
+
+// Constants of one staged angle, next to its window.
+struct AngSlot {
+    float cos_hi, cos_lo, sin_hi, sin_lo, m;
+    int ws;                      // first pair of the window in the dy row
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -57,14 +67,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     return false;
 }
 
-// Issue the window copies of one chunk (warp 0; lane i handles angles i, i+32...).
-// Window of angle k: WL pairs of dy row k starting at ws (even, so the copy is
-// 16-byte aligned), covering every bin the tile's pixels project onto.  The
-// chunk's angles are k = sub + (k0 + i) * S (one angle subset; S = 1: all).
-__device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, int sub, int S, int k0,
-                                            int cnt, int wl,
-                                            float xmin, float xmax, float ymin, float ymax,
-                                            float2* buf, int* ws_out, uint64_t* bar)
+// Stage one batch of the calling warp's angles: lane i < cnt takes the
+// warp's angle q0 + i, i.e. k = sub + (g + (q0 + i) kGroups) S, stores its
+// constants and issues the copy of its window: WL pairs of dy row k from ws
+// (even, so the copy is 16-byte aligned), covering every bin the tile's
+// pixels project onto.
+__device__ __forceinline__ void issue_batch(const BpArgs& a, const float2* dys, int sub, int S, int g, int q0,
+                                            int cnt, int wl, float xmin, float xmax, float ymin, float ymax,
+                                            float2* win, AngSlot* slots, uint64_t* bar)
 {
     const int lane = threadIdx.x & 31;
     if (lane == 0) {
@@ -73,22 +83,22 @@ __device__ __forceinline__ void issue_chunk(const BpArgs& a, const float2* dys, 
                      : "memory");
     }
     __syncwarp();
-    const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
-    for (int i = lane; i < cnt; i += 32) {
-        const int k = sub + (k0 + i) * S;
+    if (lane < cnt) {
+        const int k = sub + (g + (q0 + lane) * kGroups) * S;
         const BpAngle T = a.ang[k];
-        const float cs = T.cos_hi, sn = T.sin_hi;
-        const float b1 = fminf(xmin * cs, xmax * cs) + fminf(ymin * sn, ymax * sn) + offb;
+        const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
+        const float b1 = fminf(xmin * T.cos_hi, xmax * T.cos_hi) + fminf(ymin * T.sin_hi, ymax * T.sin_hi) + offb;
         int ws = ((int)floorf(b1) - 2) & ~1;
         ws = max(0, min(ws, a.Pb - wl));
-        ws_out[i] = ws;
+        slots[lane] = AngSlot{T.cos_hi, T.cos_lo, T.sin_hi, T.sin_lo, T.m, ws};
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                smem_u32(buf + (size_t)i * wl)),
+                smem_u32(win + (size_t)lane * wl)),
             "l"(dys + (size_t)k * a.Pb + ws), "r"((uint32_t)(wl * sizeof(float2))), "r"(smem_u32(bar))
             : "memory");
     }
+    __syncwarp();
 }
 
 
@@ -130,10 +140,9 @@ template <int PJ, bool SUB>
 __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    int* s_ws = reinterpret_cast<int*>(smem + 64);                          // [2][kChunk]
-    BpAngle* s_ang = reinterpret_cast<BpAngle*>(smem + 64 + 2 * kChunk * sizeof(int));   // [2][kChunk]
-    float2* s_win = reinterpret_cast<float2*>(smem + 64 + 2 * kChunk * (sizeof(int) + sizeof(BpAngle)));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);                             // [kGroups][kRing]
+    AngSlot* s_slot = reinterpret_cast<AngSlot*>(smem + 128);                       // [kGroups][kRing][kBatch]
+    float2* s_win = reinterpret_cast<float2*>(smem + 128 + kGroups * kRing * kBatch * sizeof(AngSlot));
     const int wl = a.wl;
     const int n = a.n;
     const int slot = blockIdx.z;
@@ -149,21 +158,26 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     // tile extent in centred coordinates (columns past the image are clamped)
     const float xmin = (float)(blockIdx.x * 32) - h, xmax = (float)min(blockIdx.x * 32 + 31, n - 1) - h;
     const float ymin = Y0, ymax = Y0 + (float)(PJ - 1);
-    // angles of this launch: one angle subset of the drawn block, or all
+    // angles of this launch: one angle subset of the drawn block, or all;
+    // this warp takes the subset's angles g, g + kGroups, ...
     const int S = SUB ? a.sel.subsets : 1;
     const int sub = SUB ? sel_subset(a.sel, slot) : 0;
     const int na_s = SUB ? (a.na - sub + S - 1) / S : a.na;
-    const int nck = (na_s + kChunk - 1) / kChunk;
+    const int nq = na_s > g ? (na_s - g + kGroups - 1) / kGroups : 0;
+    const int nbt = (nq + kBatch - 1) / kBatch;
+    uint64_t* my_full = full + g * kRing;
+    AngSlot* my_slot = s_slot + g * kRing * kBatch;
+    float2* my_win = s_win + (size_t)g * kRing * kBatch * wl;
 
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[1])) : "memory");
+    if (lane == 0) {
+        for (int i = 0; i < kRing; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&my_full[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    if (g == 0)
-        issue_chunk(a, dys, sub, S, 0, min(kChunk, na_s), wl, xmin, xmax, ymin, ymax, s_win, s_ws,
-                    &full[0]);
+    __syncwarp();
+    if (nbt > 0)
+        issue_batch(a, dys, sub, S, g, 0, min(kBatch, nq), wl, xmin, xmax, ymin, ymax, my_win, my_slot,
+                    &my_full[0]);
 
     float acc[PJ];
 #pragma unroll
@@ -173,28 +187,27 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     for (int j = 0; j < PJ; j += 2) jj[j / 2] = bp_pk2((float)j, (float)(j + 1));
     const unsigned long long mm = bp_pk2(kMagic, kMagic);
 
-    for (int ch = 0; ch < nck; ++ch) {
-        const int buf = ch & 1;
-        const int k0 = ch * kChunk;
-        const int cnt = min(kChunk, na_s - k0);
-        // angle table of this chunk, and the next chunk's windows in flight
-        for (int i = threadIdx.x; i < cnt; i += 256) s_ang[buf * kChunk + i] = a.ang[sub + (k0 + i) * S];
-        if (g == 0 && ch + 1 < nck)
-            issue_chunk(a, dys, sub, S, k0 + kChunk, min(kChunk, na_s - k0 - kChunk), wl, xmin, xmax, ymin,
-                        ymax, s_win + (size_t)(buf ^ 1) * kChunk * wl, s_ws + (buf ^ 1) * kChunk,
-                        &full[buf ^ 1]);
-        __syncthreads();
-        if (!mbar_wait(&full[buf], (uint32_t)((ch >> 1) & 1), kWaitLimit)) {
-            // a copy never landed: report, then give the other stage a bounded chance to land
-            if (threadIdx.x == 0) {
-                atomicExch(a.err, kErrTimeout);
-                mbar_wait(&full[buf ^ 1], (uint32_t)(((ch + 1) >> 1) & 1), 1u << 16);
-            }
-            return;
+    for (int bt = 0; bt < nbt; ++bt) {
+        const int st = bt & 1;
+        const int cnt = min(kBatch, nq - bt * kBatch);
+        // the next batch goes into the other half of the ring, which this warp
+        // finished reading in the previous iteration
+        if (bt + 1 < nbt)
+            issue_batch(a, dys, sub, S, g, (bt + 1) * kBatch, min(kBatch, nq - (bt + 1) * kBatch), wl, xmin, xmax,
+                        ymin, ymax, my_win + (size_t)(st ^ 1) * kBatch * wl, my_slot + (st ^ 1) * kBatch,
+                        &my_full[st ^ 1]);
+        if (!mbar_wait(&my_full[st], (uint32_t)((bt >> 1) & 1), kWaitLimit)) {
+            // a copy never landed: report, give the batch in flight a bounded
+            // chance to land, and skip the rest (the block still meets at the
+            // final barrier; the call returns the error)
+            if (lane == 0) atomicExch(a.err, kErrTimeout);
+            if (bt + 1 < nbt) mbar_wait(&my_full[st ^ 1], (uint32_t)(((bt + 1) >> 1) & 1), 1u << 16);
+            break;
         }
-        const uint32_t wbase = smem_u32(s_win + (size_t)buf * kChunk * wl) - ((uint32_t)kMagicBits << 3);
-        for (int i = g; i < cnt; i += kGroups) {
-            const BpAngle T = s_ang[buf * kChunk + i];
+        const float2* wb = my_win + (size_t)st * kBatch * wl;
+        const uint32_t wbase = smem_u32(wb) - ((uint32_t)kMagicBits << 3);
+        for (int i = 0; i < cnt; ++i) {
+            const AngSlot T = my_slot[st * kBatch + i];
             float ah, al, bh, bl, s, e, s2, e2;
             mul_df(X, T.cos_hi, T.cos_lo, ah, al);
             mul_df(Y0, T.sin_hi, T.sin_lo, bh, bl);
@@ -203,11 +216,11 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
             int bi;
             float frac;
             split_int_frac(s2, (al + bl) + (e + e2), bi, frac);
-            const uint32_t row = wbase + ((uint32_t)(i * wl + bi - s_ws[buf * kChunk + i]) << 3);
+            const uint32_t row = wbase + ((uint32_t)(i * wl + bi - T.ws) << 3);
             const float m = T.m, om = 1.0f - T.m, sn = T.sin_hi;
             const unsigned long long sn2 = bp_pk2(sn, sn), fr2 = bp_pk2(frac, frac);
 #ifdef MC_CHECKED
-            const int wofs = bi - s_ws[buf * kChunk + i];     // window offset of beta's integer part
+            const int wofs = bi - T.ws;                       // window offset of beta's integer part
 #endif
 #pragma unroll
             for (int j = 0; j < PJ; j += 2) {
@@ -224,7 +237,7 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
                 dy = b2.y - fb2.y;
                 const int o0 = wofs + (__float_as_int(t2.x) - kMagicBits);
                 const int o1 = wofs + (__float_as_int(t2.y) - kMagicBits);
-                const float2* win = reinterpret_cast<const float2*>(s_win + (size_t)buf * kChunk * wl) + (size_t)i * wl;
+                const float2* win = wb + (size_t)i * wl;
                 y0 = make_float2(0.0f, 0.0f);
                 y1 = make_float2(0.0f, 0.0f);
                 if (o0 >= 0 && o0 <= wl - 1) y0 = win[o0]; else atomicExch(a.err, kErrBounds);
@@ -238,9 +251,11 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
                                   fmaf(__saturatef(fmaf(dy, m, om)), y1.y, acc[j + 1]));
             }
         }
-        __syncthreads();
+        __syncwarp();
     }
-    // fixed-order sum of the eight angle groups (reusing the window buffers)
+    // fixed-order sum of the eight angle groups (reusing the window buffers
+    // once every warp is done with them)
+    __syncthreads();
     float* s_red = reinterpret_cast<float*>(s_win);                         // [kGroups][PJ][32]
 #pragma unroll
     for (int j = 0; j < PJ; ++j) s_red[(g * PJ + j) * 32 + lane] = acc[j];
@@ -260,12 +275,13 @@ int backproject_window(int pj) { return ((int)std::ceil(std::sqrt(31.0 * 31.0 + 
 
 size_t backproject_smem_bytes(int pj)
 {
-    const size_t win = 2 * (size_t)kChunk * backproject_window(pj) * sizeof(float2);
+    const size_t win = (size_t)kGroups * kRing * kBatch * backproject_window(pj) * sizeof(float2);
     const size_t red = (size_t)kGroups * pj * 32 * sizeof(float);
-    return 64 + 2 * kChunk * (sizeof(int) + sizeof(BpAngle)) + std::max(win, red);
+    return 128 + kGroups * kRing * kBatch * sizeof(AngSlot) + std::max(win, red);
 }
 
-#define MC_BP_INSTANCES(X) X(4, false) X(8, false) X(16, false) X(4, true) X(8, true) X(16, true)
+#define MC_BP_INSTANCES(X) \
+    X(4, false) X(8, false) X(14, false) X(16, false) X(4, true) X(8, true) X(14, true) X(16, true)
 
 cudaError_t backproject_prepare()
 {

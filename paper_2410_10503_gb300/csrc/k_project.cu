@@ -486,6 +486,10 @@ __global__ void __launch_bounds__(256) k_forward_combine(FwdArgs a)
 
 int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
 
+int forward_consumer_warps() { return kConsumers; }
+
+int forward_ring_stages() { return kStages; }
+
 int forward_static_smem() { return (int)(kConsumers * 8 * sizeof(GroupState)); }
 
 size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }

@@ -724,6 +724,99 @@ void partition_items(const GroupTable& gt, int sms, int ipb_start, std::vector<R
     }
 }
 
+// Chunks of lc lines that group {k, b0} visits in k_forward, with the cost of
+// each: the group's rays cover lines [lo, hi] (the kernel's estimate, widened
+// by one line on each side); a chunk that every lane's ray crosses is an
+// interior chunk, any other chunk in the union an edge chunk (clamped
+// positions, about 1.6 times the work).  Costs are in units of one interior
+// chunk; each visited chunk also carries the per-chunk set-up of the group.
+void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float>& cost)
+{
+    const int n = c->n, nb = c->nb, nch = (n + lc - 1) / lc;
+    const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
+    const double inv = c->inv_k[k], t = c->t_k[k];
+    cost.assign(nch, 0.0f);
+    int lo_min = n, hi_max = -1, lo_max = -1, hi_min = n;
+    for (int l = 0; l < 32; ++l) {
+        const int b = std::min(b0 + l, nb - 1);
+        const double u0 = h * t + (b - hb) * inv + h + kGuard;
+        int lo = n, hi = -1;
+        if (std::fabs(t) < 1e-6) {
+            if (u0 > kGuard - 2.0 && u0 < kGuard + n + 1.0) { lo = 0; hi = n - 1; }
+        } else {
+            const double e1 = (u0 - (kGuard + n)) / t, e3 = (u0 - (kGuard - 1)) / t;
+            const double llo = std::max(std::floor(std::min(e1, e3)) - 1.0, 0.0);
+            const double lhi = std::min(std::ceil(std::max(e1, e3)) + 1.0, (double)(n - 1));
+            if (llo <= lhi) { lo = (int)llo; hi = (int)lhi; }
+        }
+        lo_min = std::min(lo_min, lo); hi_max = std::max(hi_max, hi);
+        lo_max = std::max(lo_max, lo); hi_min = std::min(hi_min, hi);
+    }
+    if (hi_max < lo_min) return;
+    const bool any_interior = hi_min >= lo_max;
+    const int in_lo = (lo_max + lc - 1) / lc, in_hi = (hi_min + 1) / lc - 1;
+    for (int ch = lo_min / lc; ch <= hi_max / lc; ++ch)
+        cost[ch] = (any_interior && ch >= in_lo && ch <= in_hi) ? 1.3f : 1.9f;
+}
+
+// Order the groups of every item so that k_forward's fixed mapping (the p-th
+// group of an item goes to consumer warp p % W, slot p / W) hands each warp
+// about the same work in every stretch of chunks.  The ring lets warps drift
+// apart by only kStages - 1 chunks, so a warp with more active groups than
+// its neighbours over such a stretch holds the whole block back; a
+// round-robin deal of groups in angle/bin order left the busiest warp with
+// ~1.5x the mean work.  Greedy: groups by decreasing total cost, each to the
+// warp (with a free slot) whose cost summed over a window of 2 kStages - 1
+// chunks would peak lowest.  The order of groups within an item changes no
+// result: each group's rays are summed by one warp in line order either way.
+void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, const std::vector<RayItem>& items)
+{
+    const int W = forward_consumer_warps(), half = forward_ring_stages() - 1;
+    const int nch = (c->n + lc - 1) / lc;
+    std::vector<std::vector<float>> win;        // windowed cost per group of the item
+    std::vector<float> cost, load, total;
+    std::vector<int> idx, slot_of;
+    std::vector<std::vector<int>> lists(W);
+    std::vector<int2> out;
+    for (const RayItem& it : items) {
+        const int m = it.end - it.begin;
+        if (m <= 1) continue;
+        win.assign(m, std::vector<float>(nch, 0.0f));
+        total.assign(m, 0.0f);
+        for (int g = 0; g < m; ++g) {
+            const int2 grp = groups[it.begin + g];
+            group_chunk_costs(c, grp.x, grp.y, lc, cost);
+            for (int ch = 0; ch < nch; ++ch) {
+                if (cost[ch] == 0.0f) continue;
+                total[g] += cost[ch];
+                for (int q = std::max(0, ch - half); q <= std::min(nch - 1, ch + half); ++q) win[g][q] += cost[ch];
+            }
+        }
+        idx.resize(m);
+        for (int g = 0; g < m; ++g) idx[g] = g;
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return total[a] > total[b]; });
+        load.assign((size_t)W * nch, 0.0f);
+        for (auto& L : lists) L.clear();
+        for (int g : idx) {
+            int best_w = -1;
+            float best = 0.0f;
+            for (int w = 0; w < W; ++w) {
+                const int cap = w < m ? (m - w + W - 1) / W : 0;
+                if ((int)lists[w].size() >= cap) continue;
+                float peak = 0.0f;
+                for (int ch = 0; ch < nch; ++ch) peak = std::max(peak, load[(size_t)w * nch + ch] + win[g][ch]);
+                if (best_w < 0 || peak < best) { best = peak; best_w = w; }
+            }
+            lists[best_w].push_back(g);
+            for (int ch = 0; ch < nch; ++ch) load[(size_t)best_w * nch + ch] += win[g][ch];
+        }
+        out.assign(m, make_int2(0, 0));
+        for (int w = 0; w < W; ++w)
+            for (size_t s = 0; s < lists[w].size(); ++s) out[w + s * W] = groups[it.begin + lists[w][s]];
+        std::copy(out.begin(), out.end(), groups.begin() + it.begin);
+    }
+}
+
 mc_status build_tables(mc_ctx* c)
 {
     const int n = c->n, na = c->na, nb = c->nb;
@@ -772,6 +865,7 @@ mc_status build_tables(mc_ctx* c)
     std::vector<int> set_off;
     int rpt = 2, ipb = 1;
     partition_items(gt, c->sms, 1, items, set_off, ipb, rpt);
+    balance_items(c, c->lc, gt.groups, items);
     const std::vector<int2>& groups = gt.groups;
     c->ipb = ipb;
     c->rpt = rpt;
@@ -787,12 +881,18 @@ mc_status build_tables(mc_ctx* c)
     CK(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));   // host vectors go out of scope
-    // backprojection tiles: 32 columns x pj rows per block of 8 warps; the
-    // largest pj that still gives about 24 warps per SM
+    // backprojection tiles: 32 columns x pj rows per block of 8 warps.  Among
+    // the tile heights that still give about 24 warps per SM, the one whose
+    // busiest SM does the least work: ceil(blocks / SMs) tiles, each costing
+    // about 8 pj + 30 instructions per angle and lane (pj rows plus the
+    // per-angle set-up), so that the grid fills whole waves
     c->pj = 4;
-    for (int pj : {16, 8}) {
-        const long long warps = 8LL * ((n + 31) / 32) * ((n + pj - 1) / pj);
-        if (warps >= 24LL * c->sms) { c->pj = pj; break; }
+    long long best_cost = -1;
+    for (int pj : {16, 14, 8}) {
+        const long long blocks = (long long)((n + 31) / 32) * ((n + pj - 1) / pj);
+        if (8 * blocks < 24LL * c->sms) continue;
+        const long long cost = (blocks + c->sms - 1) / c->sms * (8LL * pj + 30);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; c->pj = pj; }
     }
     // dual increment layout: guards wide enough for every pixel's two bins
     const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
@@ -1162,9 +1262,12 @@ mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min)
     int ipb = 1, rpt = 2;
     partition_items(gt, c->sms, ipb_start, items, off, ipb, rpt);
     while (rpt < rpt_min && rpt < 8) rpt <<= 1;
+    balance_items(c, lc, gt.groups, items);     // the group order depends on the cut and lc
     dfree(c, &c->d_items);
     TRY(dalloc(c, &c->d_items, items.size()));
     CK(cudaMemcpyAsync(c->d_fang, fa.data(), fa.size() * sizeof(FwdAngle), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_groups, gt.groups.data(), gt.groups.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                       c->stream));
     CK(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1227,7 +1330,7 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
     // backprojection: rows per thread
     int best_pj = c->pj;
     float best_bp = 1e30f;
-    for (int pj : {4, 8, 16}) {
+    for (int pj : {4, 8, 14, 16}) {
         if (st != MC_OK) break;
         c->pj = pj;
         float ms = 0;
@@ -1271,6 +1374,7 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
         std::vector<int> cut_off;
         int ipb = 1, rpt = 2;
         partition_items(gt, std::max(1, c->sms / bands), 1, cut, cut_off, ipb, rpt);
+        balance_items(c, c->lc, gt.groups, cut);   // one order serves every band of a cut
         std::vector<RayItem> items;
         std::vector<int> off(1, 0);
         for (int q = 0; q < subsets; ++q) {

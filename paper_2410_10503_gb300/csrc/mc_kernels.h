@@ -125,6 +125,8 @@ struct FwdArgs {
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 int forward_groups_per_block(int rpt);
+int forward_consumer_warps();         // consumer warps per block
+int forward_ring_stages();            // chunks in flight (the drift between warps)
 int forward_static_smem();           // static shared memory of the largest instance
 size_t forward_smem_bytes(int lc, int P);
 cudaError_t forward_prepare(int max_smem);
@@ -138,7 +140,7 @@ struct BpArgs {
     const BpAngle* ang;
     int n, na, nb;
     int n_slots;
-    int pj;                    // pixels per thread along a column (4, 8 or 16)
+    int pj;                    // pixels per thread along a column (4, 8, 14 or 16)
     float* out;                // slot stride n*n
     int* err;
     int wl;                    // staged window length (pairs), set by the launcher
