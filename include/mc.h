@@ -317,7 +317,7 @@ const char* mc_version(void);
  * in one fixed 24 MiB device array built into the library, which every device
  * that loads the library holds until the process exits; the call makes no
  * cudaMalloc, cudaFree or other allocation.  Sizes whose scratch exceeds the
- * array (about n > 1150 at 720 angles) return MC_EINVAL.  The first call on
+ * array (about n > 1220 at 720 angles) return MC_EINVAL.  The first call on
  * each device sets up (looks up the array's device address, sets kernel
  * attributes); make that first call before any stream capture.  Every call
  * shares the array: calls that overlap on the GPU (different streams, or

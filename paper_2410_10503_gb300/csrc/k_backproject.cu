@@ -20,11 +20,14 @@
 // mbarrier, and store the angle's constants beside it.  The next batch is in
 // flight while the warp gathers from the current one, and no warp waits for
 // another until the final sum, so the gathers are shared-memory loads whose
-// lanes (consecutive columns, |cos| <= 1 bin apart) rarely share a bank.  A
-// thread owns PJ consecutive rows of one column: per angle it forms beta of
-// its first pixel in float-pair arithmetic (integer bin + fraction) and steps
-// the fraction by sin(phi) down the column, two rows at a time in paired FP32
-// arithmetic, so d is exact to ~1e-6 whatever the image size.
+// lanes (consecutive columns, |cos| <= 1 bin apart) rarely share a bank.
+//
+// Positions: the staging lane forms beta at the tile's first pixel in
+// float-pair arithmetic (integer bin + fraction f0); column c0 + l adds
+// l cos, split on the host as cos_h19 + cos_l19 with l cos_h19 exact, so a
+// lane's fraction costs two FMAs and a floor and is within ~2e-6 of exact.
+// A thread owns PJ consecutive rows of one column and steps the fraction by
+// sin(phi) down the column, two rows at a time in paired FP32 arithmetic.
 #include <algorithm>
 #include <cmath>
 
@@ -39,10 +42,14 @@ constexpr int kBatch = 8;        // angles per staged batch of one warp
 constexpr int kRing = 2;         // batches per warp in shared memory
 constexpr uint32_t kWaitLimit = 1u << 24;
 
-// Constants of one staged angle, next to its window.
-struct AngSlot {
-    float cos_hi, cos_lo, sin_hi, sin_lo, m;
-    int ws;                      // first pair of the window in the dy row
+// Constants of one staged angle, next to its window (two 16-byte loads; the
+// first pair of words is the packed row step).
+struct __align__(16) AngSlot {
+    float sin0, sin1;            // sin(phi) twice
+    float cos_h, cos_l;          // cos(phi) = cos_h + cos_l, l * cos_h exact
+    float m, om;                 // hat slope m and 1 - m
+    float f0;                    // fraction of beta at the tile's first pixel
+    int off;                     // window pair of beta's integer part there, plus slot * WL
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -68,12 +75,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
 }
 
 // Stage one batch of the calling warp's angles: lane i < cnt takes the
-// warp's angle q0 + i, i.e. k = sub + (g + (q0 + i) kGroups) S, stores its
-// constants and issues the copy of its window: WL pairs of dy row k from ws
-// (even, so the copy is 16-byte aligned), covering every bin the tile's
-// pixels project onto.
+// warp's angle q0 + i, i.e. k = sub + (g + (q0 + i) kGroups) S, forms beta of
+// the tile's first pixel (X0, Y0), stores the angle's constants and issues
+// the copy of its window: WL pairs of dy row k from ws (even, so the copy is
+// 16-byte aligned), covering every bin the tile's pixels project onto.
 __device__ __forceinline__ void issue_batch(const BpArgs& a, const float2* dys, int sub, int S, int g, int q0,
-                                            int cnt, int wl, float xmin, float xmax, float ymin, float ymax,
+                                            int cnt, int wl, float X0, float Y0, float xmax, float ymax,
                                             float2* win, AngSlot* slots, uint64_t* bar)
 {
     const int lane = threadIdx.x & 31;
@@ -87,10 +94,20 @@ __device__ __forceinline__ void issue_batch(const BpArgs& a, const float2* dys, 
         const int k = sub + (g + (q0 + lane) * kGroups) * S;
         const BpAngle T = a.ang[k];
         const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
-        const float b1 = fminf(xmin * T.cos_hi, xmax * T.cos_hi) + fminf(ymin * T.sin_hi, ymax * T.sin_hi) + offb;
+        const float b1 = fminf(X0 * T.cos_hi, xmax * T.cos_hi) + fminf(Y0 * T.sin_hi, ymax * T.sin_hi) + offb;
         int ws = ((int)floorf(b1) - 2) & ~1;
         ws = max(0, min(ws, a.Pb - wl));
-        slots[lane] = AngSlot{T.cos_hi, T.cos_lo, T.sin_hi, T.sin_lo, T.m, ws};
+        // beta(X0, Y0) = X0 cos + Y0 sin + offb as integer + fraction
+        float ah, al, bh, bl, s, e, s2, e2;
+        mul_df(X0, T.cos_hi, T.cos_lo, ah, al);
+        mul_df(Y0, T.sin_hi, T.sin_lo, bh, bl);
+        two_sum(ah, bh, s, e);
+        two_sum(s, offb, s2, e2);
+        int bi;
+        float f0;
+        split_int_frac(s2, (al + bl) + (e + e2), bi, f0);
+        slots[lane] = AngSlot{T.sin_hi, T.sin_hi, T.cos_h19, T.cos_l19, T.m, 1.0f - T.m, f0,
+                              lane * wl + bi - ws};
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -109,6 +126,7 @@ __device__ __forceinline__ unsigned long long bp_pk2(float a, float b)
     return r;
 }
 
+#ifndef MC_CHECKED
 // Two rows of one column, as PTX on packed pairs: beta = j sn + frac, its
 // floor through the round-down magic add (whose bits also give the window
 // index), the fraction d, then the two 8-byte shared loads of the rows' dy
@@ -136,6 +154,8 @@ __device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long
         : "l"(jj), "l"(sn2), "l"(fr2), "l"(mm), "r"(row));
 }
 
+#endif
+
 template <int PJ, bool SUB>
 __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 {
@@ -147,17 +167,14 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     const int n = a.n;
     const int slot = blockIdx.z;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int c = blockIdx.x * 32 + lane;
+    const int c0 = blockIdx.x * 32, c = c0 + lane;
     const int r0 = blockIdx.y * PJ;
-    const int cc = min(c, n - 1);
     const float h = 0.5f * (float)(n - 1);
-    const float X = (float)cc - h;                 // exact
-    const float Y0 = (float)r0 - h;                // exact
-    const float offb = 0.5f * (float)(a.nb - 1) + (float)a.Gb;
+    const float le = (float)min(lane, n - 1 - c0);       // column offset in the tile (clamped at the edge)
     const float2* dys = a.dy + slot * a.dy_stride;
     // tile extent in centred coordinates (columns past the image are clamped)
-    const float xmin = (float)(blockIdx.x * 32) - h, xmax = (float)min(blockIdx.x * 32 + 31, n - 1) - h;
-    const float ymin = Y0, ymax = Y0 + (float)(PJ - 1);
+    const float X0 = (float)c0 - h, xmax = (float)min(c0 + 31, n - 1) - h;   // exact
+    const float Y0 = (float)r0 - h, ymax = Y0 + (float)(PJ - 1);
     // angles of this launch: one angle subset of the drawn block, or all;
     // this warp takes the subset's angles g, g + kGroups, ...
     const int S = SUB ? a.sel.subsets : 1;
@@ -176,7 +193,7 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
     }
     __syncwarp();
     if (nbt > 0)
-        issue_batch(a, dys, sub, S, g, 0, min(kBatch, nq), wl, xmin, xmax, ymin, ymax, my_win, my_slot,
+        issue_batch(a, dys, sub, S, g, 0, min(kBatch, nq), wl, X0, Y0, xmax, ymax, my_win, my_slot,
                     &my_full[0]);
 
     float acc[PJ];
@@ -193,8 +210,8 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
         // the next batch goes into the other half of the ring, which this warp
         // finished reading in the previous iteration
         if (bt + 1 < nbt)
-            issue_batch(a, dys, sub, S, g, (bt + 1) * kBatch, min(kBatch, nq - (bt + 1) * kBatch), wl, xmin, xmax,
-                        ymin, ymax, my_win + (size_t)(st ^ 1) * kBatch * wl, my_slot + (st ^ 1) * kBatch,
+            issue_batch(a, dys, sub, S, g, (bt + 1) * kBatch, min(kBatch, nq - (bt + 1) * kBatch), wl, X0, Y0,
+                        xmax, ymax, my_win + (size_t)(st ^ 1) * kBatch * wl, my_slot + (st ^ 1) * kBatch,
                         &my_full[st ^ 1]);
         if (!mbar_wait(&my_full[st], (uint32_t)((bt >> 1) & 1), kWaitLimit)) {
             // a copy never landed: report, give the batch in flight a bounded
@@ -205,22 +222,21 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
             break;
         }
         const float2* wb = my_win + (size_t)st * kBatch * wl;
-        const uint32_t wbase = smem_u32(wb) - ((uint32_t)kMagicBits << 3);
+        // the row's pair index is off + floor(beta) + floor(j sin + frac): two
+        // magic-biased integers, so the base carries -2 kMagicBits
+        const uint32_t wbase = smem_u32(wb) - ((uint32_t)kMagicBits << 4);
         for (int i = 0; i < cnt; ++i) {
-            const AngSlot T = my_slot[st * kBatch + i];
-            float ah, al, bh, bl, s, e, s2, e2;
-            mul_df(X, T.cos_hi, T.cos_lo, ah, al);
-            mul_df(Y0, T.sin_hi, T.sin_lo, bh, bl);
-            two_sum(ah, bh, s, e);
-            two_sum(s, offb, s2, e2);
-            int bi;
-            float frac;
-            split_int_frac(s2, (al + bl) + (e + e2), bi, frac);
-            const uint32_t row = wbase + ((uint32_t)(i * wl + bi - T.ws) << 3);
-            const float m = T.m, om = 1.0f - T.m, sn = T.sin_hi;
-            const unsigned long long sn2 = bp_pk2(sn, sn), fr2 = bp_pk2(frac, frac);
+            const float4 A = *reinterpret_cast<const float4*>(my_slot + st * kBatch + i);   // sin, sin, cos_h, cos_l
+            const float4 B = *reinterpret_cast<const float4*>(&my_slot[st * kBatch + i].m); // m, 1 - m, f0, off
+            const float b0 = fmaf(le, A.w, fmaf(le, A.z, B.z));      // beta - floor(beta_tile), this column
+            const float tb = __fadd_rd(b0, kMagic);
+            const float frac = __fsub_rn(b0, __fsub_rn(tb, kMagic));  // b0 - floor(b0), one rounding at most
+            const uint32_t row = wbase + ((uint32_t)(__float_as_int(tb) + __float_as_int(B.w)) << 3);
+            const float m = B.x, om = B.y;
+            const unsigned long long sn2 = bp_pk2(A.x, A.y), fr2 = bp_pk2(frac, frac);
 #ifdef MC_CHECKED
-            const int wofs = bi - T.ws;                       // window offset of beta's integer part
+            const int wofs = (__float_as_int(tb) - kMagicBits) + __float_as_int(B.w) - i * wl;   // window offset
+            const float sn = A.x;
 #endif
 #pragma unroll
             for (int j = 0; j < PJ; j += 2) {

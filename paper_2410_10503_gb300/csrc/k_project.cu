@@ -12,15 +12,21 @@
 // its "empty" mbarrier, so warps drift by up to kStages - 1 chunks instead of
 // meeting at a block barrier every chunk.
 //
-// A group visits only the chunks its rays cross.  In interior chunks (every
-// lane's ray crosses all LC lines) a sample is an FMA for the position, one
-// round-down add whose bits give both floor and shared address, one 8-byte
-// shared load of the (w, next - w) pair and one FMA; in the few edge chunks
-// the position is clamped into the zero guard cells instead of predicating
-// lanes.  A ray's position is carried as an integer plus a float fraction:
-// computed in float-pair arithmetic at its first line, advanced between
-// chunks by the angle's exact integer/fraction split of LC * t, and stepped
-// by j * t inside a chunk, so interpolation weights stay exact to ~1e-6 px.
+// A group visits only the chunks its rays cross.  A sample is an FMA for the
+// position, one round-down add whose bits give both floor and shared address,
+// one 8-byte shared load of the (w, next - w) pair and one FMA.  A ray's
+// position is carried as an integer plus a float fraction: computed in
+// float-pair arithmetic at its first line, advanced between chunks by the
+// angle's exact integer/fraction split of LC * t, and stepped by j * t inside
+// a chunk, so interpolation weights stay exact to ~1e-6 px.  Every line has
+// kGuard = 17 zero pairs in front and at least 17 behind, and each chunk's
+// starting pair index ui is clamped to [LC - 1, kGuard + n + LC - 1].  With
+// |t| <= 1 and a fraction in [0, 1] a chunk's samples lie at pair indices
+// ui - (LC - 1) .. ui + LC, so every lane stays inside its line; and a lane
+// is clamped only when all of its samples in the chunk fall on zero pairs
+// (image coordinate <= -2 or >= n), where the clamped samples read zeros
+// too.  So the rays of a group that leave the image inside a chunk, or miss
+// it, need no predication and no separate edge path.
 #include "mc_kernels.h"
 
 namespace mcg {
@@ -85,16 +91,13 @@ constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
 constexpr int kBlock = kThreads + 32;        // plus one producer warp
 constexpr int kStages = 5;
 
-// Samples of one ray over the LC lines of an edge chunk (some lane's ray
-// leaves the image inside it).  The magic constant of line j is
-// kMagic + j * P: adding it with round-down leaves floor(w) + j * P in the
-// low mantissa bits, so the shared address of the pair is one shift-add away
-// and the fraction needs one more subtraction.  CLAMP confines positions to
-// [-ui, P - 2 - ui], i.e. into the zero guard cells, and skips lines
-// j >= lines of a short last chunk (warp-uniform).
-// In MC_CHECKED builds every pair index is checked against its line
-// (0 <= ui + floor(w) <= P - 2); a failed check sets the error word and the
-// sample reads zero.
+#ifdef MC_CHECKED
+// The samples of one ray over the LC lines of a chunk in C, the form used by
+// MC_CHECKED builds: the magic constant of line j is kMagic + j * P; adding it
+// with round-down leaves floor(w) + j * P in the low mantissa bits, so the
+// pair's index is ibase + bits with ibase = ui - kMagicBits, and every pair
+// index is checked against its line (0 <= ui + floor(w) <= P - 2); a failed
+// check sets the error word and the sample reads zero.
 __device__ __forceinline__ float2 load_pair(const float2* stage, int idx, int j, int P, int* err)
 {
 #ifdef MC_CHECKED
@@ -107,33 +110,25 @@ __device__ __forceinline__ float2 load_pair(const float2* stage, int idx, int j,
     return stage[idx];
 }
 
-template <int LC, bool CLAMP>
+template <int LC>
 __device__ __forceinline__ float sample_lines(const float2* stage, int ibase, float fr, float t, const float* mj,
-                                              float wlo, float whi, int lines, float acc, int P, int* err)
+                                              float acc, int P, int* err)
 {
-    // two lines per step: position, floor and fraction in paired FP32 ops; the
-    // round-down sum's bits are kMagicBits + floor(w) + j * P, so the pair's
-    // index is ibase + bits with ibase = ui - kMagicBits
 #pragma unroll
     for (int j = 0; j < LC; j += 2) {
-        if (CLAMP && j >= lines) break;
-        float2 w2 = __ffma2_rn(make_float2(-(float)j, -(float)(j + 1)), make_float2(t, t),
-                               make_float2(fr, fr));
-        if (CLAMP) {
-            w2.x = fminf(fmaxf(w2.x, wlo), whi);
-            w2.y = fminf(fmaxf(w2.y, wlo), whi);
-        }
+        const float2 w2 = __ffma2_rn(make_float2(-(float)j, -(float)(j + 1)), make_float2(t, t),
+                                     make_float2(fr, fr));
         const float2 t2 = __fadd2_rd(w2, make_float2(mj[j], mj[j + 1]));
         const float2 d2 = __fadd2_rn(t2, make_float2(-mj[j], -mj[j + 1]));     // floor(w), exact
         const float2 f2 = __ffma2_rn(d2, make_float2(-1.0f, -1.0f), w2);       // w - floor(w), exact
         const float2 v0 = load_pair(stage, ibase + __float_as_int(t2.x), j, P, err);
         acc += fmaf(f2.x, v0.y, v0.x);
-        if (CLAMP && j + 1 >= lines) break;
         const float2 v1 = load_pair(stage, ibase + __float_as_int(t2.y), j + 1, P, err);
         acc += fmaf(f2.y, v1.y, v1.x);
     }
     return acc;
 }
+#endif
 
 // Two FP32 values as one 64-bit register pair (the operand form of the
 // f32x2 instructions).
@@ -144,7 +139,7 @@ __device__ __forceinline__ unsigned long long pk2(float a, float b)
     return r;
 }
 
-// The same samples for an interior chunk, written as PTX on packed pairs:
+// The same samples written as PTX on packed pairs:
 // the line constants jj = (-j, -(j+1)) and mm = (magic_j, magic_{j+1}) stay
 // in registers for the whole kernel, tt = (t, t) and ff = (fr, fr) are
 // packed once per group and chunk, and gbase = shared address of the stage
@@ -181,11 +176,12 @@ __device__ __forceinline__ float sample_interior(uint32_t gbase, unsigned long l
     return acc;
 }
 
-// Per-warp, per-slot group description kept in shared memory.
-struct GroupState {
-    float t, step_frac;
-    int step_int, k;
-    int c_lo, c_hi, in_lo, in_hi;     // chunk range and interior chunk range
+// Per-warp, per-slot constants of the chunk loop, in shared memory: the
+// slope twice (one 16-byte load gives the packed operand of the position
+// FMA) and the exact split of the per-chunk advance.
+struct SlotState {
+    float t0, t1, step_frac;
+    int step_int;
 };
 
 // BANDED (angle-subset launches): an item also names a band of chunks
@@ -201,13 +197,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kStages;
     int* s_flag = reinterpret_cast<int*>(smem + 96);
-    __shared__ GroupState s_grp[kConsumers * RPT];
+    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
     float2* stage0 = reinterpret_cast<float2*>(smem + 128);
-    const size_t stage_pairs = (size_t)LC * a.P;
+    const size_t stage_pairs = (size_t)LC * a.P;   // one chunk: LC whole lines
 
     const int slot = blockIdx.y;
     const int n = a.n, nb = a.nb;
-    const int nch = (n + LC - 1) / LC;
+    const int nch = layout_lines(n) / LC;        // the layouts hold whole chunks (zero lines past n)
     // this launch's item table: all angles, or the drawn block's angle subset
     const int sub = sel_subset(a.sel, slot);
     const RayItem* items = a.sub_off ? a.items + a.sub_off[sub] : a.items;
@@ -247,10 +243,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                             break;
                         }
                         if (*(volatile int*)s_flag) { stop = true; break; }
-                        const int l0 = c * LC;
-                        const int lines = min(LC, n - l0);
-                        bulk_load(stage0 + st * stage_pairs, src + (size_t)l0 * a.P,
-                                  (uint32_t)(lines * a.P * sizeof(float2)), &full[st]);
+                        bulk_load(stage0 + st * stage_pairs, src + (size_t)c * stage_pairs,
+                                  (uint32_t)(stage_pairs * sizeof(float2)), &full[st]);
                     }
                 }
             } else {
@@ -265,10 +259,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                         break;
                     }
                     if (*(volatile int*)s_flag) break;
-                    const int l0 = c * LC;
-                    const int lines = min(LC, n - l0);
-                    bulk_load(stage0 + st * stage_pairs, src + (size_t)l0 * a.P,
-                              (uint32_t)(lines * a.P * sizeof(float2)), &full[st]);
+                    bulk_load(stage0 + st * stage_pairs, src + (size_t)c * stage_pairs,
+                              (uint32_t)(stage_pairs * sizeof(float2)), &full[st]);
                 }
             }
         }
@@ -283,13 +275,15 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     float mj[LC];
 #pragma unroll
     for (int j = 0; j < LC; ++j) mj[j] = kMagic + (float)(j * a.P);
-    GroupState* my = s_grp + warp * RPT;
+    SlotState* my = s_slot + warp * RPT;
     unsigned long long jj[LC / 2], mm[LC / 2];
 #pragma unroll
     for (int q = 0; q < LC / 2; ++q) {
         jj[q] = pk2(-(float)(2 * q), -(float)(2 * q + 1));
         mm[q] = pk2(mj[2 * q], mj[2 * q + 1]);
     }
+    // clamp of a chunk's first-line pair index (see the file comment)
+    const int ui_lo = LC - 1, ui_hi = kGuard + n + LC - 1;
 
     int q_run = 0;                        // BANDED: chunks consumed so far
     for (int it = 0; it < n_it; ++it) {
@@ -300,6 +294,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         const int ns = max(0, min(RPT, (item.end - item.begin - warp + kConsumers - 1) / kConsumers));
         float frac[RPT], acc[RPT];
         int ui[RPT];
+        int my_lo = nch, my_hi = -1;      // lane m < RPT: chunk range of slot m
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             acc[m] = 0.0f; frac[m] = 0.0f; ui[m] = 0;
@@ -311,7 +306,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
             const float B = (float)b - hb;                      // exact
             const float t = T.t_hi;
             // lines with a non-zero weight have u in (kGuard - 1, kGuard + n);
-            // widen by up to two lines (guards absorb the extra samples)
+            // widen by up to two lines (extra samples read zeros)
             const float u0 = fmaf(h, t, fmaf(B, T.inv_hi, off));
             int lo = n, hi = -1;
             if (fabsf(t) < 1e-6f) {
@@ -323,23 +318,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 const float l_hi = fminf(ceilf(fmaxf(e1, e3)) + 1.0f, (float)(n - 1));
                 if (l_lo <= l_hi) { lo = (int)l_lo; hi = (int)l_hi; }
             }
-            // group chunk range (union) and interior (every lane covers all LC lines)
+            // chunks of the group: the union of its rays' ranges
             const int lo_min = __reduce_min_sync(0xffffffffu, lo);
             const int hi_max = __reduce_max_sync(0xffffffffu, hi);
-            const int lo_max = __reduce_max_sync(0xffffffffu, lo);
-            const int hi_min = __reduce_min_sync(0xffffffffu, hi);
             const int c_lo = (hi_max >= lo_min) ? (BANDED ? max(lo_min / LC, cb0) : lo_min / LC) : nch;
             const int c_hi = (hi_max >= lo_min) ? (BANDED ? min(hi_max / LC, cb1 - 1) : hi_max / LC) : -1;
-            const int in_lo = (lo_max + LC - 1) / LC;
-            const int in_hi = (hi_min + 1) / LC - 1;
-            if (lane == 0) {
-                GroupState gs;
-                gs.t = t; gs.step_frac = T.step_frac; gs.step_int = T.step_int; gs.k = k;
-                gs.c_lo = c_lo; gs.c_hi = c_hi;
-                gs.in_lo = (hi_min >= lo_max && in_lo <= in_hi) ? in_lo : 1;
-                gs.in_hi = (hi_min >= lo_max && in_lo <= in_hi) ? in_hi : 0;
-                my[m] = gs;
-            }
+            if (lane == m) { my_lo = c_lo; my_hi = c_hi; }
+            if (lane == 0) my[m] = SlotState{t, t, T.step_frac, T.step_int};
             // position at the group's first line L = c_lo * LC:
             // u(L) = B inv - (L - h) t + h + guard, in float pairs
             const float L = (float)(min(c_lo, nch - 1) * LC) - h;   // exact
@@ -361,27 +346,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 return;
             }
             const float2* sp = stage0 + st * stage_pairs;
-            const int lines = min(LC, n - ch * LC);
+            // slots whose group crosses this chunk, one bit each
+            const uint32_t act = __ballot_sync(0xffffffffu, ch >= my_lo && ch <= my_hi);
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
-                if (m >= ns) break;
-                const GroupState gs = my[m];
-                if (ch < gs.c_lo || ch > gs.c_hi) continue;
-                const int ib = ui[m] - kMagicBits;
-                if (ch >= gs.in_lo && ch <= gs.in_hi) {
+                if (!((act >> m) & 1u)) continue;
+                const float4 gs = *reinterpret_cast<const float4*>(my + m);   // {t, t, step_frac, step_int}
+                const int ib = min(max(ui[m], ui_lo), ui_hi) - kMagicBits;
 #ifdef MC_CHECKED
-                    acc[m] = sample_lines<LC, false>(sp, ib, frac[m], gs.t, mj, 0.0f, 0.0f, LC, acc[m], a.P, a.err);
+                acc[m] = sample_lines<LC>(sp, ib, frac[m], gs.x, mj, acc[m], a.P, a.err);
 #else
-                    const uint32_t gbase = (uint32_t)__cvta_generic_to_shared(sp) + ((uint32_t)ib << 3);
-                    acc[m] = sample_interior<LC>(gbase, pk2(gs.t, gs.t), pk2(frac[m], frac[m]), jj, mm, acc[m]);
+                const uint32_t gbase = (uint32_t)__cvta_generic_to_shared(sp) + ((uint32_t)ib << 3);
+                acc[m] = sample_interior<LC>(gbase, pk2(gs.x, gs.y), pk2(frac[m], frac[m]), jj, mm, acc[m]);
 #endif
-                } else {
-                    const float wlo = -(float)ui[m], whi = (float)(a.P - 2 - ui[m]);
-                    acc[m] = sample_lines<LC, true>(sp, ib, frac[m], gs.t, mj, wlo, whi, lines, acc[m], a.P, a.err);
-                }
                 // advance to the first line of the next chunk: u -= LC * t
-                float nf = frac[m] - gs.step_frac;
-                int nu = ui[m] - gs.step_int;
+                float nf = frac[m] - gs.z;
+                int nu = ui[m] - __float_as_int(gs.w);
                 if (nf < 0.0f) { nf += 1.0f; nu -= 1; }
                 frac[m] = nf;
                 ui[m] = nu;
@@ -490,7 +470,7 @@ int forward_consumer_warps() { return kConsumers; }
 
 int forward_ring_stages() { return kStages; }
 
-int forward_static_smem() { return (int)(kConsumers * 8 * sizeof(GroupState)); }
+int forward_static_smem() { return (int)(kConsumers * 8 * sizeof(SlotState)); }
 
 size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }
 

@@ -47,6 +47,17 @@ void split_f(double v, float& hi, float& lo)
     lo = (float)(v - (double)hi);
 }
 
+// v = hi + lo with hi rounded to 19 significant bits (so hi times any integer
+// below 32 is exact in float32) and lo the float32 remainder.
+void split_f19(double v, float& hi, float& lo)
+{
+    int e = 0;
+    const double m = std::frexp(v, &e);                   // v = m 2^e, 0.5 <= |m| < 1
+    const double h = std::ldexp(std::nearbyint(std::ldexp(m, 19)), e - 19);
+    hi = (float)h;
+    lo = (float)(v - h);
+}
+
 Steps make_steps(double norm2, double alpha, int N, int n_iter_per_epoch)
 {
     // strongly convex PDHG/SPDHG steps: mu_g = 2 alpha, mu_f = N / 2
@@ -343,7 +354,7 @@ FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
         a.groups = c->d_sgroups; a.items = c->d_sitems; a.sub_off = c->d_soff;
         a.n_items = c->s_nitems; a.ipb = c->s_ipb; a.rpt = c->s_rpt;
         if (c->s_bands > 1) {
-            const int nch = (c->n + c->lc - 1) / c->lc;
+            const int nch = layout_lines(c->n) / c->lc;
             a.nbands = c->s_bands;
             a.cpb = (nch + c->s_bands - 1) / c->s_bands;
             a.part = c->d_bandpart;
@@ -724,19 +735,17 @@ void partition_items(const GroupTable& gt, int sms, int ipb_start, std::vector<R
     }
 }
 
-// Chunks of lc lines that group {k, b0} visits in k_forward, with the cost of
-// each: the group's rays cover lines [lo, hi] (the kernel's estimate, widened
-// by one line on each side); a chunk that every lane's ray crosses is an
-// interior chunk, any other chunk in the union an edge chunk (clamped
-// positions, about 1.6 times the work).  Costs are in units of one interior
-// chunk; each visited chunk also carries the per-chunk set-up of the group.
+// Chunks of lc lines that group {k, b0} visits in k_forward: its rays cover
+// lines [lo, hi] (the kernel's estimate, widened by one line on each side) and
+// the group visits the union of their chunks, each at the same cost (one
+// chunk of samples of all 32 lanes plus the per-chunk set-up of the group).
 void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float>& cost)
 {
-    const int n = c->n, nb = c->nb, nch = (n + lc - 1) / lc;
+    const int n = c->n, nb = c->nb, nch = layout_lines(n) / lc;
     const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
     const double inv = c->inv_k[k], t = c->t_k[k];
     cost.assign(nch, 0.0f);
-    int lo_min = n, hi_max = -1, lo_max = -1, hi_min = n;
+    int lo_min = n, hi_max = -1;
     for (int l = 0; l < 32; ++l) {
         const int b = std::min(b0 + l, nb - 1);
         const double u0 = h * t + (b - hb) * inv + h + kGuard;
@@ -750,13 +759,9 @@ void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float
             if (llo <= lhi) { lo = (int)llo; hi = (int)lhi; }
         }
         lo_min = std::min(lo_min, lo); hi_max = std::max(hi_max, hi);
-        lo_max = std::max(lo_max, lo); hi_min = std::min(hi_min, hi);
     }
     if (hi_max < lo_min) return;
-    const bool any_interior = hi_min >= lo_max;
-    const int in_lo = (lo_max + lc - 1) / lc, in_hi = (hi_min + 1) / lc - 1;
-    for (int ch = lo_min / lc; ch <= hi_max / lc; ++ch)
-        cost[ch] = (any_interior && ch >= in_lo && ch <= in_hi) ? 1.3f : 1.9f;
+    for (int ch = lo_min / lc; ch <= hi_max / lc; ++ch) cost[ch] = 1.0f;
 }
 
 // Order the groups of every item so that k_forward's fixed mapping (the p-th
@@ -772,7 +777,7 @@ void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float
 void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, const std::vector<RayItem>& items)
 {
     const int W = forward_consumer_warps(), half = forward_ring_stages() - 1;
-    const int nch = (c->n + lc - 1) / lc;
+    const int nch = layout_lines(c->n) / lc;
     std::vector<std::vector<float>> win;        // windowed cost per group of the item
     std::vector<float> cost, load, total;
     std::vector<int> idx, slot_of;
@@ -820,13 +825,13 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, const std
 mc_status build_tables(mc_ctx* c)
 {
     const int n = c->n, na = c->na, nb = c->nb;
-    // line layouts: kGuard zero pairs in front, >= 4 behind, 16-byte pitch;
-    // chunks of lc in {8, 4, 2} lines per ring stage (five stages of at most
-    // ~34 KB in the one block per SM)
-    c->P = ((n + 2 * kGuard) + 3) / 4 * 4;
-    c->layout_stride = (size_t)n * c->P;
+    // line layouts: kGuard zero pairs in front, >= kGuard behind, 16-byte
+    // pitch, lines padded to whole chunks; chunks of lc in {8, 4, 2} lines per
+    // ring stage (five stages of at most 36 KB in the one block per SM)
+    c->P = layout_pitch(n);
+    c->layout_stride = (size_t)layout_lines(n) * c->P;
     c->lc = 8;
-    while (c->lc > 2 && (size_t)c->lc * c->P * sizeof(float2) > 34816) c->lc >>= 1;
+    while (c->lc > 2 && (size_t)c->lc * c->P * sizeof(float2) > kMaxStageBytes) c->lc >>= 1;
     std::vector<FwdAngle> fa(na);
     std::vector<BpAngle> ba(na);
     std::vector<int> order;
@@ -850,6 +855,7 @@ mc_status build_tables(mc_ctx* c)
         split_f(sn, b.sin_hi, b.sin_lo);
         b.m = (float)std::fabs(inv);
         b.m2 = (float)(inv * inv);
+        split_f19(cs, b.cos_h19, b.cos_l19);
         ba[k] = b;
     }
     // forward ray groups: up to 32 consecutive bins of one angle, rows-driven
@@ -1305,7 +1311,7 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
     float best = 1e30f;
     for (int lc : {2, 4, 8}) {
         if (st != MC_OK) break;
-        if ((size_t)lc * c->P * sizeof(float2) > 34816) continue;
+        if ((size_t)lc * c->P * sizeof(float2) > kMaxStageBytes) continue;
         int ipb0 = 0;
         for (int step = 0; step < 3 && st == MC_OK; ++step) {
             const int ipb_try = ipb0 ? ipb0 + step : 1;

@@ -1,9 +1,11 @@
 // Device-side layouts, tables and helpers shared by the libmc kernels.
 //
 // HBM layouts (per gate slot):
-//   line layouts  Two copies of the warped image w = D_i x, each as n lines
-//                 of pitch P float2 "pairs" (w[p], w[p+1] - w[p]) with kGuard
-//                 zero cells before the data:
+//   line layouts  Two copies of the warped image w = D_i x, each as
+//                 layout_lines(n) lines (n rounded up to a multiple of 8, the
+//                 extra lines zero) of pitch P = layout_pitch(n) float2
+//                 "pairs" (w[p], w[p+1] - w[p]) with kGuard zero cells before
+//                 the data and at least kGuard after it:
 //                 ROWS  line l = image row l    (used by rows-driven angles),
 //                 COLS  line l = image column l (used by columns-driven angles).
 //                 One 8-byte load gives both interpolation taps, and the zero
@@ -21,7 +23,15 @@
 
 namespace mcg {
 
-constexpr int kGuard = 4;                 // zero cells before each image line
+constexpr int kGuard = 17;                // zero cells before each image line
+
+// Lines and pitch (pairs) of a line layout: whole chunks of up to 8 lines, and
+// room for the forward projector's clamped chunk positions (kGuard >= 2 x 8 + 1
+// zero pairs in front, P >= n + 2 kGuard).
+__host__ __device__ constexpr int layout_lines(int n) { return (n + 7) / 8 * 8; }
+__host__ __device__ constexpr int layout_pitch(int n) { return (n + 2 * kGuard + 3) / 4 * 4; }
+// Largest ring stage (bytes) of the forward projector: lc lines x P pairs.
+constexpr size_t kMaxStageBytes = 36864;
 constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 
@@ -46,7 +56,8 @@ struct BpAngle {
     float cos_hi, cos_lo, sin_hi, sin_lo;
     float m;                // 1/max(|sin|, |cos|): step length, also hat slope
     float m2;               // m*m
-    float pad0, pad1;
+    float cos_h19, cos_l19; // cos = cos_h19 + cos_l19 with at most 19 significant bits in
+                            // cos_h19, so that l * cos_h19 is exact for 0 <= l < 32
 };
 
 // Rigid warp of one gate: q = R(phi) p + t about the image centre, stored as

@@ -56,8 +56,8 @@ Layout layout_for(int n, int na, int nb, int P, int n_items)
     L.ang = o;    o += align256((size_t)na * sizeof(FwdAngle));
     L.groups = o; o += align256((size_t)na * gpa * sizeof(int2));
     L.items = o;  o += align256((size_t)n_items * sizeof(RayItem));
-    L.lrow = o;   o += align256((size_t)n * P * sizeof(float2));
-    L.lcol = o;   o += align256((size_t)n * P * sizeof(float2));
+    L.lrow = o;   o += align256((size_t)layout_lines(n) * P * sizeof(float2));
+    L.lcol = o;   o += align256((size_t)layout_lines(n) * P * sizeof(float2));
     L.total = o;
     return L;
 }
@@ -209,9 +209,9 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
 
     // sizes: same line pitch and chunking as the context path; items of at
     // most gpi groups, gpi sized for one block per SM
-    const int P = ((n + 2 * kGuard) + 3) / 4 * 4;
+    const int P = layout_pitch(n);
     int lc = 8;
-    while (lc > 2 && (size_t)lc * P * sizeof(float2) > 34816) lc >>= 1;
+    while (lc > 2 && (size_t)lc * P * sizeof(float2) > kMaxStageBytes) lc >>= 1;
     const int gpa = (nb + 31) / 32;
     const int kx0 = (na + 3) / 4, kx1 = (3 * na) / 4;
     const int ny = kx0 + (na - 1 - kx1);
@@ -228,7 +228,7 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     if (L.total > kStaticScratchBytes) {
         set_msg(err, err_cap,
                 "n=%d, n_angles=%d, n_bins=%d need %zu bytes of scratch; the fixed scratch holds %zu "
-                "(about n <= 1150 at 720 angles)",
+                "(about n <= 1220 at 720 angles)",
                 n, na, nb, L.total, kStaticScratchBytes);
         return MC_EINVAL;
     }
@@ -259,10 +259,10 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     WarpArgs w{};
     w.x = x; w.n = n; w.rigid = d_rg; w.field = nullptr; w.identity = rigid ? 0 : 1;
     w.sel = GateSel{nullptr, 0}; w.n_slots = 1;
-    w.lrow = d_lrow; w.lcol = d_lcol; w.layout_stride = (size_t)n * P; w.P = P;
+    w.lrow = d_lrow; w.lcol = d_lcol; w.layout_stride = (size_t)layout_lines(n) * P; w.P = P;
     if (e == cudaSuccess) e = launch_warp_layouts(w, s);
     FwdArgs f{};
-    f.lrow = d_lrow; f.lcol = d_lcol; f.layout_stride = (size_t)n * P; f.P = P;
+    f.lrow = d_lrow; f.lcol = d_lcol; f.layout_stride = (size_t)layout_lines(n) * P; f.P = P;
     f.ang = d_ang; f.groups = d_groups; f.items = d_items; f.n_items = n_items;
     f.ipb = ipb; f.rpt = rpt; f.lc = lc; f.n = n; f.na = na; f.nb = nb;
     f.sel = GateSel{nullptr, 0}; f.n_slots = 1; f.mode = 0; f.out = out; f.err = d_err;
