@@ -4,7 +4,9 @@
 //
 // Rays are processed in warp-wide groups of up to 32 consecutive bins of one
 // angle.  Work items are ranges of groups that share a driving axis, cut on
-// the host so that every item has the same number of samples; one block per
+// the host so that every item has the same number of samples, and dealt to
+// the consumer warps on the host (entry p of an item goes to warp p % W, slot
+// p / W; an entry {-1, 0} is an empty slot); one block per
 // SM takes `ipb` consecutive items and streams the whole warped image through
 // shared memory for each, in chunks of LC lines.  One producer warp issues a
 // bulk TMA copy (cp.async.bulk) per chunk into a ring of kStages buffers; the
@@ -300,6 +302,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
             acc[m] = 0.0f; frac[m] = 0.0f; ui[m] = 0;
             if (m >= ns) continue;
             const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+            if (grp.x < 0) continue;                            // empty slot of the item's deal
             const int k = grp.x;
             const int b = min(grp.y + lane, nb - 1);           // idle lanes repeat the last ray
             const FwdAngle T = a.ang[k];
@@ -377,7 +380,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 if (m >= ns) break;
                 const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
                 const int b = grp.y + lane;
-                if (b < nb) a.part[((size_t)item.band * a.na + grp.x) * nb + b] = acc[m];
+                if (grp.x >= 0 && b < nb) a.part[((size_t)item.band * a.na + grp.x) * nb + b] = acc[m];
             }
         } else {
 #pragma unroll
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 if (m >= ns) break;
                 const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
                 const int k = grp.x, b = grp.y + lane;
-                if (b >= nb) continue;
+                if (k < 0 || b >= nb) continue;
                 const float delta = __ldg(&a.ang[k].delta);
                 const float val = delta * acc[m];
                 const size_t idx = (size_t)k * nb + b;

@@ -617,20 +617,6 @@ mc_status check_gate(mc_ctx* c, int gate)
 }
 
 // ---- creation ---------------------------------------------------------------
-// Number of lines on which ray (k, b) has a non-zero interpolation weight:
-// positions u(l) = (b - hb) inv - (l - h) t + h in (-1, n), l = 0..n-1.
-long long ray_samples(int n, double hb, double inv, double t, int b)
-{
-    const double h = 0.5 * (n - 1);
-    const double a = (b - hb) * inv + h * t + h;        // u(0); u(l) = a - l t
-    if (std::fabs(t) < 1e-12) return (a > -1.0 && a < n) ? n : 0;
-    double l1 = (a - n) / t, l2 = (a + 1.0) / t;       // u = n and u = -1
-    if (l1 > l2) std::swap(l1, l2);
-    const long long lo = std::max<long long>(0, (long long)std::floor(l1) + 1);
-    const long long hi = std::min<long long>(n - 1, (long long)std::ceil(l2) - 1);
-    return hi >= lo ? hi - lo + 1 : 0;
-}
-
 // Forward angle table for chunks of lc lines: slope split into float pairs and
 // the exact integer/fraction split of the per-chunk advance lc * t.
 std::vector<FwdAngle> fwd_angles(const mc_ctx* c, int lc)
@@ -657,20 +643,22 @@ std::vector<FwdAngle> fwd_angles(const mc_ctx* c, int lc)
 // Ray groups of the forward projector (up to 32 consecutive bins of one
 // angle) for S interleaved angle subsets: subset s holds the angles k = s
 // (mod S), rows-driven angles first; its groups are sets[s] = {first,
-// first columns-driven, end}.  cum holds running sample weights (a fixed
-// setup cost per group plus its in-image samples).
+// first columns-driven, end}.  cum holds running work weights (a fixed
+// setup cost per group plus its chunks, weighted by their load wavefronts).
 struct GroupTable {
     std::vector<int2> groups;
     std::vector<long long> cum;
     std::vector<std::array<long long, 3>> sets;
 };
 
+void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float>& cost);
+
 void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vector<double>& inv_k,
-                  const std::vector<double>& t_k, int S, GroupTable& gt)
+                  const std::vector<double>& t_k, int S, int lc, GroupTable& gt)
 {
-    const int n = c->n, na = c->na, nb = c->nb;
-    const double hb = 0.5 * (nb - 1);
+    const int na = c->na, nb = c->nb;
     const int gpa = (nb + 31) / 32;                        // groups per angle
+    std::vector<float> cost;
     gt.groups.clear();
     gt.cum.assign(1, 0);
     gt.sets.clear();
@@ -682,10 +670,18 @@ void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vec
             if (k % S != sub) continue;
             const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
             if (xd && set[1] < 0) set[1] = (long long)gt.groups.size();
+            // a half-warp's 64-bit load (16 consecutive bins, |inv| pairs apart)
+            // takes about wf = 1 + min(1, 15 (|inv| - 1)) shared-memory
+            // wavefronts: one near the driving axis, two from ~20 degrees on.
+            // Measured block times on rigid512 fit chunks x (2.8 + wf) (R^2 0.91)
+            const double wf = 1.0 + std::min(1.0, 15.0 * (std::fabs(inv_k[k]) - 1.0));
             for (int g = 0; g < gpa; ++g) {
+                // the work k_forward does for the group: all 32 lanes over every
+                // chunk of the union of its rays' line ranges, each chunk
+                // weighted by the shared-memory wavefronts of the angle's loads
+                group_chunk_costs(c, k, g * 32, lc, cost);
                 long long w = 64;
-                for (int b = g * 32; b < std::min(nb, g * 32 + 32); ++b)
-                    w += ray_samples(n, hb, inv_k[k], t_k[k], b);
+                for (float q : cost) w += q > 0.0f ? (long long)(32.0 * lc * (2.8 + wf)) : 0LL;
                 gt.groups.push_back(make_int2(k, g * 32));
                 gt.cum.push_back(gt.cum.back() + w);
             }
@@ -738,7 +734,8 @@ void partition_items(const GroupTable& gt, int sms, int ipb_start, std::vector<R
 // Chunks of lc lines that group {k, b0} visits in k_forward: its rays cover
 // lines [lo, hi] (the kernel's estimate, widened by one line on each side) and
 // the group visits the union of their chunks, each at the same cost (one
-// chunk of samples of all 32 lanes plus the per-chunk set-up of the group).
+// chunk of samples of all 32 lanes plus the per-chunk set-up of the group;
+// measured per-block times follow these counts, whatever the angle).
 void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float>& cost)
 {
     const int n = c->n, nb = c->nb, nch = layout_lines(n) / lc;
@@ -764,28 +761,35 @@ void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float
     for (int ch = lo_min / lc; ch <= hi_max / lc; ++ch) cost[ch] = 1.0f;
 }
 
-// Order the groups of every item so that k_forward's fixed mapping (the p-th
-// group of an item goes to consumer warp p % W, slot p / W) hands each warp
-// about the same work in every stretch of chunks.  The ring lets warps drift
-// apart by only kStages - 1 chunks, so a warp with more active groups than
-// its neighbours over such a stretch holds the whole block back; a
-// round-robin deal of groups in angle/bin order left the busiest warp with
-// ~1.5x the mean work.  Greedy: groups by decreasing total cost, each to the
-// warp (with a free slot) whose cost summed over a window of 2 kStages - 1
-// chunks would peak lowest.  The order of groups within an item changes no
-// result: each group's rays are summed by one warp in line order either way.
-void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, const std::vector<RayItem>& items)
+// Deal the groups of every item to k_forward's consumer warps so that each
+// warp gets about the same work in every stretch of chunks.  The kernel maps
+// the p-th entry of an item to warp p % W, slot p / W; the ring lets warps
+// drift apart by only kStages - 1 chunks, so a warp with more active groups
+// than its neighbours over such a stretch holds the whole block back (a
+// round-robin deal in angle/bin order left the busiest warp with ~1.5x the
+// mean work), and a block takes about the sum over chunks of its busiest
+// warp's load.  Greedy: loads smoothed over a window of 2 kStages - 1 chunks;
+// groups by decreasing total cost, each to the warp where it raises that sum
+// least (ties: the warp with the least total), any warp taking up to two
+// groups more than an even share (at most 8); the
+// item is then rewritten as W x L entries, L the most groups any warp got,
+// with empty entries {-1, 0} that the kernel skips.  The groups array and the
+// items' ranges are rebuilt; rpt becomes the smallest slot count >= L.  The
+// order of groups changes no result: each group's rays are summed by one warp
+// in line order either way.
+void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vector<RayItem>& items, int& rpt)
 {
     const int W = forward_consumer_warps(), half = forward_ring_stages() - 1;
     const int nch = layout_lines(c->n) / lc;
     std::vector<std::vector<float>> win;        // windowed cost per group of the item
-    std::vector<float> cost, load, total;
-    std::vector<int> idx, slot_of;
+    std::vector<float> cost, load, total, top, wsum;
+    std::vector<int> idx;
     std::vector<std::vector<int>> lists(W);
     std::vector<int2> out;
-    for (const RayItem& it : items) {
+    out.reserve(groups.size() + items.size() * W);
+    int most = 1;
+    for (RayItem& it : items) {
         const int m = it.end - it.begin;
-        if (m <= 1) continue;
         win.assign(m, std::vector<float>(nch, 0.0f));
         total.assign(m, 0.0f);
         for (int g = 0; g < m; ++g) {
@@ -800,26 +804,45 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, const std
         idx.resize(m);
         for (int g = 0; g < m; ++g) idx[g] = g;
         std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return total[a] > total[b]; });
+        const int cap = std::min(8, (m + W - 1) / W + 2);
         load.assign((size_t)W * nch, 0.0f);
+        top.assign(nch, 0.0f);
+        wsum.assign(W, 0.0f);
         for (auto& L : lists) L.clear();
         for (int g : idx) {
             int best_w = -1;
             float best = 0.0f;
             for (int w = 0; w < W; ++w) {
-                const int cap = w < m ? (m - w + W - 1) / W : 0;
                 if ((int)lists[w].size() >= cap) continue;
-                float peak = 0.0f;
-                for (int ch = 0; ch < nch; ++ch) peak = std::max(peak, load[(size_t)w * nch + ch] + win[g][ch]);
-                if (best_w < 0 || peak < best) { best = peak; best_w = w; }
+                float rise = 0.0f;
+                for (int ch = 0; ch < nch; ++ch)
+                    rise += std::max(0.0f, load[(size_t)w * nch + ch] + win[g][ch] - top[ch]);
+                if (best_w < 0 || rise < best || (rise == best && wsum[w] < wsum[best_w])) {
+                    best = rise;
+                    best_w = w;
+                }
             }
             lists[best_w].push_back(g);
-            for (int ch = 0; ch < nch; ++ch) load[(size_t)best_w * nch + ch] += win[g][ch];
+            wsum[best_w] += total[g];
+            for (int ch = 0; ch < nch; ++ch) {
+                float& l = load[(size_t)best_w * nch + ch];
+                l += win[g][ch];
+                top[ch] = std::max(top[ch], l);
+            }
         }
-        out.assign(m, make_int2(0, 0));
-        for (int w = 0; w < W; ++w)
-            for (size_t s = 0; s < lists[w].size(); ++s) out[w + s * W] = groups[it.begin + lists[w][s]];
-        std::copy(out.begin(), out.end(), groups.begin() + it.begin);
+        int L = 0;
+        for (const auto& l : lists) L = std::max(L, (int)l.size());
+        most = std::max(most, L);
+        const int begin = (int)out.size();
+        for (int sl = 0; sl < L; ++sl)
+            for (int w = 0; w < W; ++w)
+                out.push_back(sl < (int)lists[w].size() ? groups[it.begin + lists[w][sl]] : make_int2(-1, 0));
+        it.begin = begin;
+        it.end = (int)out.size();
     }
+    groups.swap(out);
+    rpt = 2;
+    while (rpt < most) rpt <<= 1;
 }
 
 mc_status build_tables(mc_ctx* c)
@@ -834,13 +857,24 @@ mc_status build_tables(mc_ctx* c)
     while (c->lc > 2 && (size_t)c->lc * c->P * sizeof(float2) > kMaxStageBytes) c->lc >>= 1;
     std::vector<FwdAngle> fa(na);
     std::vector<BpAngle> ba(na);
+    // forward group order: rows-driven angles first, then columns-driven; in
+    // each class the angles are taken round-robin from 8 contiguous bands, so
+    // that every work item (a contiguous range of this order) mixes angles of
+    // all obliquities -- long and short ray groups -- which lets the warp deal
+    // of balance_items even out
     std::vector<int> order;
     order.reserve(na);
-    for (int pass = 0; pass < 2; ++pass)
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<int> cls;
         for (int k = 0; k < na; ++k) {
             const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
-            if ((pass == 1) == xd) order.push_back(k);
+            if ((pass == 1) == xd) cls.push_back(k);
         }
+        const int C = (int)cls.size(), B = (C + 7) / 8;
+        for (int i = 0; i < B; ++i)
+            for (int band = 0; band < 8; ++band)
+                if (band * B + i < C) order.push_back(cls[band * B + i]);
+    }
     std::vector<double> inv_k(na), t_k(na);
     for (int k = 0; k < na; ++k) {
         const double phi = (double)k * kPi / (double)na;
@@ -866,12 +900,12 @@ mc_status build_tables(mc_ctx* c)
     c->t_k = t_k;
     fa = fwd_angles(c, c->lc);
     GroupTable gt;
-    build_groups(c, order, inv_k, t_k, 1, gt);
+    build_groups(c, order, inv_k, t_k, 1, c->lc, gt);
     std::vector<RayItem> items;
     std::vector<int> set_off;
     int rpt = 2, ipb = 1;
     partition_items(gt, c->sms, 1, items, set_off, ipb, rpt);
-    balance_items(c, c->lc, gt.groups, items);
+    balance_items(c, c->lc, gt.groups, items, rpt);
     const std::vector<int2>& groups = gt.groups;
     c->ipb = ipb;
     c->rpt = rpt;
@@ -1262,15 +1296,17 @@ mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min)
 {
     std::vector<FwdAngle> fa = fwd_angles(c, lc);
     GroupTable gt;
-    build_groups(c, c->order, c->inv_k, c->t_k, 1, gt);
+    build_groups(c, c->order, c->inv_k, c->t_k, 1, lc, gt);
     std::vector<RayItem> items;
     std::vector<int> off;
     int ipb = 1, rpt = 2;
     partition_items(gt, c->sms, ipb_start, items, off, ipb, rpt);
+    balance_items(c, lc, gt.groups, items, rpt);    // the deal depends on the cut and lc
     while (rpt < rpt_min && rpt < 8) rpt <<= 1;
-    balance_items(c, lc, gt.groups, items);     // the group order depends on the cut and lc
     dfree(c, &c->d_items);
+    dfree(c, &c->d_groups);
     TRY(dalloc(c, &c->d_items, items.size()));
+    TRY(dalloc(c, &c->d_groups, gt.groups.size()));
     CK(cudaMemcpyAsync(c->d_fang, fa.data(), fa.size() * sizeof(FwdAngle), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_groups, gt.groups.data(), gt.groups.size() * sizeof(int2), cudaMemcpyHostToDevice,
                        c->stream));
@@ -1375,12 +1411,12 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
         // into ~SMs / B ranges, each repeated for every band
         const int bands = std::min(8, std::max(1, subsets / 2));
         GroupTable gt;
-        build_groups(c, c->order, c->inv_k, c->t_k, subsets, gt);
+        build_groups(c, c->order, c->inv_k, c->t_k, subsets, c->lc, gt);
         std::vector<RayItem> cut;
         std::vector<int> cut_off;
         int ipb = 1, rpt = 2;
         partition_items(gt, std::max(1, c->sms / bands), 1, cut, cut_off, ipb, rpt);
-        balance_items(c, c->lc, gt.groups, cut);   // one order serves every band of a cut
+        balance_items(c, c->lc, gt.groups, cut, rpt);   // one deal serves every band of a cut
         std::vector<RayItem> items;
         std::vector<int> off(1, 0);
         for (int q = 0; q < subsets; ++q) {
