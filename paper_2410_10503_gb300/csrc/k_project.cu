@@ -87,6 +87,26 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
+// L2 prefetch of this block's share of a gate's CSR of D_i^T (row pointers
+// and entries), as 16-byte-aligned bulk prefetches inside each array's range.
+__device__ __forceinline__ void prefetch_span(const void* base, size_t bytes, int part, int parts)
+{
+    const uintptr_t b0 = (uintptr_t)base, b1 = b0 + bytes;
+    uintptr_t s = b0 + bytes * part / parts, e = b0 + bytes * (part + 1) / parts;
+    s = (s + 15) & ~(uintptr_t)15;
+    e = min(e, b1) & ~(uintptr_t)15;
+    if (e > s)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
+}
+
+__device__ __forceinline__ void prefetch_csr(const FwdArgs& a, int gate)
+{
+    const size_t n2 = (size_t)a.n * a.n;
+    const int* rp = a.pf_rowptr + (size_t)gate * (n2 + 1);
+    prefetch_span(rp, (n2 + 1) * sizeof(int), blockIdx.x, gridDim.x);
+    prefetch_span(a.pf_ent + a.pf_ent_off[gate], (size_t)__ldg(rp + n2) * sizeof(int2), blockIdx.x, gridDim.x);
+}
+
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up
 constexpr int kConsumers = 24;               // consumer warps per block
 constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
@@ -266,6 +286,9 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                 }
             }
         }
+        // off the ring's critical path: prefetch the CSR the iteration's
+        // transpose warp will read (a.pf_rowptr is set for one-slot SPDHG launches)
+        if (lane == 1 && a.pf_rowptr && a.n_slots == 1) prefetch_csr(a, sel_gate(a.sel, slot));
         return;
     }
 

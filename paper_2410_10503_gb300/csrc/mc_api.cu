@@ -435,6 +435,7 @@ mc_status enqueue_spdhg_epoch(mc_ctx* c, uint64_t seed, uint32_t stream)
         TRY(warp_into_layouts(c, xin, sel, 1, false));
         FwdArgs fa = fwd_args(c, sel, 1);
         fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y; fa.sigma = sigma; fa.inv_den = inv_den;
+        fa.pf_rowptr = c->d_rowptr; fa.pf_ent = c->d_ent; fa.pf_ent_off = c->d_ent_off;   // gate's CSR into L2
         fa.store = c->store; fa.dh = c->d_dh; fa.yh = c->d_yh;
         TRY(launch(c, C_PROJ, "project", [&] { return launch_forward(fa, c->stream); }));
         TRY(backproject(c, sel, 1, c->d_b));

@@ -122,6 +122,12 @@ struct FwdArgs {
     const unsigned short* dh;  // mode 1, store != 0: data and dual, gate stride na*nb
     unsigned short* yh;
     int* err;
+    // optional (one slot): the CSR of D_i^T of the slot's gate (layout as in
+    // WarpAdjArgs) is prefetched into L2 by an idle lane of each block's
+    // producer warp, for the transpose warp at the end of the same iteration
+    const int* pf_rowptr;
+    const int2* pf_ent;
+    const long long* pf_ent_off;
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 int forward_groups_per_block(int rpt);
