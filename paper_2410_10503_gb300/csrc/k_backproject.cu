@@ -159,6 +159,8 @@ __device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long
 template <int PJ, bool SUB>
 __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);                             // [kGroups][kRing]
     AngSlot* s_slot = reinterpret_cast<AngSlot*>(smem + 128);                       // [kGroups][kRing][kBatch]
@@ -321,8 +323,7 @@ cudaError_t launch_backproject(const BpArgs& a_in, cudaStream_t s)
     const bool sub = a.sel.subsets > 1;      // one angle subset per launch
 #define MC_BP_LAUNCH(P, B)                                     \
     if (a.pj == P && sub == B) {                               \
-        k_backproject<P, B><<<grid, 256, smem, s>>>(a);        \
-        return cudaGetLastError();                             \
+        return pdl_launch(k_backproject<P, B>, grid, dim3(256), smem, s, a);   \
     }
     MC_BP_INSTANCES(MC_BP_LAUNCH)
 #undef MC_BP_LAUNCH

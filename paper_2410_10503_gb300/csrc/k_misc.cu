@@ -15,6 +15,8 @@ namespace {
 __global__ void k_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
                              uint64_t k0_in, int count, int n_gates, int* out)
 {
+    pdl_wait();
+    pdl_trigger();
     const uint64_t k0 = kctr ? (uint64_t)*kctr : k0_in;
     for (int j = threadIdx.x; j < count; j += blockDim.x) {
         const uint32_t w = philox_word0(seed, stream, k0 + (uint64_t)j);
@@ -144,8 +146,7 @@ __global__ void k_fill_nan(double* p, int count)
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
                               uint64_t k0, int count, int n_gates, int* out, cudaStream_t s)
 {
-    k_draw_gates<<<1, 256, 0, s>>>(seed, stream, kctr, k0, count, n_gates, out);
-    return cudaGetLastError();
+    return pdl_launch(k_draw_gates, dim3(1), dim3(256), 0, s, seed, stream, kctr, k0, count, n_gates, out);
 }
 
 cudaError_t launch_pad_sino(const float* y, float2* dy, const BpAngle* ang, int na, int nb,

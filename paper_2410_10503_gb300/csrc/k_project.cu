@@ -215,6 +215,8 @@ struct SlotState {
 template <int RPT, int LC, bool BANDED>
 __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kStages;
@@ -450,6 +452,8 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 // ray of the launch's angle subset.
 __global__ void __launch_bounds__(256) k_forward_combine(FwdArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     const int slot = blockIdx.y;
     const int nb = a.nb;
     const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;
@@ -526,14 +530,14 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
 #define MC_LAUNCH(R, L)                                                                   \
     if (a.rpt == R && a.lc == L) {                                                        \
         if (a.nbands > 1) {                                                               \
-            k_forward<R, L, true><<<grid, kBlock, smem, s>>>(a);                          \
+            cudaError_t e = pdl_launch(k_forward<R, L, true>, grid, dim3(kBlock), smem, s, a);  \
+            if (e != cudaSuccess) return e;                                               \
             const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;                          \
             const int rays = ((a.na + S - 1) / S) * a.nb;                                 \
-            k_forward_combine<<<dim3((rays + 255) / 256, a.n_slots), 256, 0, s>>>(a);     \
+            return pdl_launch(k_forward_combine, dim3((rays + 255) / 256, a.n_slots), dim3(256), 0, s, a); \
         } else {                                                                          \
-            k_forward<R, L, false><<<grid, kBlock, smem, s>>>(a);                         \
+            return pdl_launch(k_forward<R, L, false>, grid, dim3(kBlock), smem, s, a);    \
         }                                                                                 \
-        return cudaGetLastError();                                                        \
     }
     MC_FWD_INSTANCES(MC_LAUNCH)
 #undef MC_LAUNCH

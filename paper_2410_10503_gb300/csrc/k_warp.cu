@@ -37,6 +37,8 @@ __device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
 // samples taken by the first threads afterwards.
 __global__ void __launch_bounds__(1024) k_warp_layouts(WarpArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float w_s[33][34];
     const int slot = blockIdx.z;
     const int gate = sel_gate(a.sel, slot);
@@ -101,8 +103,7 @@ __global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
 {
     dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 32);
-    k_warp_layouts<<<grid, block, 0, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_warp_layouts, grid, block, 0, s, a);
 }
 
 cudaError_t launch_warp_plain(const WarpArgs& a, cudaStream_t s)
@@ -306,6 +307,8 @@ cudaError_t launch_field_vjp(int n, const float* field, const float* x, const fl
 template <bool UPDATE>
 __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
 {
+    pdl_wait();
+    pdl_trigger();
     const int n2 = a.n * a.n;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n2) return;
@@ -349,15 +352,13 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
 cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s)
 {
     const int n2 = a.n * a.n;
-    k_warp_adjoint<false><<<(n2 + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_warp_adjoint<false>, dim3((n2 + 255) / 256), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s)
 {
     const int n2 = a.n * a.n;
-    k_warp_adjoint<true><<<(n2 + 255) / 256, 256, 0, s>>>(a);
-    return cudaGetLastError();
+    return pdl_launch(k_warp_adjoint<true>, dim3((n2 + 255) / 256), dim3(256), 0, s, a);
 }
 
 }  // namespace mcg

@@ -17,6 +17,7 @@
 //                 one 8-byte load and no bounds checks.
 #pragma once
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -73,6 +74,34 @@ struct RigidGate {
 struct RayItem {
     int begin, end, dir, band;     // band: chunk band of a banded (angle-subset) item, else 0
 };
+
+// ---- programmatic dependent launch ----------------------------------------
+// The kernels of an iteration are launched with programmatic stream
+// serialisation (pdl_launch below): the next kernel's blocks may be scheduled
+// while the previous kernel finishes.  Each such kernel first waits until its
+// predecessor has completed and its writes are visible (pdl_wait), and only
+// then lets its own successor be scheduled (pdl_trigger), so at most one
+// kernel is waiting behind a running one.  For a kernel launched the ordinary
+// way both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args&&... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ---- exact little helpers ------------------------------------------------
 // floor(v) as float, and its integer in i (valid for |v| < 2^22): adding
