@@ -206,6 +206,14 @@ struct SlotState {
     int step_int;
 };
 
+// A slot's group {angle, first bin} and the angle's Joseph table, fetched by
+// one lane per slot at the start of an item so that the slots' dependent
+// global loads are in flight together.
+struct SlotRec {
+    FwdAngle T;
+    int2 grp;
+};
+
 // BANDED (angle-subset launches): an item also names a band of chunks
 // [band * cpb, (band + 1) * cpb); its rays' partial sums over that band go to
 // a.part[band] and k_forward_combine adds the bands in order and runs the
@@ -222,6 +230,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     uint64_t* empty = full + kStages;
     int* s_flag = reinterpret_cast<int*>(smem + 96);
     __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
+    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
     float2* stage0 = reinterpret_cast<float2*>(smem + 128);
     const size_t stage_pairs = (size_t)LC * a.P;   // one chunk: LC whole lines
 
@@ -322,15 +331,22 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         float frac[RPT], acc[RPT];
         int ui[RPT];
         int my_lo = nch, my_hi = -1;      // lane m < RPT: chunk range of slot m
+        SlotRec* rec = s_rec + warp * RPT;
+        if (lane < ns) {
+            SlotRec r;
+            r.grp = __ldg(a.groups + item.begin + warp + lane * kConsumers);
+            if (r.grp.x >= 0) r.T = a.ang[r.grp.x];
+            rec[lane] = r;
+        }
+        __syncwarp();
 #pragma unroll
         for (int m = 0; m < RPT; ++m) {
             acc[m] = 0.0f; frac[m] = 0.0f; ui[m] = 0;
             if (m >= ns) continue;
-            const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+            const int2 grp = rec[m].grp;
             if (grp.x < 0) continue;                            // empty slot of the item's deal
-            const int k = grp.x;
             const int b = min(grp.y + lane, nb - 1);           // idle lanes repeat the last ray
-            const FwdAngle T = a.ang[k];
+            const FwdAngle T = rec[m].T;
             const float B = (float)b - hb;                      // exact
             const float t = T.t_hi;
             // lines with a non-zero weight have u in (kGuard - 1, kGuard + n);
@@ -399,44 +415,61 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         }
 
         // ---- epilogue ---------------------------------------------------------
+        // slots' groups and angle steps come from the staged records; every
+        // slot's y and d are loaded before any store, so their latencies overlap
         if constexpr (BANDED) {
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
                 if (m >= ns) break;
-                const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+                const int2 grp = rec[m].grp;
                 const int b = grp.y + lane;
                 if (grp.x >= 0 && b < nb) a.part[((size_t)item.band * a.na + grp.x) * nb + b] = acc[m];
             }
         } else {
+            float yo[RPT], dv[RPT];
+#pragma unroll
+            for (int m = 0; m < RPT; ++m) {
+                yo[m] = 0.0f; dv[m] = 0.0f;
+                if (m >= ns || a.mode == 0) continue;
+                const int2 grp = rec[m].grp;
+                const int b = grp.y + lane;
+                if (grp.x < 0 || b >= nb) continue;
+                const size_t gi = ((size_t)gate * a.na + grp.x) * nb + b;
+                if (a.store == 0) {
+                    yo[m] = a.y[gi];
+                    dv[m] = a.d[gi];
+                } else {
+                    yo[m] = load_store(a.yh[gi], a.store);
+                    dv[m] = load_store(a.dh[gi], a.store);
+                }
+            }
 #pragma unroll
             for (int m = 0; m < RPT; ++m) {
                 if (m >= ns) break;
-                const int2 grp = __ldg(a.groups + item.begin + warp + m * kConsumers);
+                const int2 grp = rec[m].grp;
                 const int k = grp.x, b = grp.y + lane;
                 if (k < 0 || b >= nb) continue;
-                const float delta = __ldg(&a.ang[k].delta);
+                const float delta = rec[m].T.delta;
                 const float val = delta * acc[m];
                 const size_t idx = (size_t)k * nb + b;
                 if (a.mode == 0) {
                     a.out[(size_t)slot * a.na * nb + idx] = val;
                 } else {
                     const size_t gi = (size_t)gate * a.na * nb + idx;
-                    float yo, yn;
+                    float yn;
                     if (a.store == 0) {
-                        yo = a.y[gi];
-                        yn = (yo + a.sigma * (val - a.d[gi])) * a.inv_den;
+                        yn = (yo[m] + a.sigma * (val - dv[m])) * a.inv_den;
                         a.y[gi] = yn;
                     } else {
                         // reduced-precision d and y: arithmetic in float32, the new
                         // y rounded on store and the increment taken from stored values
-                        yo = load_store(a.yh[gi], a.store);
-                        const float yf = (yo + a.sigma * (val - load_store(a.dh[gi], a.store))) * a.inv_den;
+                        const float yf = (yo[m] + a.sigma * (val - dv[m])) * a.inv_den;
                         const unsigned short q = to_store(yf, a.store);
                         a.yh[gi] = q;
                         yn = load_store(q, a.store);
                     }
                     // dy pairs scaled by the angle's step: (m dy[b], m dy[b+1])
-                    const float v = delta * (yn - yo);
+                    const float v = delta * (yn - yo[m]);
                     float* dyp = reinterpret_cast<float*>(a.dy + slot * a.dy_stride + (size_t)k * a.Pb + a.Gb + b);
                     dyp[0] = v;
                     dyp[-1] = v;
@@ -500,7 +533,7 @@ int forward_consumer_warps() { return kConsumers; }
 
 int forward_ring_stages() { return kStages; }
 
-int forward_static_smem() { return (int)(kConsumers * 8 * sizeof(SlotState)); }
+int forward_static_smem() { return (int)(kConsumers * 8 * (sizeof(SlotState) + sizeof(SlotRec))); }
 
 size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }
 
