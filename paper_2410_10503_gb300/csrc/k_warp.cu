@@ -28,56 +28,63 @@ __device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
     return acc;
 }
 
-// Layout mode: a 32 x 32 tile of w = D x plus a one-pixel halo (33 x 33) is
-// computed into shared memory, then written as (w, next - w) pairs into the
-// row-line and the column-line layouts (the halo supplies "next"; pixels past
-// the image edge are zero).  The pair just before each line's data,
-// (0, w[0]), is written by the tile that holds position 0.  One thread per
-// tile pixel (1024 per block, so a 512^2 image fits in one wave), the 65 halo
-// samples taken by the first threads afterwards.
+// Layout mode: a tile of 32 columns x 30 rows of w = D x plus a one-pixel
+// halo (33 x 31) is computed into shared memory, then written as
+// (w, next - w) pairs into the row-line and the column-line layouts (the halo
+// supplies "next"; pixels past the image edge are zero).  The 960 tile and
+// 63 halo samples take one thread each of a 1024-thread block, so every
+// sample's loads are issued in the same round.  The pair just before each
+// line's data, (0, w[0]), is written by the tile that holds position 0.
+constexpr int kWarpTileRows = 30;
+
 __global__ void __launch_bounds__(1024) k_warp_layouts(WarpArgs a)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ float w_s[33][34];
+    __shared__ float w_s[kWarpTileRows + 1][34];
     const int slot = blockIdx.z;
     const int gate = sel_gate(a.sel, slot);
     const int n = a.n;
     const RigidGate* rg = a.rigid ? a.rigid + gate : nullptr;
     const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
-    const int r_t = blockIdx.y * 32, c_t = blockIdx.x * 32;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    auto sample = [&](int rr, int cc) {
-        const int r = r_t + rr, c = c_t + cc;
-        float w = 0.0f;
-        if (r < n && c < n)
-            w = a.identity ? __ldg(a.x + (size_t)r * n + c) : warp_sample(a.x, n, rg, field, r, c);
-        w_s[rr][cc] = w;
-    };
-    sample(threadIdx.y, threadIdx.x);
-    if (tid < 65) {                        // halo: column 32 (rows 0..32), row 32 (columns 0..31)
-        if (tid < 33) sample(tid, 32);
-        else sample(32, tid - 33);
+    const int r_t = blockIdx.y * kWarpTileRows, c_t = blockIdx.x * 32;
+    const int tid = threadIdx.x;
+    {
+        // thread -> sample: tile (rows 0..29, columns 0..31), then the halo
+        // column 32 (rows 0..30), then the halo row 30 (columns 0..31)
+        int rr = -1, cc = 0;
+        if (tid < 32 * kWarpTileRows) { rr = tid >> 5; cc = tid & 31; }
+        else if (tid < 32 * kWarpTileRows + kWarpTileRows + 1) { rr = tid - 32 * kWarpTileRows; cc = 32; }
+        else if (tid < 32 * kWarpTileRows + kWarpTileRows + 33) { rr = kWarpTileRows; cc = tid - (32 * kWarpTileRows + kWarpTileRows + 1); }
+        if (rr >= 0) {
+            const int r = r_t + rr, c = c_t + cc;
+            float w = 0.0f;
+            if (r < n && c < n)
+                w = a.identity ? __ldg(a.x + (size_t)r * n + c) : warp_sample(a.x, n, rg, field, r, c);
+            w_s[rr][cc] = w;
+        }
     }
     __syncthreads();
     float2* lrow = a.lrow + slot * a.layout_stride;
     float2* lcol = a.lcol + slot * a.layout_stride;
-    {   // row lines: lanes along the columns of one row
-        const int rr = threadIdx.y, cc = threadIdx.x;
-        const int r = r_t + rr, c = c_t + cc;
-        if (r < n && c < n) {
-            const float v = w_s[rr][cc];
-            lrow[(size_t)r * a.P + kGuard + c] = make_float2(v, w_s[rr][cc + 1] - v);
-            if (c == 0) lrow[(size_t)r * a.P + kGuard - 1] = make_float2(0.0f, v);
+    if (tid < 32 * kWarpTileRows) {
+        {   // row lines: lanes along the columns of one row
+            const int rr = tid >> 5, cc = tid & 31;
+            const int r = r_t + rr, c = c_t + cc;
+            if (r < n && c < n) {
+                const float v = w_s[rr][cc];
+                lrow[(size_t)r * a.P + kGuard + c] = make_float2(v, w_s[rr][cc + 1] - v);
+                if (c == 0) lrow[(size_t)r * a.P + kGuard - 1] = make_float2(0.0f, v);
+            }
         }
-    }
-    {   // column lines: lanes along the rows of one column
-        const int cc = threadIdx.y, rr = threadIdx.x;
-        const int r = r_t + rr, c = c_t + cc;
-        if (r < n && c < n) {
-            const float v = w_s[rr][cc];
-            lcol[(size_t)c * a.P + kGuard + r] = make_float2(v, w_s[rr + 1][cc] - v);
-            if (r == 0) lcol[(size_t)c * a.P + kGuard - 1] = make_float2(0.0f, v);
+        {   // column lines: consecutive threads along the rows of one column
+            const int cc = tid / kWarpTileRows, rr = tid - cc * kWarpTileRows;
+            const int r = r_t + rr, c = c_t + cc;
+            if (r < n && c < n) {
+                const float v = w_s[rr][cc];
+                lcol[(size_t)c * a.P + kGuard + r] = make_float2(v, w_s[rr + 1][cc] - v);
+                if (r == 0) lcol[(size_t)c * a.P + kGuard - 1] = make_float2(0.0f, v);
+            }
         }
     }
 }
@@ -102,7 +109,7 @@ __global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
 
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
 {
-    dim3 grid((a.n + 31) / 32, (a.n + 31) / 32, a.n_slots), block(32, 32);
+    dim3 grid((a.n + 31) / 32, (a.n + kWarpTileRows - 1) / kWarpTileRows, a.n_slots), block(1024);
     return pdl_launch(k_warp_layouts, grid, block, 0, s, a);
 }
 
@@ -312,6 +319,9 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
     const int n2 = a.n * a.n;
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n2) return;
+    // the update's own operands first: their loads overlap the CSR chain
+    float z0 = 0.0f, x0 = 0.0f;
+    if (UPDATE) { z0 = a.z[q]; x0 = a.x_in[q]; }
     float v = 0.0f;
     for (int s = 0; s < a.n_slots; ++s) {
         const int gate = sel_gate(a.sel, s);
@@ -340,10 +350,10 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
     if (UPDATE) {
         // (iii) z^{k+1} = z^k + v, zbar^{k+1} = z^{k+1} + (theta/p_i) v, then
         // (i) of the next iteration: x^{k+2} = (x^{k+1} - tau zbar^{k+1}) / (1 + 2 tau alpha)
-        const float zn = a.z[q] + v;
+        const float zn = z0 + v;
         const float zbar = fmaf(a.coef, v, zn);
         a.z[q] = zn;
-        a.x_out[q] = fmaf(-a.tau, zbar, a.x_in[q]) * a.prox_scale;
+        a.x_out[q] = fmaf(-a.tau, zbar, x0) * a.prox_scale;
     } else {
         a.out[q] = v;
     }
