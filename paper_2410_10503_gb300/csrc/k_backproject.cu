@@ -157,7 +157,7 @@ __device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long
 #endif
 
 template <int PJ, bool SUB>
-__global__ void __launch_bounds__(256) k_backproject(BpArgs a)
+__global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
 {
     pdl_wait();
     pdl_trigger();
@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(256) k_backproject(BpArgs a)
         // the row's pair index is off + floor(beta) + floor(j sin + frac): two
         // magic-biased integers, so the base carries -2 kMagicBits
         const uint32_t wbase = smem_u32(wb) - ((uint32_t)kMagicBits << 4);
-        for (int i = 0; i < cnt; ++i) {
+#pragma unroll
+        for (int i = 0; i < kBatch; ++i) {
+            if (i >= cnt) break;
             const float4 A = *reinterpret_cast<const float4*>(my_slot + st * kBatch + i);   // sin, sin, cos_h, cos_l
             const float4 B = *reinterpret_cast<const float4*>(&my_slot[st * kBatch + i].m); // m, 1 - m, f0, off
             const float b0 = fmaf(le, A.w, fmaf(le, A.z, B.z));      // beta - floor(beta_tile), this column
