@@ -27,6 +27,7 @@ std::mutex g_err_mu;
 std::string g_create_err;
 
 constexpr double kPi = 3.14159265358979323846;
+constexpr int kPlanRounds = 6;   // re-cuts of the forward's items by simulated block time
 constexpr int kNumClasses = 6;
 const char* kClassNames[kNumClasses] = {"warp", "project", "backproject",
                                         "warp_adjoint_update", "gate_draw", "misc"};
@@ -778,7 +779,16 @@ void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float
 // items' ranges are rebuilt; rpt becomes the smallest slot count >= L.  The
 // order of groups changes no result: each group's rays are summed by one warp
 // in line order either way.
-void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vector<RayItem>& items, int& rpt)
+// Wavefronts per 64-bit shared load of a half-warp for angle k's 16
+// consecutive bins: about 1 + min(1, 15 (|inv| - 1)), one near the driving
+// axis and two from ~20 degrees on.
+double load_wavefronts(const mc_ctx* c, int k)
+{
+    return 1.0 + std::min(1.0, 15.0 * (std::fabs(c->inv_k[k]) - 1.0));
+}
+
+void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vector<RayItem>& items, int& rpt,
+                   std::vector<double>* item_time = nullptr)
 {
     const int W = forward_consumer_warps(), half = forward_ring_stages() - 1;
     const int nch = layout_lines(c->n) / lc;
@@ -834,6 +844,33 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vect
         int L = 0;
         for (const auto& l : lists) L = std::max(L, (int)l.size());
         most = std::max(most, L);
+        if (item_time) {
+            // the block's time in a model of the ring: a warp may start chunk ch
+            // once every warp has released chunk ch - kStages; a group's chunk
+            // costs 2.8 + its angle's load wavefronts (the fit of measured block
+            // times), plus a fixed share per chunk
+            const int S = half + 1;
+            std::vector<double> R((size_t)W * nch, 0.0), done((size_t)W * nch, 0.0);
+            for (int w = 0; w < W; ++w)
+                for (int g : lists[w]) {
+                    const int2 grp = groups[it.begin + g];
+                    group_chunk_costs(c, grp.x, grp.y, lc, cost);
+                    const double f = 2.8 + load_wavefronts(c, grp.x);
+                    for (int ch = 0; ch < nch; ++ch) R[(size_t)w * nch + ch] += cost[ch] * f;
+                }
+            double T = 0.0;
+            for (int ch = 0; ch < nch; ++ch) {
+                double gate = 0.0;
+                if (ch >= S)
+                    for (int w = 0; w < W; ++w) gate = std::max(gate, done[(size_t)w * nch + ch - S]);
+                for (int w = 0; w < W; ++w) {
+                    const double prev = ch > 0 ? done[(size_t)w * nch + ch - 1] : 0.0;
+                    done[(size_t)w * nch + ch] = std::max(prev, gate) + R[(size_t)w * nch + ch] + 0.5;
+                    if (ch == nch - 1) T = std::max(T, done[(size_t)w * nch + ch]);
+                }
+            }
+            item_time->push_back(T);
+        }
         const int begin = (int)out.size();
         for (int sl = 0; sl < L; ++sl)
             for (int w = 0; w < W; ++w)
@@ -844,6 +881,55 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vect
     groups.swap(out);
     rpt = 2;
     while (rpt < most) rpt <<= 1;
+}
+
+// Cut the groups of gt into items (partition_items), deal every item to the
+// warps (balance_items) and, for refine > 0 rounds, re-cut with each group's
+// weight scaled by its item's simulated block time over the mean (the time
+// model of balance_items), keeping the cut whose slowest block is fastest.
+// On return gt.groups holds the dealt group entries and items their ranges.
+void plan_forward(const mc_ctx* c, int lc, int sms, int ipb_start, int refine, GroupTable& gt,
+                  std::vector<RayItem>& items, std::vector<int>& set_off, int& ipb, int& rpt)
+{
+    const std::vector<int2> base = gt.groups;
+    std::vector<double> wts(base.size());
+    for (size_t g = 0; g < base.size(); ++g) wts[g] = (double)(gt.cum[g + 1] - gt.cum[g]);
+    double best_T = -1.0;
+    std::vector<int2> best_groups;
+    std::vector<RayItem> best_items;
+    std::vector<int> best_off;
+    int best_ipb = 1, best_rpt = 2;
+    for (int round = 0; round <= refine; ++round) {
+        GroupTable t = gt;
+        t.groups = base;
+        for (size_t g = 0; g < base.size(); ++g) t.cum[g + 1] = t.cum[g] + (long long)std::llround(wts[g]);
+        std::vector<RayItem> its;
+        std::vector<int> off;
+        int ipb_r = 1, rpt_r = 2;
+        partition_items(t, sms, ipb_start, its, off, ipb_r, rpt_r);
+        const std::vector<RayItem> cut = its;        // undealt ranges, for the re-weighting
+        std::vector<double> T;
+        balance_items(c, lc, t.groups, its, rpt_r, refine > 0 ? &T : nullptr);
+        double Tmax = 0.0, Tsum = 0.0;
+        for (double v : T) { Tmax = std::max(Tmax, v); Tsum += v; }
+        if (best_T < 0.0 || Tmax < best_T) {
+            best_T = Tmax;
+            best_groups = t.groups;
+            best_items = its;
+            best_off = off;
+            best_ipb = ipb_r;
+            best_rpt = rpt_r;
+        }
+        if (refine == 0 || T.empty()) break;
+        const double Tmean = Tsum / (double)T.size();
+        for (size_t i = 0; i < cut.size(); ++i)
+            for (int g = cut[i].begin; g < cut[i].end; ++g) wts[g] *= std::pow(T[i] / Tmean, 0.7);
+    }
+    gt.groups.swap(best_groups);
+    items.swap(best_items);
+    set_off.swap(best_off);
+    ipb = best_ipb;
+    rpt = best_rpt;
 }
 
 mc_status build_tables(mc_ctx* c)
@@ -905,8 +991,7 @@ mc_status build_tables(mc_ctx* c)
     std::vector<RayItem> items;
     std::vector<int> set_off;
     int rpt = 2, ipb = 1;
-    partition_items(gt, c->sms, 1, items, set_off, ipb, rpt);
-    balance_items(c, c->lc, gt.groups, items, rpt);
+    plan_forward(c, c->lc, c->sms, 1, kPlanRounds, gt, items, set_off, ipb, rpt);
     const std::vector<int2>& groups = gt.groups;
     c->ipb = ipb;
     c->rpt = rpt;
@@ -1293,7 +1378,7 @@ mc_status mc_warp_adjoint(mc_ctx* c, int32_t gate, const float* v, float* out)
 
 // Install the all-angle forward tables for chunks of lc lines and at least
 // ipb_start items per block (rpt = 0: the smallest that fits, else at least rpt).
-mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min)
+mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min, int refine = 0)
 {
     std::vector<FwdAngle> fa = fwd_angles(c, lc);
     GroupTable gt;
@@ -1301,8 +1386,7 @@ mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min)
     std::vector<RayItem> items;
     std::vector<int> off;
     int ipb = 1, rpt = 2;
-    partition_items(gt, c->sms, ipb_start, items, off, ipb, rpt);
-    balance_items(c, lc, gt.groups, items, rpt);    // the deal depends on the cut and lc
+    plan_forward(c, lc, c->sms, ipb_start, refine, gt, items, off, ipb, rpt);   // the deal depends on the cut and lc
     while (rpt < rpt_min && rpt < 8) rpt <<= 1;
     dfree(c, &c->d_items);
     dfree(c, &c->d_groups);
@@ -1369,7 +1453,7 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
             }
         }
     }
-    if (st == MC_OK) st = install_forward_tables(c, best_lc, best_ipb, best_rpt);
+    if (st == MC_OK) st = install_forward_tables(c, best_lc, best_ipb, best_rpt, kPlanRounds);
     // backprojection: rows per thread
     int best_pj = c->pj;
     float best_bp = 1e30f;
