@@ -1416,13 +1416,21 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // each repetition timed on its own: launched back to back, a kernel's
+    // successor (here the same kernel) would start in its tail and flatter
+    // launch shapes whose tails the iteration's real successor does not hide
     auto timed = [&](auto&& body, float& ms) -> mc_status {
         TRY(body());                                   // warm-up
-        CK(cudaEventRecord(e0, c->stream));
-        for (int r = 0; r < reps; ++r) TRY(body());
-        CK(cudaEventRecord(e1, c->stream));
-        CK(cudaEventSynchronize(e1));
-        CK(cudaEventElapsedTime(&ms, e0, e1));
+        ms = 0.0f;
+        for (int r = 0; r < reps; ++r) {
+            CK(cudaEventRecord(e0, c->stream));
+            TRY(body());
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            float one = 0.0f;
+            CK(cudaEventElapsedTime(&one, e0, e1));
+            ms += one;
+        }
         return MC_OK;
     };
     // the forward's work does not depend on the values: warp the current x of gate 0
@@ -1454,14 +1462,19 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
         }
     }
     if (st == MC_OK) st = install_forward_tables(c, best_lc, best_ipb, best_rpt, kPlanRounds);
-    // backprojection: rows per thread
+    // backprojection: rows per thread, each candidate timed behind a forward
+    // projection (as in the iteration, where the backprojection's blocks fill
+    // the SMs as the forward's blocks drain); the forward is the same for all
     int best_pj = c->pj;
     float best_bp = 1e30f;
     for (int pj : {4, 8, 14, 16}) {
         if (st != MC_OK) break;
         c->pj = pj;
         float ms = 0;
-        st = timed([&] { return backproject(c, GateSel{nullptr, 0}, 1, c->d_b); }, ms);
+        st = timed([&] {
+            TRY(project_store(c, GateSel{nullptr, 0}, 1, c->d_sinoN));
+            return backproject(c, GateSel{nullptr, 0}, 1, c->d_b);
+        }, ms);
         if (st == MC_OK && ms < best_bp) { best_bp = ms; best_pj = pj; }
     }
     c->pj = best_pj;
