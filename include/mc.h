@@ -80,7 +80,7 @@ enum {
     MC_OPT_GRAPH = 1,            /* 1 (default): replay each epoch as a CUDA graph */
     MC_OPT_PROFILE = 2,          /* 1: time every launch with CUDA events (slower)  */
     MC_OPT_TRACE_OBJECTIVE = 3,  /* 1: trace also evaluates O(x) (N extra A_i x)    */
-    MC_OPT_STORAGE = 4           /* storage type of the data d and the dual y read and
+    MC_OPT_STORAGE = 4,          /* storage type of the data d and the dual y read and
                                     written by every iteration: MC_STORE_F32 (default),
                                     MC_STORE_F16 (IEEE binary16) or MC_STORE_BF16
                                     (bfloat16); arithmetic stays float32.  d is rounded
@@ -92,6 +92,17 @@ enum {
                                     within ||d_h - d|| / (2 sqrt(alpha N)).  The float32 d
                                     is kept for mc_objective, mc_set_reference and
                                     mc_solve_normal.  Switching converts the current y. */
+    MC_OPT_TEST_STALL = 5        /* 1: for testing the failure path of the bounded
+                                    device-side waits.  The next forward projection
+                                    this context launches (runs then launch epochs
+                                    directly instead of replaying a graph) gets a
+                                    TMA producer that issues no copies and consumer
+                                    waits limited to 2^12 polls: the waits run out,
+                                    the consumers leave without touching y, the
+                                    device error word is set (so a run reports
+                                    MC_ETIMEOUT) and nothing is left in flight, so
+                                    the context stays usable.  Cleared by that
+                                    launch; 0 clears it before. */
 };
 
 enum { MC_STORE_F32 = 0, MC_STORE_F16 = 1, MC_STORE_BF16 = 2 };

@@ -107,7 +107,7 @@ __device__ __forceinline__ void prefetch_csr(const FwdArgs& a, int gate)
     prefetch_span(a.pf_ent + a.pf_ent_off[gate], (size_t)__ldg(rp + n2) * sizeof(int2), blockIdx.x, gridDim.x);
 }
 
-constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up
+constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up (unless the launch sets one)
 constexpr int kConsumers = 24;               // consumer warps per block
 constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
 constexpr int kBlock = kThreads + 32;        // plus one producer warp
@@ -255,8 +255,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     }
     __syncthreads();
 
+    const uint32_t wlim = a.wait_limit ? a.wait_limit : kWaitLimit;
+
     // ---- producer warp: fill the ring, item after item ----------------------
     if (warp == kConsumers) {
+        if (a.stall) return;          // test of the waits' failure path: no copies in flight
         if (lane == 0) {
             if constexpr (BANDED) {
                 // running chunk count q over the items' bands
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                     for (int c = cb0; c < cb1; ++c, ++q) {
                         const int st = q % kStages;
                         if (q >= kStages &&
-                            !mbar_wait(&empty[st], (uint32_t)((q / kStages - 1) & 1), kWaitLimit)) {
+                            !mbar_wait(&empty[st], (uint32_t)((q / kStages - 1) & 1), wlim)) {
                             atomicExch(s_flag, 1);
                             atomicExch(a.err, kErrTimeout);
                             stop = true;
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                     const float2* src = (items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
                     const int st = g % kStages;
                     if (g >= kStages &&
-                        !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), kWaitLimit)) {
+                        !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), wlim)) {
                         atomicExch(s_flag, 1);
                         atomicExch(a.err, kErrTimeout);
                         break;
@@ -384,7 +387,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         for (int ch = cb0; ch < cb1; ++ch) {
             const int g = BANDED ? q_run++ : it * nch + ch;
             const int st = g % kStages;
-            if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), kWaitLimit)) {
+            if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), wlim)) {
                 atomicExch(s_flag, 1);
                 atomicExch(a.err, kErrTimeout);
                 return;

@@ -163,6 +163,7 @@ struct mc_ctx {
 
     // options
     bool graph_on = true, prof_on = false, trace_obj = false;
+    bool test_stall = false;          // MC_OPT_TEST_STALL: the next forward launch's waits run out
 
     // graphs: [0] SPDHG, [1] PDHG; index parity of cur at capture
     cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
@@ -362,6 +363,12 @@ FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
         }
     }
     a.sel = sel; a.n_slots = n_slots;
+    a.wait_limit = 1u << 24;
+    if (c->test_stall) {              // MC_OPT_TEST_STALL: this launch's waits run out
+        a.stall = 1;
+        a.wait_limit = 1u << 12;
+        c->test_stall = false;
+    }
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
     a.err = c->d_err;
     return a;
@@ -484,7 +491,7 @@ mc_status run_epoch(mc_ctx* c, int which, uint64_t seed, uint32_t stream)
         return which == 0 ? enqueue_spdhg_epoch(c, seed, stream) : enqueue_pdhg_iter(c);
     };
     const int flips = (which == 0) ? ((c->N * c->S) & 1) : 1;
-    if (!c->graph_on || c->prof_on) return enqueue();
+    if (!c->graph_on || c->prof_on || c->test_stall) return enqueue();
     const int par = c->cur;
     if (which == 0 && c->gexec[0][par] && (c->g_seed[0] != seed || c->g_stream[0] != stream)) {
         drop_graphs(c);
@@ -1926,6 +1933,7 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
     case MC_OPT_GRAPH: c->graph_on = value != 0; if (!c->graph_on) drop_graphs(c); return MC_OK;
     case MC_OPT_PROFILE: c->prof_on = value != 0; return MC_OK;
     case MC_OPT_TRACE_OBJECTIVE: c->trace_obj = value != 0; return MC_OK;
+    case MC_OPT_TEST_STALL: c->test_stall = value != 0; return MC_OK;
     case MC_OPT_STORAGE: {
         if (value < 0 || value > 2) return fail(c, MC_EINVAL, "storage must be 0 (f32), 1 (f16) or 2 (bf16)");
         const int v = (int)value;

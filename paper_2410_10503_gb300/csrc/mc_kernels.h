@@ -128,6 +128,8 @@ struct FwdArgs {
     const int* pf_rowptr;
     const int2* pf_ent;
     const long long* pf_ent_off;
+    unsigned wait_limit;       // polls before a ring wait gives up (0: the default 2^24)
+    int stall;                 // 1: the producer issues no copies (tests the waits' failure path)
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 int forward_groups_per_block(int rpt);

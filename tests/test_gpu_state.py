@@ -1,6 +1,7 @@
 """Checkpoint / resume of the solver state and host-simulated allocation
 failure (the failure handling the method itself does not have)."""
 import os
+import time
 
 import numpy as np
 import pytest
@@ -112,3 +113,26 @@ def test_simulated_allocation_failure_is_reported_and_leaves_nothing(mc, prob):
     ok = mc.Context(W.n, W.n_angles, W.n_bins, W.n_gates, rigid=P.motion.rigid)
     ok.set_storage("f16")
     ok.close()
+
+
+@pytest.mark.parametrize("subsets", [1, 4])
+def test_bounded_wait_running_out_is_reported_and_the_context_recovers(mc, prob, subsets):
+    """The failure path of the device-side waits, without a fault: with
+    MC_OPT_TEST_STALL the next forward's producer issues no copies, so its
+    consumers' bounded ring waits run out; the run reports MC_ETIMEOUT, and
+    afterwards the same context (reset) reproduces an undisturbed run bit for
+    bit.  subsets=4 takes the banded forward."""
+    from paper_2410_10503_gb300 import _native as N
+    W, P, sd, norms = prob
+    ref_ctx = make(mc, W, P, norms, subsets=subsets)
+    ref, _ = ref_ctx.spdhg_run(3, seed=sd["gates"])
+    ctx = make(mc, W, P, norms, subsets=subsets)
+    ctx.set_option(N.MC_OPT_TEST_STALL, 1)
+    t0 = time.perf_counter()
+    with pytest.raises(mc.MCError) as e:
+        ctx.spdhg_run(1, seed=sd["gates"])
+    print(f"stalled epoch returned after {time.perf_counter() - t0:.3f} s")
+    assert "MC_ETIMEOUT" in str(e.value)
+    ctx.reset()
+    x, _ = ctx.spdhg_run(3, seed=sd["gates"])
+    np.testing.assert_array_equal(x, ref)
