@@ -251,18 +251,22 @@ def run_ours(args, W):
 
     # ---- roofline of the dominant kernel (on-chip gather bytes)
     S_cnt = algorithmic_units(W)
-    dom = max(("project", "backproject"), key=lambda k: kernels[k]["avg_us"] or 0)
-    if dom == "project":
-        alg_bytes = 8.0 * S_cnt            # two texel reads per in-image sample
-    else:
-        alg_bytes = 8.0 * S_cnt            # one dual value per (pixel, bin) pair: 2S pairs x 4 B
-    avg_s = kernels[dom]["avg_us"] * 1e-6
     peak = float(args.l1_peak_gbs)
-    achieved = alg_bytes / avg_s / 1e9
-    roof = {"bound": "l1", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-            "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(dom),
-            "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
-            "peak_source": "152 SMs x 128 B/clk shared/L1 load x 2.07 GHz (derived)"}
+
+    def roofline(kern):
+        # both projectors: 8 B per unit of work (forward: two texel reads per
+        # in-image sample; backprojection: 2 S (pixel, bin) pairs x 4 B)
+        alg_bytes = 8.0 * S_cnt
+        avg_s = kernels[kern]["avg_us"] * 1e-6
+        achieved = alg_bytes / avg_s / 1e9
+        return {"bound": "l1", "kernel": kern, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kern),
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_us": round(avg_s * 1e6, 2),
+                "peak_source": "152 SMs x 128 B/clk shared/L1 load x 2.07 GHz (derived)"}
+
+    dom = max(("project", "backproject"), key=lambda k: kernels[k]["avg_us"] or 0)
+    roof = roofline(dom)
+    roof_other = roofline("backproject" if dom == "project" else "project")
     hbm_peak = None
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -275,7 +279,8 @@ def run_ours(args, W):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": workload_config(W) | {"parallelism": f"replicas x{world}"},
-        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * (1 + 4 * N),
+        "roofline": roof, "roofline_other_projector": roof_other, "e2e": e2e,
+        "gpu_launches": args.steps * (1 + 4 * N),
         "clocks": clk.summary(), "kernels": kernels,
         "norms2_max": float(np.max(norms[:N])), "kappa_spdhg": ctx.steps()["kappa"],
         "hbm_peak_gbs_measured": hbm_peak, "wall_s": round(wall, 3),
