@@ -249,7 +249,7 @@ def run_ours(args, W):
     e2e = {"value": args.steps * N * world / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(d_host.numel() * 4), "d2h_bytes_per_step": int(x_host.numel() * 4)}
 
-    # ---- roofline of the dominant kernel (on-chip gather bytes)
+    # ---- roofline of the dominant kernel (on-chip gather bytes per unit of work)
     S_cnt = algorithmic_units(W)
     peak = float(args.l1_peak_gbs)
 
