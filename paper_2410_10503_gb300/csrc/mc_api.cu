@@ -273,7 +273,10 @@ cudaEvent_t ev_get(mc_ctx* c)
         return e;
     }
     cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;   // the launch then goes untimed
+    }
     return e;
 }
 
@@ -285,10 +288,15 @@ mc_status launch(mc_ctx* c, int cls, const char* what, F&& f)
     if (c->prof_on) {
         a = ev_get(c);
         b = ev_get(c);
-        cudaEventRecord(a, c->stream);
+        if (!a || !b) {
+            if (a) c->ev_pool.push_back(a);
+            if (b) c->ev_pool.push_back(b);
+            a = b = nullptr;
+        }
     }
+    if (a) cudaEventRecord(a, c->stream);
     const cudaError_t e = f();
-    if (c->prof_on) {
+    if (a) {
         cudaEventRecord(b, c->stream);
         c->prof.push_back({cls, a, b});
     }
@@ -1418,11 +1426,15 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
     if (reps < 1 || reps > 1000) return fail(c, MC_EINVAL, "reps must be in [1, 1000]");
     CK(cudaStreamSynchronize(c->stream));
     drop_graphs(c);
-    const bool prof = c->prof_on;
-    c->prof_on = false;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(e0);
+        return fail(c, MC_ECUDA, "cudaEventCreate failed");
+    }
+    const bool prof = c->prof_on;
+    c->prof_on = false;
     // each repetition timed on its own: launched back to back, a kernel's
     // successor (here the same kernel) would start in its tail and flatter
     // launch shapes whose tails the iteration's real successor does not hide
