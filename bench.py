@@ -62,6 +62,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.start = 0
 
     def __enter__(self):
         try:
@@ -71,8 +72,14 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: wait (at most 3 s) for its first
+            # sample so that the timed region is covered from its start
+            t_end = time.perf_counter() + 3.0
+            while not self.lines and self.proc.poll() is None and time.perf_counter() < t_end:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.start = len(self.lines)
         return self
 
     def _read(self):
@@ -91,7 +98,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # samples taken inside the timed region; the one before it only when the
+        # region was shorter than the sampling interval
+        inside = self.lines[self.start:]
+        for ln in inside or self.lines:
             p = [t.strip() for t in ln.split(",")]
             if len(p) < 9:
                 continue
