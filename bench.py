@@ -574,13 +574,14 @@ def run_reference(args, W):
     dt = time.perf_counter() - t0
     v = args.steps / stride / dt
     sample = (f"one A_i+A_i^* pair of {W.name} per step" if stride == 1 else
-              f"per step one A_i+A_i^* pair of {W.name} on every {stride}th angle "
-              f"({W.n_angles // stride} of {W.n_angles}: 1/{stride} of a pair)")
+              f"per step one A_i+A_i^* pair of {W.name} on the {W.n_angles // stride} angles "
+              f"k = 0, {stride}, {2 * stride}, ... of {W.n_angles} (1/{stride} of a pair)")
     out = {"metric": METRIC, "value": round(v, 4), "unit": UNIT, "impl": "reference",
            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(dt / args.steps * 1e3, 2), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": workload_config(W) | {"step": f"1/{stride} of an A_i+A_i^* pair (FP64 oracle, host)"},
+           "config": workload_config(W) | {"step": f"1/{stride} of an A_i+A_i^* pair (FP64 oracle, host)",
+                                           "l2": "not applicable (host oracle)"},
            "cpu_baseline": {"value": round(v, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": round(v, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -63,4 +63,4 @@ def test_reference_arm_prints_one_json_line():
     out = json.loads(lines[0])
     assert out["impl"] == "reference" and out["unit"] == bench.UNIT and out["steps"] == 2
     assert out["value"] > 0 and out["e2e"]["value"] == out["value"]
-    assert out["cpu_baseline"]["kind"] == "oracle" and "every 4th angle" in out["cpu_baseline"]["sample"]
+    assert out["cpu_baseline"]["kind"] == "oracle" and "k = 0, 4, 8, ..." in out["cpu_baseline"]["sample"]
