@@ -64,3 +64,26 @@ def test_reference_arm_prints_one_json_line():
     assert out["impl"] == "reference" and out["unit"] == bench.UNIT and out["steps"] == 2
     assert out["value"] > 0 and out["e2e"]["value"] == out["value"]
     assert out["cpu_baseline"]["kind"] == "oracle" and "k = 0, 4, 8, ..." in out["cpu_baseline"]["sample"]
+
+
+@pytest.mark.parametrize("n,na,nb", [(16, 12, 23), (15, 20, 22), (9, 4, 13), (12, 16, 12)])
+def test_algorithmic_units_match_a_brute_force_count(n, na, nb):
+    """S (the roofline's unit: Joseph samples with a non-zero in-image
+    weight) against the oracle: an image that is 1 on one driving line (a
+    column for column-driven angles, a row otherwise) projects to a non-zero
+    value on ray (k, b) exactly when that ray's sample on the line has a
+    non-zero weight, since the ray's other samples lie on other lines."""
+    from types import SimpleNamespace
+    g = O.Geometry(n, na, nb)
+    cols = np.zeros(na, dtype=np.int64)
+    rows = np.zeros(na, dtype=np.int64)
+    for l in range(n):
+        e = np.zeros((n, n))
+        e[:, l] = 1.0
+        cols += np.count_nonzero(O.A(e, g), axis=1)
+        e = np.zeros((n, n))
+        e[l, :] = 1.0
+        rows += np.count_nonzero(O.A(e, g), axis=1)
+    xd = np.array([na <= 4 * k <= 3 * na for k in range(na)])
+    brute = int(np.sum(np.where(xd, cols, rows)))
+    assert bench.algorithmic_units(SimpleNamespace(n=n, n_angles=na, n_bins=nb)) == brute
