@@ -133,6 +133,24 @@ const char* mc_last_error(const mc_ctx* ctx);
  * g(x) = alpha ||x||^2 (Sec. II-A).  Resets the solver state. */
 mc_status mc_set_data(mc_ctx* ctx, const float* d, double alpha);
 
+/* Double-buffered upload for callers that reconstruct one data set after
+ * another (the gated data d of Sec. II-A).  mc_stage_data starts copying the
+ * next d (N x n_angles x n_bins float32, HOST memory; pinned memory makes the
+ * copy asynchronous) into a staging buffer of the context, on a copy stream
+ * of the context's own, and returns without waiting: the upload overlaps
+ * whatever the context runs meanwhile.  d must stay valid and unchanged until
+ * the copy has landed, at the latest when mc_commit_data returns.  A second
+ * mc_stage_data before the commit replaces the staged data.  The staging
+ * buffer (one d) is allocated on the first call.  Errors: MC_EINVAL (NULL or
+ * device d), MC_ENOMEM, MC_ECUDA.
+ * mc_commit_data then makes the staged data current exactly as
+ * mc_set_data(ctx, d, alpha) does (same solver-state reset, step sizes and
+ * storage conversion): the context's stream waits for the upload and copies
+ * it into place on the device; the call returns when that is done.  MC_ESTATE
+ * when nothing is staged. */
+mc_status mc_stage_data(mc_ctx* ctx, const float* d);
+mc_status mc_commit_data(mc_ctx* ctx, double alpha);
+
 /* out = A_i x = A D_i x (Sec. II-A).  x: n x n; out: n_angles x n_bins. */
 mc_status mc_forward(mc_ctx* ctx, int32_t gate, const float* x, float* out);
 

@@ -225,6 +225,24 @@ class Context:
         p, k = _arg(d, np.float32, self.n_gates * self.sino_count, "d")
         self._call(self._L.mc_set_data, p, float(alpha), cuda_args=(d,))
 
+    def stage_data(self, d):
+        """Start uploading the next data set (host array; pinned memory for an
+        asynchronous copy) while the context keeps working (mc_stage_data);
+        commit_data makes it current.  The arrays are kept alive until then."""
+        if _is_tensor(d) and d.is_cuda:
+            raise TypeError("stage_data takes host data; use set_data for CUDA tensors")
+        p, k = _arg(d, np.float32, self.n_gates * self.sino_count, "d")
+        self._check(self._L.mc_stage_data(self._h, p))
+        # every array staged since the last commit may still be in flight
+        self._staged = (getattr(self, "_staged", None) or []) + [k]
+
+    def commit_data(self, alpha: float):
+        """Make the staged data current, as set_data would (mc_commit_data).
+        The staged arrays are released once the commit has succeeded (a
+        refused commit leaves the upload staged)."""
+        self._check(self._L.mc_commit_data(self._h, float(alpha)))
+        self._staged = None
+
     @property
     def n_blocks(self) -> int:
         """Sampled blocks: gates, or gates x angle subsets after set_subsets."""

@@ -35,6 +35,8 @@ SIGNATURES = {
     "mc_destroy": (None, [_VP]),
     "mc_last_error": (ctypes.c_char_p, [_VP]),
     "mc_set_data": (_I32, [_VP, _VP, _D]),
+    "mc_stage_data": (_I32, [_VP, _VP]),
+    "mc_commit_data": (_I32, [_VP, _D]),
     "mc_forward": (_I32, [_VP, _I32, _VP, _VP]),
     "mc_adjoint": (_I32, [_VP, _I32, _VP, _VP]),
     "mc_project": (_I32, [_VP, _VP, _VP]),

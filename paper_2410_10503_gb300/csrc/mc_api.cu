@@ -125,6 +125,13 @@ struct mc_ctx {
     bool have_data = false;
     double alpha = 0;
 
+    // staged upload of the next data set (mc_stage_data / mc_commit_data), allocated on first use
+    float* d_stage = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t stage_ev = nullptr;   // the staged upload has landed
+    cudaEvent_t commit_ev = nullptr;  // the commit's device copy has read the staging buffer
+    bool staged = false;
+
     // scratch per gate slot
     float2* d_lrow = nullptr;
     float2* d_lcol = nullptr;
@@ -1181,6 +1188,12 @@ void mc_destroy(mc_ctx* c)
     drop_graphs(c);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->stage_ev) cudaEventDestroy(c->stage_ev);
+    if (c->commit_ev) cudaEventDestroy(c->commit_ev);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1275,14 +1288,12 @@ mc_status mc_reset(mc_ctx* c)
     return finish(c);
 }
 
-mc_status mc_set_data(mc_ctx* c, const float* d, double alpha)
+namespace {
+
+// the part of mc_set_data after d has been copied into d_d on the context's stream
+mc_status data_in_place(mc_ctx* c, double alpha)
 {
-    if (!c) return MC_EINVAL;
-    TRY(check_ptr(c, d, "d"));
-    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MC_EINVAL, "alpha must be finite and > 0");
     const size_t cnt = (size_t)c->N * c->na * c->nb;
-    CK(cudaMemcpyAsync(c->d_d, d, cnt * sizeof(float),
-                       ptr_kind(c, d) == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (c->store != 0)
         TRY(launch(c, C_MISC, "to_store", [&] { return launch_to_store(c->d_d, c->d_dh, cnt, c->store, c->stream); }));
     c->alpha = alpha;
@@ -1292,6 +1303,56 @@ mc_status mc_set_data(mc_ctx* c, const float* d, double alpha)
     TRY(update_steps(c));
     CK(cudaStreamSynchronize(c->stream));
     return finish(c);
+}
+
+}  // namespace
+
+mc_status mc_set_data(mc_ctx* c, const float* d, double alpha)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_ptr(c, d, "d"));
+    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MC_EINVAL, "alpha must be finite and > 0");
+    const size_t cnt = (size_t)c->N * c->na * c->nb;
+    CK(cudaMemcpyAsync(c->d_d, d, cnt * sizeof(float),
+                       ptr_kind(c, d) == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    return data_in_place(c, alpha);
+}
+
+mc_status mc_stage_data(mc_ctx* c, const float* d)
+{
+    if (!c) return MC_EINVAL;
+    TRY(check_ptr(c, d, "d"));
+    if (ptr_kind(c, d) != 0) return fail(c, MC_EINVAL, "d must be host memory (use mc_set_data for device data)");
+    const size_t cnt = (size_t)c->N * c->na * c->nb;
+    if (!c->d_stage) {
+        TRY(dalloc(c, &c->d_stage, cnt));
+        // dalloc clears the buffer on the context's stream: let that finish
+        // before the copy stream writes into it
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (!c->copy_stream) CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    if (!c->stage_ev) CK(cudaEventCreateWithFlags(&c->stage_ev, cudaEventDisableTiming));
+    if (!c->commit_ev) CK(cudaEventCreateWithFlags(&c->commit_ev, cudaEventDisableTiming));
+    // a commit still reading the staging buffer on the context's stream finishes first
+    // (waiting on an event never recorded returns at once)
+    CK(cudaStreamWaitEvent(c->copy_stream, c->commit_ev, 0));
+    CK(cudaMemcpyAsync(c->d_stage, d, cnt * sizeof(float), cudaMemcpyHostToDevice, c->copy_stream));
+    CK(cudaEventRecord(c->stage_ev, c->copy_stream));
+    c->staged = true;
+    return finish(c);
+}
+
+mc_status mc_commit_data(mc_ctx* c, double alpha)
+{
+    if (!c) return MC_EINVAL;
+    if (!c->staged) return fail(c, MC_ESTATE, "no data staged (mc_stage_data)");
+    if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MC_EINVAL, "alpha must be finite and > 0");
+    const size_t cnt = (size_t)c->N * c->na * c->nb;
+    CK(cudaStreamWaitEvent(c->stream, c->stage_ev, 0));
+    CK(cudaMemcpyAsync(c->d_d, c->d_stage, cnt * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaEventRecord(c->commit_ev, c->stream));
+    c->staged = false;
+    return data_in_place(c, alpha);
 }
 
 mc_status mc_forward(mc_ctx* c, int32_t gate, const float* x, float* out)
