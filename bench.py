@@ -11,8 +11,8 @@ and N transpose warps with the fused z / zbar / prox update: N pairs.  The
 epoch is replayed as a CUDA graph.  Inputs stay resident in HBM; L2 (129 MB)
 is flushed between steps by writing a 256 MB buffer outside the timed events.
 
---impl reference times the FP64 CPU oracle (a deliberately slow checker) on
-one pair per step.
+--impl reference times the FP64 CPU oracle (a deliberately slow checker) on a
+bounded sample per step: one pair on every s-th angle of the workload.
 """
 from __future__ import annotations
 
@@ -310,6 +310,7 @@ def run_ours(args, W):
         out["batch_mixed_slices"] = batch_legs(args.batch_slices, args.batch_epochs)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
+        out["cpu_baseline_more"] = cpu_baseline_more(W)
     ctx.close()
     if dist:
         dist.destroy_process_group()
@@ -562,6 +563,80 @@ def cpu_baseline(W, samples=3):
     dt = time.perf_counter() - t0
     return {"value": round(samples / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{samples} A_i+A_i^* pairs of {W.name} (FP64, single thread)"}
+
+
+def _oracle_pairs_worker(job):
+    """Spawned process: time `count` A_i + A_i^* pairs of workload `wl` on
+    the oracle (one thread); returns (count, seconds)."""
+    wl, count, first = job
+    W = S.WORKLOADS[wl]
+    O, P, x, y = _oracle_pair_setup(W)
+    t0 = time.perf_counter()
+    for i in range(first, first + count):
+        O.Ai(x, P, i % W.n_gates)
+        O.Ait(y, P, i % W.n_gates)
+    return count, time.perf_counter() - t0
+
+
+def cpu_baseline_more(W, cores=None, small="rigid128", small_pairs=20, epochs=50, timeout_s=300.0):
+    """Further timings of the oracle as it stands, baselines only; each leg is
+    fenced, so that a failure is reported in its entry instead of ending the run:
+    - all_cores: one pair of W per core, in that many spawned processes (the
+      oracle itself stays single-threaded); pairs / the slowest process's time;
+    - pairs_<small>: pairs/s on the 128^2 workload, one thread;
+    - solvers_<small>: a whole `epochs`-epoch SPDHG and PDHG run of it, one
+      thread (norms and data set up outside the timing)."""
+    from concurrent.futures import ProcessPoolExecutor
+    import multiprocessing as mp
+    out = {}
+    try:
+        if cores is None:
+            cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+        ex = ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"))
+        try:
+            futs = [ex.submit(_oracle_pairs_worker, (W.name, 1, c)) for c in range(cores)]
+            res = [f.result(timeout=timeout_s) for f in futs]
+        finally:
+            ex.shutdown(wait=False, cancel_futures=True)
+        n = sum(r[0] for r in res)
+        slowest = max(r[1] for r in res)
+        out["all_cores"] = {"value": round(n / slowest, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"one A_i+A_i^* pair of {W.name} in each of {cores} spawned processes "
+                                      f"(one thread each); pairs / the slowest process's time"}
+    except Exception as e:
+        out["all_cores"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    W1 = S.WORKLOADS[small]
+    try:
+        O, P1, x1, y1 = _oracle_pair_setup(W1)
+        t0 = time.perf_counter()
+        for i in range(small_pairs):
+            O.Ai(x1, P1, i % W1.n_gates)
+            O.Ait(y1, P1, i % W1.n_gates)
+        dt = time.perf_counter() - t0
+        out[f"pairs_{small}"] = {"value": round(small_pairs / dt, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                                 "sample": f"{small_pairs} A_i+A_i^* pairs of {small}"}
+    except Exception as e:
+        out[f"pairs_{small}"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    try:
+        import oracle as O
+        sd = S.seeds(W1.cid)
+        g = O.Geometry(W1.n, W1.n_angles, W1.n_bins)
+        m = O.Motion(rigid=S.rigid_motion(W1.n_gates, W1.max_rot_deg, W1.max_shift, sd["motion"]))
+        xt = S.phantom(W1.n, W1.n_ellipses, sd["phantom"], W1.axis_lo, W1.axis_hi)
+        P = O.make_problem(g, m, xt, S.noise(W1.n_gates, W1.n_angles, W1.n_bins, sd["noise"]),
+                           W1.alpha, W1.noise_level)
+        norms = O.gate_norms2(P, iters=30, tol=1e-13)
+        t0 = time.perf_counter()
+        O.spdhg(P, epochs, O.step_sizes(norms[:P.N].max(), P.alpha, P.N, P.N), seed=sd["gates"])
+        t_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        O.pdhg(P, epochs, O.step_sizes(norms[P.N], P.alpha, P.N, 1))
+        t_p = time.perf_counter() - t0
+        out[f"solvers_{small}"] = {"epochs": epochs, "spdhg_s": round(t_s, 3), "pdhg_s": round(t_p, 3),
+                                   "cores": 1, "kind": "oracle"}
+    except Exception as e:
+        out[f"solvers_{small}"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    return out
 
 
 def run_reference(args, W):

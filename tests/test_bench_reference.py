@@ -87,3 +87,14 @@ def test_algorithmic_units_match_a_brute_force_count(n, na, nb):
     xd = np.array([na <= 4 * k <= 3 * na for k in range(na)])
     brute = int(np.sum(np.where(xd, cols, rows)))
     assert bench.algorithmic_units(SimpleNamespace(n=n, n_angles=na, n_bins=nb)) == brute
+
+
+def test_cpu_baseline_more_legs_report_without_failing():
+    """The extra oracle timings on a small workload: two spawned processes,
+    a few pairs and a short solver run; every leg reports a value."""
+    out = bench.cpu_baseline_more(S.WORKLOADS["rigid128"], cores=2, small_pairs=2, epochs=2,
+                                  timeout_s=120.0)
+    assert out["all_cores"]["cores"] == 2 and out["all_cores"]["value"] > 0, out
+    assert out["pairs_rigid128"]["value"] > 0, out
+    s = out["solvers_rigid128"]
+    assert s["epochs"] == 2 and s["spdhg_s"] > 0 and s["pdhg_s"] > 0, out
