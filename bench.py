@@ -308,7 +308,7 @@ def run_ours(args, W):
         out["storage_rbf512"] = storage_legs(args.storage_epochs)
     if args.batch_slices > 0:
         out["batch_mixed_slices"] = batch_legs(args.batch_slices, args.batch_epochs)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
         out["cpu_baseline_more"] = cpu_baseline_more(W)
     ctx.close()
