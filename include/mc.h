@@ -70,9 +70,21 @@ typedef struct {
                               host or device; q = p + u(p)                     */
 } mc_motion;
 
+/* Serial sampling of one gate per SPDHG iteration, P(i) = p_i (Algorithm 1
+ * step (ii), Sec. II-A).  p == NULL: uniform, p_i = 1/N, gate =
+ * floor(word0 N / 2^32).  Otherwise p (HOST, N doubles, each finite and > 0)
+ * is normalised to sum 1 and the gate is the first i with
+ * word0 < floor(2^32 (p_0 + ... + p_i)) (the running sum taken in gate order;
+ * the last threshold is 2^32), word0 the first Philox4x32-10 output word of
+ * the iteration's counter.  Step (iii) then weights the increment by theta/p_i,
+ * and the step sizes follow the uniform rule (mc_get_steps) with n = 1/min_i p_i
+ * in place of N, so that omega tau sigma ||A_i||^2 = min_j p_j <= p_i for every
+ * gate (reduces to the uniform steps at p_i = 1/N).  Non-uniform p is defined
+ * over gates only: with angle subsets (mc_set_subsets, S > 1) p must be NULL. */
 typedef struct {
     uint64_t seed;         /* Philox4x32-10 key                                */
     uint32_t stream;       /* counter word 1; lets runs share a seed           */
+    const double* p;       /* NULL (uniform) or N sampling probabilities, host */
 } mc_sampling;
 
 /* Options for mc_set_option. */
@@ -239,7 +251,9 @@ mc_status mc_set_norms(mc_ctx* ctx, const double* norms2);
  * norm for PDHG), s = sqrt(1 + kappa), n = N (SPDHG) or 1 (PDHG):
  * omega = 1 - 2/(n (1 + s)), sigma_i = 1/(mu_f (s - 1)),
  * tau = (1 - omega)/(2 mu_g omega), theta = omega, so that the per-epoch rate
- * is omega^n = l(kappa, n) of Sec. II-B.  MC_ESTATE before norms and data. */
+ * is omega^n = l(kappa, n) of Sec. II-B.  After an SPDHG run (or batch run)
+ * with non-uniform sampling p, the SPDHG steps use n = 1/min_i p_i (see
+ * mc_sampling) until a run with another p.  MC_ESTATE before norms and data. */
 mc_status mc_get_steps(mc_ctx* ctx, int32_t pdhg, double* out);
 
 /* Reference solution x* (n x n) for the trace; y_i* = (2/N)(A_i x* - d_i)
@@ -261,7 +275,8 @@ mc_status mc_reset(mc_ctx* ctx);
  * from the current state:
  *   (i)   x^{k+1} = prox_{tau g}(x^k - tau zbar^k) = (x^k - tau zbar^k)/(1 + 2 tau alpha)
  *   (ii)  draw i (Philox4x32-10 on the device, key = seed, counter =
- *         (k mod 2^32, stream, k >> 32, 0), i = floor(word0 * N / 2^32));
+ *         (k mod 2^32, stream, k >> 32, 0), i = floor(word0 * N / 2^32), or by
+ *         the thresholds of sampling->p, see mc_sampling);
  *         y_i^{k+1} = prox_{sigma f_i^*}(y_i^k + sigma A_i x^{k+1})
  *                   = (y_i^k + sigma (A_i x^{k+1} - d_i)) / (1 + sigma N/2)
  *   (iii) z^{k+1} = z^k + A_i^* (y_i^{k+1} - y_i^k),
@@ -330,6 +345,18 @@ mc_status mc_state_size(mc_ctx* ctx, uint64_t* bytes);
 mc_status mc_save_state(mc_ctx* ctx, void* buf, uint64_t cap);
 mc_status mc_load_state(mc_ctx* ctx, const void* buf, uint64_t size);
 
+/* Measured rate of conflict-free 64-bit shared-memory loads on the current
+ * device (no context needed): the bound of both projectors, which gather
+ * 8-byte pairs from shared memory (the roofline of the Joseph A and A^T of
+ * Sec. II-A).  Two blocks of 1024 threads per SM stream ld.shared.b64 at
+ * consecutive addresses, about reps x 5 GB in total after one warm-up
+ * launch, timed by CUDA events on a stream of its own.  out (host, 3 doubles):
+ * {bytes per second over the whole GPU, bytes per SM clock, the SM clock in
+ * GHz seen by the kernel (clock64 span / event time)}.  Allocates two small
+ * scratch buffers and frees them; changes no device setting.  The paper has
+ * no counterpart; this is a measurement aid. */
+mc_status mc_measure_shared_load_peak(int32_t reps, double* out);
+
 /* Library version string. */
 const char* mc_version(void);
 
@@ -348,14 +375,34 @@ const char* mc_version(void);
  * cudaMalloc, cudaFree or other allocation.  Sizes whose scratch exceeds the
  * array (about n > 1220 at 720 angles) return MC_EINVAL.  The first call on
  * each device sets up (looks up the array's device address, sets kernel
- * attributes); make that first call before any stream capture.  Every call
+ * attributes); make that first call before any stream capture (a first call
+ * inside a capture returns MC_ESTATE).  Every later call made outside a
+ * capture looks the address up again, so a device reset by the host
+ * application leaves no stale pointer.  Every call
  * shares the array: calls that overlap on the GPU (different streams, or
  * different host threads) race and must be serialised by the caller.  Work
  * is ordered on cuda_stream (NULL = legacy default stream) and the call
  * returns before it completes.  err (nullable, err_cap bytes) receives a
- * message on failure. */
+ * message when the call itself fails (arguments, sizes, launches).  A
+ * failure on the device while the work runs (a bounded wait that ran out) is
+ * not known when the call returns: it is recorded in the array's error word
+ * and reported by mc_forward_static_status.  Test hook: with the environment
+ * variable MC_STATIC_TEST_STALL=1 (read at every call) the projection's TMA
+ * producer issues no copies and its consumers' waits run out after 2^12
+ * polls, leaving nothing in flight, so that the failure report can be tested. */
 mc_status mc_forward_static(const mc_geometry* geom, const double* rigid, const float* x,
                             float* out, void* cuda_stream, char* err, int32_t err_cap);
+
+/* Outcome on the device of the last mc_forward_static call on the current
+ * device: waits for cuda_stream (the stream that call used, or one ordered
+ * after it; not while it is being captured), reads the 4-byte error word of
+ * the fixed array, and returns MC_OK, MC_ETIMEOUT (a bounded wait of the
+ * projection ran out: out is incomplete) or MC_EDEVICE (a bounds check of a
+ * checked build fired).  The word is cleared by the next mc_forward_static
+ * call, not by this one.  Allocates nothing.  MC_ESTATE before the first
+ * mc_forward_static call on the device; err as in mc_forward_static.  The
+ * paper has no counterpart; this belongs to the allocation-free entry point. */
+mc_status mc_forward_static_status(void* cuda_stream, char* err, int32_t err_cap);
 
 #ifdef __cplusplus
 }

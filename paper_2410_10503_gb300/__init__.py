@@ -107,6 +107,13 @@ class Context:
         self._h = out.value
         self.kind = "rigid" if rigid is not None else "field"
         self._field_version = {}
+        # the field each gate currently uses (copies), so that autograd can put
+        # a field back after differentiating through an older one
+        self._fields_now = {}
+        self._fields_init = None
+        if fields is not None:
+            self._fields_init = (fields.detach().clone() if _is_tensor(fields)
+                                 else np.array(fields, dtype=np.float32, copy=True))
         self.subsets = 1
 
     # -- plumbing --------------------------------------------------------------
@@ -201,10 +208,22 @@ class Context:
         p, k = _arg(field, np.float32, 2 * self.img_count, "field")
         self._call(self._L.mc_set_field, gate, p, cuda_args=(field,))
         self._field_version[gate] = self._field_version.get(gate, 0) + 1
+        self._fields_now[gate] = (field.detach().clone() if _is_tensor(field)
+                                  else np.array(field, dtype=np.float32, copy=True))
 
     def field_version(self, gate: int) -> int:
         """How many times set_field replaced this gate's field."""
         return self._field_version.get(gate, 0)
+
+    def current_field(self, gate: int):
+        """A copy of the field gate `gate` uses now (2 x n x n): the last one
+        given to set_field, else the one given at construction."""
+        if self.kind != "field":
+            raise ValueError("rigid-motion context has no displacement field")
+        if gate in self._fields_now:
+            return self._fields_now[gate]
+        f = self._fields_init
+        return f.reshape(self.n_gates, 2, self.n, self.n)[gate]
 
     def vjp(self, gate: int, x, r, grad_x=True, grad_field=True):
         """(A_i^* r, b * grad of the warp sample w.r.t. u_i) with b = A^T r
@@ -291,7 +310,19 @@ class Context:
                    cuda_args=(x_out,))
         return x_out, int(info[0]), float(info[1])
 
-    def _run(self, which, epochs, seed, stream, x_out, trace, like):
+    def _sampling(self, seed, stream, p):
+        """mc_sampling for a run or draw; p (N probabilities) is kept alive
+        on the struct while the call runs."""
+        s = N.mc_sampling(int(seed), int(stream), None)
+        if p is not None:
+            arr = np.ascontiguousarray(p, dtype=np.float64)
+            if arr.size != self.n_gates:
+                raise ValueError(f"p: expected {self.n_gates} probabilities, got {arr.size}")
+            s.p = arr.ctypes.data
+            s._keep = arr
+        return s
+
+    def _run(self, which, epochs, seed, stream, x_out, trace, like, p=None):
         if x_out is None:
             x_out = _empty_like_kind(like, (self.n, self.n)) if like is not None else \
                 np.empty((self.n, self.n), np.float32)
@@ -301,26 +332,28 @@ class Context:
         tr = np.full((max(epochs, 0), 3), np.nan) if trace else None
         pt = tr.ctypes.data if tr is not None else None
         if which == 0:
-            s = N.mc_sampling(seed, stream)
+            s = self._sampling(seed, stream, p)
             self._call(self._L.mc_spdhg_run, epochs, ctypes.byref(s), px, pt, cuda_args=(x_out,))
         else:
             self._call(self._L.mc_pdhg_run, epochs, px, pt, cuda_args=(x_out,))
         return x_out, tr
 
-    def spdhg_run(self, epochs: int, seed: int, stream: int = 0, x_out=None, trace=False, like=None):
+    def spdhg_run(self, epochs: int, seed: int, stream: int = 0, x_out=None, trace=False, like=None,
+                  p=None):
         """Algorithm 1 for `epochs` epochs; returns (x^K, trace or None).
-        x_out=False skips the copy of x (fully asynchronous with device arrays)."""
-        return self._run(0, epochs, seed, stream, x_out, trace, like)
+        x_out=False skips the copy of x (fully asynchronous with device arrays).
+        p: None (uniform) or N sampling probabilities P(i) = p_i."""
+        return self._run(0, epochs, seed, stream, x_out, trace, like, p)
 
     def pdhg_run(self, epochs: int, x_out=None, trace=False, like=None):
         return self._run(1, epochs, 0, 0, x_out, trace, like)
 
-    def draw_gates(self, seed: int, stream: int, k0: int, count: int, out=None):
+    def draw_gates(self, seed: int, stream: int, k0: int, count: int, out=None, p=None):
         if out is None:
             out = np.empty(count, np.int32)
-        p = _arg(out, np.int32, count, "out")[0]
-        s = N.mc_sampling(seed, stream)
-        self._call(self._L.mc_draw_gates, ctypes.byref(s), k0, count, p, cuda_args=(out,))
+        po = _arg(out, np.int32, count, "out")[0]
+        s = self._sampling(seed, stream, p)
+        self._call(self._L.mc_draw_gates, ctypes.byref(s), k0, count, po, cuda_args=(out,))
         return out
 
     def objective(self, x) -> float:
@@ -379,6 +412,20 @@ class Context:
         return out.value
 
 
+def shared_load_peak(reps: int = 20):
+    """Measured conflict-free 64-bit shared-load rate of the current device
+    (mc_measure_shared_load_peak): dict with bytes_per_s, bytes_per_clk_per_sm,
+    sm_ghz and sms, or None if the measurement failed."""
+    out = np.zeros(3)
+    st = lib().mc_measure_shared_load_peak(int(reps), out.ctypes.data)
+    if st != 0:
+        return None
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count \
+        if torch is not None and torch.cuda.is_available() else None
+    return {"bytes_per_s": float(out[0]), "bytes_per_clk_per_sm": float(out[1]), "sm_ghz": float(out[2]),
+            "sms": sms}
+
+
 def project_gate(ctx: Context, gate: int, x, field=None):
     """Differentiable A_i x = A D_{u_i} x on CUDA tensors (torch autograd).
 
@@ -389,15 +436,19 @@ def project_gate(ctx: Context, gate: int, x, field=None):
     return GateProjection.apply(ctx, gate, x, field)
 
 
-def batch_spdhg_run(contexts, epochs: int, seeds, streams=None):
+def batch_spdhg_run(contexts, epochs: int, seeds, streams=None, ps=None):
     """SPDHG epochs on many independent slice contexts at once
     (mc_batch_spdhg_run): per context identical to ctx.spdhg_run(epochs,
-    seed) but interleaved epoch by epoch across the contexts' streams."""
+    seed) but interleaved epoch by epoch across the contexts' streams.
+    ps: None, or per context None / N sampling probabilities."""
     count = len(contexts)
     if streams is None:
         streams = [0] * count
+    if ps is None:
+        ps = [None] * count
     arr = (ctypes.c_void_p * count)(*[c._h for c in contexts])
-    smp = (N.mc_sampling * count)(*[N.mc_sampling(int(s), int(t)) for s, t in zip(seeds, streams)])
+    one = [c._sampling(s, t, p) for c, s, t, p in zip(contexts, seeds, streams, ps)]
+    smp = (N.mc_sampling * count)(*[N.mc_sampling(o.seed, o.stream, o.p) for o in one])
     failed = ctypes.c_int32(-1)
     L = lib()
     if torch is not None and torch.cuda.is_available():

@@ -24,7 +24,7 @@ class mc_motion(ctypes.Structure):
 
 
 class mc_sampling(ctypes.Structure):
-    _fields_ = [("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32)]
+    _fields_ = [("seed", ctypes.c_uint64), ("stream", ctypes.c_uint32), ("p", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes); every declaration of include/mc.h
@@ -66,7 +66,9 @@ SIGNATURES = {
     "mc_save_state": (_I32, [_VP, _VP, _U64]),
     "mc_load_state": (_I32, [_VP, _VP, _U64]),
     "mc_version": (ctypes.c_char_p, []),
+    "mc_measure_shared_load_peak": (_I32, [_I32, _VP]),
     "mc_forward_static": (_I32, [ctypes.POINTER(mc_geometry), _VP, _VP, _VP, _VP, ctypes.c_char_p, _I32]),
+    "mc_forward_static_status": (_I32, [_VP, ctypes.c_char_p, _I32]),
 }
 
 _lib = None

@@ -8,8 +8,11 @@ the bilinear sample at p + u_i(p).  Both run in libmc's kernels; there is no
 PyTorch fallback.
 
 The context holds one field per gate.  If the gate's field was replaced
-between forward and backward, backward puts the saved field back first, so a
-graph always differentiates the operator its forward applied.
+between forward and backward, backward puts the saved field back for its
+mc_vjp call and then restores the field that was current before, so a graph
+always differentiates the operator its forward applied and later users of the
+context see the field most recently set.  Each replacement rebuilds the gate's
+D_i^T and, as every mc_set_field does, drops the context's norms and step sizes.
 """
 from __future__ import annotations
 
@@ -44,7 +47,12 @@ class GateProjection(torch.autograd.Function):
         if not (need_x or need_f):
             return None, None, None, None
         if fctx.has_field and ctx.field_version(gate) != fctx.version:
+            now = ctx.current_field(gate)
             ctx.set_field(gate, field.detach())
-            fctx.version = ctx.field_version(gate)
+            try:
+                gx, gf = ctx.vjp(gate, x.detach(), gy.contiguous(), grad_x=need_x, grad_field=need_f)
+            finally:
+                ctx.set_field(gate, now)
+            return None, None, gx, gf
         gx, gf = ctx.vjp(gate, x.detach(), gy.contiguous(), grad_x=need_x, grad_field=need_f)
         return None, None, gx, gf

@@ -22,7 +22,8 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libmc.so")
 CHECKED_DIR = os.path.join(OUT_DIR, "checked")
 CHECKED_LIB = os.path.join(CHECKED_DIR, "libmc.so")
-SOURCES = ["k_warp.cu", "k_project.cu", "k_backproject.cu", "k_misc.cu", "mc_api.cu", "mc_static.cu"]
+SOURCES = ["k_warp.cu", "k_project.cu", "k_backproject.cu", "k_misc.cu", "k_peak.cu", "mc_api.cu",
+           "mc_static.cu"]
 HEADERS = ["mc_device.cuh", "mc_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -12,15 +12,26 @@ namespace {
 
 // One block.  kctr != null: k0 = *kctr and the counter advances by count
 // after every thread has read it (graph replays draw fresh gates).
+// thr == null: uniform, gate = floor(word0 * N / 2^32).  Otherwise serial
+// sampling with P(i) = p_i: gate = the first i with word0 < thr[i], where
+// thr[i] = floor(2^32 (p_0 + ... + p_i)) and thr[N-1] = 2^32.
 __global__ void k_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
-                             uint64_t k0_in, int count, int n_gates, int* out)
+                             uint64_t k0_in, int count, int n_gates, const unsigned long long* thr,
+                             int* out)
 {
     pdl_wait();
     pdl_trigger();
     const uint64_t k0 = kctr ? (uint64_t)*kctr : k0_in;
     for (int j = threadIdx.x; j < count; j += blockDim.x) {
         const uint32_t w = philox_word0(seed, stream, k0 + (uint64_t)j);
-        out[j] = (int)(((uint64_t)w * (uint64_t)n_gates) >> 32);
+        int g;
+        if (!thr) {
+            g = (int)(((uint64_t)w * (uint64_t)n_gates) >> 32);
+        } else {
+            g = 0;
+            while (g < n_gates - 1 && (unsigned long long)w >= thr[g]) ++g;
+        }
+        out[j] = g;
     }
     __syncthreads();
     if (kctr && threadIdx.x == 0) *kctr = (unsigned long long)(k0 + (uint64_t)count);
@@ -144,9 +155,11 @@ __global__ void k_fill_nan(double* p, int count)
 }  // namespace
 
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
-                              uint64_t k0, int count, int n_gates, int* out, cudaStream_t s)
+                              uint64_t k0, int count, int n_gates, const unsigned long long* thr, int* out,
+                              cudaStream_t s)
 {
-    return pdl_launch(k_draw_gates, dim3(1), dim3(256), 0, s, seed, stream, kctr, k0, count, n_gates, out);
+    return pdl_launch(k_draw_gates, dim3(1), dim3(256), 0, s, seed, stream, kctr, k0, count, n_gates, thr,
+                      out);
 }
 
 cudaError_t launch_pad_sino(const float* y, float2* dy, const BpAngle* ang, int na, int nb,

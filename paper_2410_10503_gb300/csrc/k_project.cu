@@ -58,22 +58,53 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
                  : "memory");
 }
 
+__device__ __forceinline__ bool mbar_try(uint32_t addr, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
 // Bounded wait on an mbarrier phase; false after `limit` failed polls.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit)
 {
     const uint32_t addr = smem_u32(bar);
+    for (uint32_t it = 0; it < limit; ++it)
+        if (mbar_try(addr, parity)) return true;
+    return false;
+}
+
+// The producer's wait for a free stage: bounded, and it also gives up as soon
+// as a consumer has raised the block's failure flag (the consumers that left
+// will never release the stage).
+__device__ __forceinline__ bool mbar_wait_or_flag(uint64_t* bar, uint32_t parity, uint32_t limit,
+                                                  const int* flag)
+{
+    const uint32_t addr = smem_u32(bar);
     for (uint32_t it = 0; it < limit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(addr), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(addr, parity)) return true;
+        if ((it & 63u) == 63u && *(const volatile int*)flag) return false;
     }
     return false;
+}
+
+// Before the producer leaves: every copy it issued has landed, so no bulk
+// copy is still writing into the block's shared memory when the block ends.
+// Copies g in [issued - kStages, issued) may still be in flight (older ones
+// were waited for by the consumers before the producer could reuse their
+// stage); each completes the phase g / stages of its stage's full barrier.
+// Bounded: a copy that never lands leaves after `limit` polls with the error
+// word already set.
+__device__ __forceinline__ void drain_copies(uint64_t* full, int issued, int stages, uint32_t limit)
+{
+    for (int g = max(0, issued - stages); g < issued; ++g)
+        mbar_wait(&full[g % stages], (uint32_t)((g / stages) & 1), limit);
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
@@ -258,21 +289,25 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     const uint32_t wlim = a.wait_limit ? a.wait_limit : kWaitLimit;
 
     // ---- producer warp: fill the ring, item after item ----------------------
+    // On a failure (its own wait for a free stage ran out, or a consumer raised
+    // the block's flag) the producer issues nothing more and waits for the
+    // copies it has in flight before it leaves.
     if (warp == kConsumers) {
         if (a.stall) return;          // test of the waits' failure path: no copies in flight
         if (lane == 0) {
+            int issued = 0;           // copies issued so far (ring position of the next one)
             if constexpr (BANDED) {
                 // running chunk count q over the items' bands
-                int q = 0;
                 bool stop = false;
                 for (int it = 0; it < n_it && !stop; ++it) {
                     const RayItem item = items[it0 + it];
                     const float2* src = (item.dir ? a.lcol : a.lrow) + slot * a.layout_stride;
                     const int cb0 = item.band * a.cpb, cb1 = min(nch, cb0 + a.cpb);
-                    for (int c = cb0; c < cb1; ++c, ++q) {
+                    for (int c = cb0; c < cb1; ++c) {
+                        const int q = issued;
                         const int st = q % kStages;
                         if (q >= kStages &&
-                            !mbar_wait(&empty[st], (uint32_t)((q / kStages - 1) & 1), wlim)) {
+                            !mbar_wait_or_flag(&empty[st], (uint32_t)((q / kStages - 1) & 1), wlim, s_flag)) {
                             atomicExch(s_flag, 1);
                             atomicExch(a.err, kErrTimeout);
                             stop = true;
@@ -281,6 +316,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                         if (*(volatile int*)s_flag) { stop = true; break; }
                         bulk_load(stage0 + st * stage_pairs, src + (size_t)c * stage_pairs,
                                   (uint32_t)(stage_pairs * sizeof(float2)), &full[st]);
+                        ++issued;
                     }
                 }
             } else {
@@ -289,7 +325,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                     const float2* src = (items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
                     const int st = g % kStages;
                     if (g >= kStages &&
-                        !mbar_wait(&empty[st], (uint32_t)((g / kStages - 1) & 1), wlim)) {
+                        !mbar_wait_or_flag(&empty[st], (uint32_t)((g / kStages - 1) & 1), wlim, s_flag)) {
                         atomicExch(s_flag, 1);
                         atomicExch(a.err, kErrTimeout);
                         break;
@@ -297,8 +333,10 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
                     if (*(volatile int*)s_flag) break;
                     bulk_load(stage0 + st * stage_pairs, src + (size_t)c * stage_pairs,
                               (uint32_t)(stage_pairs * sizeof(float2)), &full[st]);
+                    ++issued;
                 }
             }
+            drain_copies(full, issued, kStages, wlim);
         }
         // off the ring's critical path: prefetch the CSR the iteration's
         // transpose warp will read (a.pf_rowptr is set for one-slot SPDHG launches)
@@ -387,7 +425,11 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         for (int ch = cb0; ch < cb1; ++ch) {
             const int g = BANDED ? q_run++ : it * nch + ch;
             const int st = g % kStages;
-            if (!mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), wlim)) {
+            // one verdict per warp, so that all lanes leave or none does
+            if (!__all_sync(0xffffffffu, mbar_wait_or_flag(&full[st], (uint32_t)((g / kStages) & 1), wlim, s_flag))) {
+                // this wait ran out, or another warp's did: the producer sees
+                // the flag, stops issuing and drains the copies it has in
+                // flight before the block ends
                 atomicExch(s_flag, 1);
                 atomicExch(a.err, kErrTimeout);
                 return;

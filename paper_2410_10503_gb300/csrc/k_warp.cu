@@ -351,7 +351,8 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
         // (iii) z^{k+1} = z^k + v, zbar^{k+1} = z^{k+1} + (theta/p_i) v, then
         // (i) of the next iteration: x^{k+2} = (x^{k+1} - tau zbar^{k+1}) / (1 + 2 tau alpha)
         const float zn = z0 + v;
-        const float zbar = fmaf(a.coef, v, zn);
+        const float coef = a.coef_tab ? __ldg(a.coef_tab + sel_block(a.sel, 0)) : a.coef;
+        const float zbar = fmaf(coef, v, zn);
         a.z[q] = zn;
         a.x_out[q] = fmaf(-a.tau, zbar, x0) * a.prox_scale;
     } else {

@@ -59,7 +59,7 @@ void split_f19(double v, float& hi, float& lo)
     lo = (float)(v - h);
 }
 
-Steps make_steps(double norm2, double alpha, int N, int n_iter_per_epoch)
+Steps make_steps(double norm2, double alpha, int N, double n_iter_per_epoch)
 {
     // strongly convex PDHG/SPDHG steps: mu_g = 2 alpha, mu_f = N / 2
     Steps s;
@@ -154,6 +154,15 @@ struct mc_ctx {
     double* d_trace = nullptr;
     int trace_cap = 0;
 
+    // non-uniform serial sampling P(i) = p_i (mc_sampling.p): p normalised to
+    // sum 1 (empty: uniform), the draw's thresholds and theta / p_i per gate as
+    // uploaded (device tables allocated on first use)
+    std::vector<double> p_steps;      // p the step sizes and coefficients follow
+    std::vector<double> p_thr;        // p the uploaded thresholds follow
+    std::vector<float> coef_host;     // theta / p_i as uploaded
+    unsigned long long* d_thr = nullptr;
+    float* d_coef = nullptr;
+
     // steps
     bool have_norms = false;
     std::vector<double> norms2;
@@ -172,8 +181,10 @@ struct mc_ctx {
     bool graph_on = true, prof_on = false, trace_obj = false;
     bool test_stall = false;          // MC_OPT_TEST_STALL: the next forward launch's waits run out
 
-    // graphs: [0] SPDHG, [1] PDHG; index parity of cur at capture
-    cudaGraphExec_t gexec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    // graphs: [0] SPDHG, [1] PDHG; index parity of cur at capture; which of the
+    // two data buffers was current (commits swap d_d and d_stage)
+    cudaGraphExec_t gexec[2][2][2] = {};
+    int dsel = 0;
     uint64_t g_seed[2] = {0, 0};
     uint32_t g_stream[2] = {0, 0};
 
@@ -346,8 +357,9 @@ mc_status check_err_word(mc_ctx* c)
 void drop_graphs(mc_ctx* c)
 {
     for (auto& row : c->gexec)
-        for (auto& g : row)
-            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        for (auto& pair : row)
+            for (auto& g : pair)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
 }
 
 // ---- building blocks ------------------------------------------------------
@@ -446,8 +458,10 @@ mc_status adjoint_from_dy(mc_ctx* c, GateSel sel, int n_slots, float* out)
 mc_status enqueue_spdhg_epoch(mc_ctx* c, uint64_t seed, uint32_t stream)
 {
     const int N = c->N, nblk = N * c->S;     // blocks: gates, or gates x angle subsets
+    const bool nonuni = !c->p_steps.empty();
     TRY(launch(c, C_DRAW, "draw_gates", [&] {
-        return launch_draw_gates(seed, stream, c->d_k, 0, nblk, nblk, c->d_gates, c->stream);
+        return launch_draw_gates(seed, stream, c->d_k, 0, nblk, nblk, nonuni ? c->d_thr : nullptr, c->d_gates,
+                                 c->stream);
     }));
     const float sigma = (float)c->sS.sigma;
     const float inv_den = (float)(1.0 / (1.0 + c->sS.sigma * N / 2.0));
@@ -465,6 +479,7 @@ mc_status enqueue_spdhg_epoch(mc_ctx* c, uint64_t seed, uint32_t stream)
         WarpAdjArgs wa = wadj_args(c, sel, 1, c->d_b);
         wa.z = c->d_z; wa.x_in = xin; wa.x_out = xout;
         wa.coef = (float)(c->sS.theta * nblk);            // theta / p_j, p_j = 1/(N S)
+        wa.coef_tab = nonuni ? c->d_coef : nullptr;       // theta / p_i, non-uniform p
         wa.tau = (float)c->sS.tau;
         wa.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sS.tau * c->alpha));
         TRY(launch(c, C_WADJ, "warp_adjoint_update", [&] {
@@ -507,11 +522,14 @@ mc_status run_epoch(mc_ctx* c, int which, uint64_t seed, uint32_t stream)
     };
     const int flips = (which == 0) ? ((c->N * c->S) & 1) : 1;
     if (!c->graph_on || c->prof_on || c->test_stall) return enqueue();
-    const int par = c->cur;
-    if (which == 0 && c->gexec[0][par] && (c->g_seed[0] != seed || c->g_stream[0] != stream)) {
-        drop_graphs(c);
+    const int par = c->cur, ds = c->dsel;
+    if (which == 0 && (c->g_seed[0] != seed || c->g_stream[0] != stream)) {
+        bool any = false;
+        for (auto& pair : c->gexec[0])
+            for (auto& g : pair) any = any || g;
+        if (any) drop_graphs(c);
     }
-    if (!c->gexec[which][par]) {
+    if (!c->gexec[which][par][ds]) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         const mc_status st = enqueue();
@@ -523,10 +541,10 @@ mc_status run_epoch(mc_ctx* c, int which, uint64_t seed, uint32_t stream)
         const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (e2 != cudaSuccess) return fail(c, MC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
-        c->gexec[which][par] = ge;
+        c->gexec[which][par][ds] = ge;
         if (which == 0) { c->g_seed[0] = seed; c->g_stream[0] = stream; }
     }
-    CK(cudaGraphLaunch(c->gexec[which][par], c->stream));
+    CK(cudaGraphLaunch(c->gexec[which][par][ds], c->stream));
     c->cur ^= flips;
     return MC_OK;
 }
@@ -588,7 +606,11 @@ mc_status update_steps(mc_ctx* c)
         drop_graphs(c);
         return fail(c, MC_EINVAL, "operator norms must be positive");
     }
-    const Steps s = make_steps(mx, c->alpha, c->N, nblk);
+    // non-uniform p: the steps of the uniform rule with n = 1 / min_i p_i, so
+    // that omega tau sigma ||A_i||^2 = min_j p_j <= p_i for every gate
+    double n_eff = nblk;
+    if (!c->p_steps.empty()) n_eff = 1.0 / *std::min_element(c->p_steps.begin(), c->p_steps.end());
+    const Steps s = make_steps(mx, c->alpha, c->N, n_eff);
     const Steps p = make_steps(c->norms2[nblk], c->alpha, c->N, 1);
     // captured epochs bake the steps into their kernel arguments
     auto same = [](const Steps& a, const Steps& b) {
@@ -598,7 +620,69 @@ mc_status update_steps(mc_ctx* c)
     c->sS = s;
     c->sP = p;
     c->steps_ok = true;
+    if (!c->p_steps.empty()) {
+        // theta / p_i per gate, uploaded when it changed (the graphs read it
+        // at run time)
+        std::vector<float> cf(c->N);
+        for (int i = 0; i < c->N; ++i) cf[i] = (float)(s.theta / c->p_steps[i]);
+        if (cf != c->coef_host) {
+            if (!c->d_coef) TRY(dalloc(c, &c->d_coef, c->N));
+            c->coef_host = cf;
+            CK(cudaMemcpyAsync(c->d_coef, c->coef_host.data(), c->N * sizeof(float), cudaMemcpyHostToDevice,
+                               c->stream));
+        }
+    }
     return MC_OK;
+}
+
+// The sampling's p (normalised), or an empty vector for uniform sampling.
+mc_status read_p(mc_ctx* c, const mc_sampling* smp, std::vector<double>& p)
+{
+    p.clear();
+    if (!smp || !smp->p) return MC_OK;
+    if (c->S > 1) return fail(c, MC_EINVAL, "non-uniform sampling (p) is defined over gates only (subsets = 1)");
+    if (ptr_kind(c, smp->p) != 0) return fail(c, MC_EINVAL, "sampling p must be host memory");
+    double sum = 0.0;
+    for (int i = 0; i < c->N; ++i) {
+        const double v = smp->p[i];
+        if (!(v > 0.0) || !std::isfinite(v)) return fail(c, MC_EINVAL, "sampling p[%d] must be finite and > 0", i);
+        sum += v;                                   // in gate order
+    }
+    p.resize(c->N);
+    for (int i = 0; i < c->N; ++i) p[i] = smp->p[i] / sum;
+    return MC_OK;
+}
+
+// Upload the draw's thresholds for p (non-empty): thr[i] = floor(2^32 (p_0 + ... + p_i)),
+// the running sum taken in gate order, thr[N-1] = 2^32.
+mc_status set_thresholds(mc_ctx* c, const std::vector<double>& p)
+{
+    if (p.empty() || p == c->p_thr) return MC_OK;
+    if (!c->d_thr) TRY(dalloc(c, &c->d_thr, c->N));
+    std::vector<unsigned long long> th(c->N);
+    double cum = 0.0;
+    for (int i = 0; i < c->N; ++i) {
+        cum += p[i];
+        th[i] = (unsigned long long)std::floor(cum * 4294967296.0);
+    }
+    th[c->N - 1] = 4294967296ULL;
+    CK(cudaMemcpy(c->d_thr, th.data(), c->N * sizeof(unsigned long long), cudaMemcpyHostToDevice));
+    c->p_thr = p;
+    return MC_OK;
+}
+
+// Make the context follow the sampling of a run: thresholds, step sizes and
+// theta / p_i.  A change of p drops the captured epochs.
+mc_status apply_sampling(mc_ctx* c, const mc_sampling* smp)
+{
+    std::vector<double> p;
+    TRY(read_p(c, smp, p));
+    if (p == c->p_steps) return MC_OK;
+    TRY(set_thresholds(c, p));
+    c->p_steps = p;
+    c->coef_host.clear();
+    drop_graphs(c);
+    return update_steps(c);
 }
 
 // copy an input to device memory if it is a host pointer
@@ -1290,8 +1374,9 @@ mc_status mc_reset(mc_ctx* c)
 
 namespace {
 
-// the part of mc_set_data after d has been copied into d_d on the context's stream
-mc_status data_in_place(mc_ctx* c, double alpha)
+// the part of mc_set_data after d has been copied into d_d on the context's
+// stream; sync: wait for the stream (the caller's host array may be reused)
+mc_status data_in_place(mc_ctx* c, double alpha, bool sync)
 {
     const size_t cnt = (size_t)c->N * c->na * c->nb;
     if (c->store != 0)
@@ -1301,7 +1386,7 @@ mc_status data_in_place(mc_ctx* c, double alpha)
     c->have_ref = false;
     TRY(mc_reset(c));
     TRY(update_steps(c));
-    CK(cudaStreamSynchronize(c->stream));
+    if (sync) CK(cudaStreamSynchronize(c->stream));
     return finish(c);
 }
 
@@ -1315,7 +1400,7 @@ mc_status mc_set_data(mc_ctx* c, const float* d, double alpha)
     const size_t cnt = (size_t)c->N * c->na * c->nb;
     CK(cudaMemcpyAsync(c->d_d, d, cnt * sizeof(float),
                        ptr_kind(c, d) == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
-    return data_in_place(c, alpha);
+    return data_in_place(c, alpha, true);
 }
 
 mc_status mc_stage_data(mc_ctx* c, const float* d)
@@ -1347,12 +1432,16 @@ mc_status mc_commit_data(mc_ctx* c, double alpha)
     if (!c) return MC_EINVAL;
     if (!c->staged) return fail(c, MC_ESTATE, "no data staged (mc_stage_data)");
     if (!(alpha > 0) || !std::isfinite(alpha)) return fail(c, MC_EINVAL, "alpha must be finite and > 0");
-    const size_t cnt = (size_t)c->N * c->na * c->nb;
-    CK(cudaStreamWaitEvent(c->stream, c->stage_ev, 0));
-    CK(cudaMemcpyAsync(c->d_d, c->d_stage, cnt * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    // the caller's host array is free once the upload has landed; the staged
+    // buffer then becomes the data and the old data buffer the next staging
+    // buffer (no device copy).  commit_ev marks the end of the work enqueued so
+    // far, the last to read the old buffer: the next upload waits for it.
+    CK(cudaEventSynchronize(c->stage_ev));
     CK(cudaEventRecord(c->commit_ev, c->stream));
+    std::swap(c->d_d, c->d_stage);
+    c->dsel ^= 1;
     c->staged = false;
-    return data_in_place(c, alpha);
+    return data_in_place(c, alpha, false);
 }
 
 mc_status mc_forward(mc_ctx* c, int32_t gate, const float* x, float* out)
@@ -1583,6 +1672,8 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
     c->S = 1;
     c->s_bands = 1;
     c->have_norms = false;
+    c->p_steps.clear();               // block sampling is uniform; a later run's p is applied anew
+    c->coef_host.clear();
     if (subsets > 1) {
         // forward work items per angle subset, one table, subset s at soff[s];
         // with B = S / 2 line bands (at most 8) each subset's groups are cut
@@ -1875,6 +1966,7 @@ static mc_status run_common(mc_ctx* c, int which, int32_t epochs, const mc_sampl
         TRY(dalloc(c, &c->d_trace, 3 * (size_t)epochs));
         c->trace_cap = epochs;
     }
+    if (which == 0) TRY(apply_sampling(c, smp));
     const uint64_t seed = smp ? smp->seed : 0;
     const uint32_t strm = smp ? smp->stream : 0;
     for (int e = 0; e < epochs; ++e) {
@@ -1923,6 +2015,8 @@ mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
                         c->dev != dev ? "batch contexts must share one device"
                                       : "runs need mc_set_data and mc_norms/mc_set_norms first");
         }
+        const mc_status st = apply_sampling(c, &sampling[i]);
+        if (st != MC_OK) { if (failed) *failed = i; return st; }
     }
     // epoch by epoch, every slice in turn: each context's graph goes to its
     // own stream, so the slices' kernels overlap on the device
@@ -1963,8 +2057,12 @@ mc_status mc_draw_gates(mc_ctx* c, const mc_sampling* smp, uint64_t k0, int32_t 
         }
         o = c->d_draw_out;
     }
+    std::vector<double> p;
+    TRY(read_p(c, smp, p));
+    TRY(set_thresholds(c, p));
     TRY(launch(c, C_DRAW, "draw_gates", [&] {
-        return launch_draw_gates(smp->seed, smp->stream, nullptr, k0, count, c->N * c->S, o, c->stream);
+        return launch_draw_gates(smp->seed, smp->stream, nullptr, k0, count, c->N * c->S,
+                                 p.empty() ? nullptr : c->d_thr, o, c->stream);
     }));
     if (!dev) {
         CK(cudaMemcpyAsync(out, o, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost, c->stream));

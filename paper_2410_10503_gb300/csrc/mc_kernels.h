@@ -81,7 +81,8 @@ struct WarpAdjArgs {
     float* z;
     const float* x_in;
     float* x_out;
-    float coef;                // theta / p_i
+    float coef;                // theta / p_i (uniform sampling)
+    const float* coef_tab;     // non-null: theta / p_i per gate, read for the slot's block
     float tau;
     float prox_scale;          // 1 / (1 + 2 tau alpha)
 };
@@ -157,8 +158,10 @@ cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
 cudaError_t backproject_prepare();
 
 // ---- misc -------------------------------------------------------------------
+// thr: null for uniform sampling, else N cumulative thresholds (see k_draw_gates)
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
-                              uint64_t k0, int count, int n_gates, int* out, cudaStream_t s);
+                              uint64_t k0, int count, int n_gates, const unsigned long long* thr, int* out,
+                              cudaStream_t s);
 // write a na x nb sinogram into the padded, m_k-scaled pair layout of dy
 // (guards stay zero)
 cudaError_t launch_pad_sino(const float* y, float2* dy, const BpAngle* ang, int na, int nb,

@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -128,23 +129,37 @@ __global__ void k_static_tables(int n, int na, int nb, int lc, int gpi, int item
     }
 }
 
-// Per-device set-up, once per device under the lock: the device address of
-// the scratch array (the host-side symbol is only a stand-in and must never
-// reach a kernel) and the forward kernels' shared-memory attribute.
-mc_status device_setup(int dev, void** ptr, int* sms, char* err, int cap)
+// Per-device set-up under the lock: the device address of the scratch array
+// (the host-side symbol is only a stand-in and must never reach a kernel) and,
+// once per device, the forward kernels' shared-memory attribute.  The address
+// is looked up again on every call made outside stream capture (a cheap
+// query that allocates nothing), so a device or primary-context reset by the
+// host application cannot leave a stale pointer behind; inside a capture the
+// address of the last call made outside one is used.
+mc_status device_setup(int dev, bool capturing, void** ptr, int* sms, char* err, int cap)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     if (dev < 0 || dev >= kMaxDevices) {
         set_msg(err, cap, "device %d beyond the %d devices this entry point tracks", dev, kMaxDevices);
         return MC_EDEVICE;
     }
-    if (!g_ptr[dev]) {
+    if (capturing && !g_ptr[dev]) {
+        set_msg(err, cap, "the first call on a device must come before any stream capture");
+        return MC_ESTATE;
+    }
+    if (!capturing) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) {
+            cudaGetLastError();
             set_msg(err, cap, "cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
             return MC_ECUDA;
         }
+        if (p != g_ptr[dev]) g_sms[dev] = 0;     // new context: attributes again
+        g_ptr[dev] = p;
+    }
+    if (!g_sms[dev]) {
+        cudaError_t e;
         int optin = 0;
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
         e = forward_prepare(optin - forward_static_smem());
@@ -155,11 +170,19 @@ mc_status device_setup(int dev, void** ptr, int* sms, char* err, int cap)
         int s = 0;
         cudaDeviceGetAttribute(&s, cudaDevAttrMultiProcessorCount, dev);
         g_sms[dev] = s > 0 ? s : 1;
-        g_ptr[dev] = p;
     }
     *ptr = g_ptr[dev];
     *sms = g_sms[dev];
     return MC_OK;
+}
+
+// MC_STATIC_TEST_STALL=1 in the environment (read at every call) makes the
+// projection's waits run out, so that tests can check that the failure is
+// reported by mc_forward_static_status.
+bool stall_requested()
+{
+    const char* v = std::getenv("MC_STATIC_TEST_STALL");
+    return v && v[0] == '1';
 }
 
 bool on_device(const void* p, int dev)
@@ -202,9 +225,16 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
         set_msg(err, err_cap, "x and out must be device memory of the current device");
         return MC_EINVAL;
     }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap_st) != cudaSuccess) {
+        cudaGetLastError();
+        set_msg(err, err_cap, "invalid stream");
+        return MC_EINVAL;
+    }
     void* base = nullptr;
     int sms = 1;
-    mc_status st = device_setup(dev, &base, &sms, err, err_cap);
+    mc_status st = device_setup(dev, cap_st != cudaStreamCaptureStatusNone, &base, &sms, err, err_cap);
     if (st != MC_OK) return st;
 
     // sizes: same line pitch and chunking as the context path; items of at
@@ -234,7 +264,6 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     }
 
     unsigned char* b = static_cast<unsigned char*>(base);
-    cudaStream_t s = (cudaStream_t)cuda_stream;
     int* d_err = reinterpret_cast<int*>(b + L.err);
     RigidGate* d_rg = reinterpret_cast<RigidGate*>(b + L.rigid);
     FwdAngle* d_ang = reinterpret_cast<FwdAngle*>(b + L.ang);
@@ -266,10 +295,60 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     f.ang = d_ang; f.groups = d_groups; f.items = d_items; f.n_items = n_items;
     f.ipb = ipb; f.rpt = rpt; f.lc = lc; f.n = n; f.na = na; f.nb = nb;
     f.sel = GateSel{nullptr, 0}; f.n_slots = 1; f.mode = 0; f.out = out; f.err = d_err;
+    if (stall_requested()) {
+        // test hook of the failure path: the producer issues no copies and the
+        // consumers' waits run out after 2^12 polls, setting the error word
+        f.stall = 1;
+        f.wait_limit = 1u << 12;
+    }
     if (e == cudaSuccess) e = launch_forward(f, s);
     if (e != cudaSuccess) {
         set_msg(err, err_cap, "kernel launch failed: %s", cudaGetErrorString(e));
         return MC_ECUDA;
+    }
+    return MC_OK;
+}
+
+extern "C" mc_status mc_forward_static_status(void* cuda_stream, char* err, int32_t err_cap)
+{
+    if (err && err_cap > 0) err[0] = '\0';
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        set_msg(err, err_cap, "no CUDA device");
+        return MC_EDEVICE;
+    }
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (dev >= 0 && dev < kMaxDevices) base = g_ptr[dev];
+    }
+    if (!base) {
+        set_msg(err, err_cap, "mc_forward_static has not run on device %d", dev);
+        return MC_ESTATE;
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap_st) != cudaSuccess || cap_st != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        set_msg(err, err_cap, "the status is read outside stream capture, on a valid stream");
+        return MC_EINVAL;
+    }
+    // the error word sits at the start of the scratch array
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, base, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        set_msg(err, err_cap, "reading the error word failed: %s", cudaGetErrorString(e));
+        return MC_ECUDA;
+    }
+    if (h == kErrTimeout) {
+        set_msg(err, err_cap, "a device-side wait of the projection ran out of polls; out is incomplete");
+        return MC_ETIMEOUT;
+    }
+    if (h != kErrNone) {
+        set_msg(err, err_cap, "device error word %d (out-of-bounds sample); out is incomplete", h);
+        return MC_EDEVICE;
     }
     return MC_OK;
 }

@@ -238,3 +238,27 @@ def test_backward_restores_the_forward_field(mc):
                        O.Problem(P.geom, O.Motion(fields=F[None]), np.zeros(1), 1.0), 0)
         ref = O.warp_field_vjp(x.cpu().numpy(), O.At(r, P.geom), F, n)
         assert rel_l2(f.grad.cpu().numpy(), ref) <= 1e-4
+
+
+def test_backward_through_an_older_field_leaves_the_newest_in_place(mc):
+    """Backward of a graph whose field has since been replaced uses that
+    graph's field for its gradient, then puts the newest field back: a later
+    forward of the gate outside autograd applies the field set last."""
+    W = S.WORKLOADS["rbf256"].scaled(**SMALL)
+    P, _ = field_problem(W)
+    n = W.n
+    ctx = mc.Context(n, W.n_angles, W.n_bins, W.n_gates, fields=P.motion.fields)
+    F1 = S.rbf_fields(n, W.n_gates, 4343, W.rbf_count, W.rbf_width, W.rbf_max_disp)
+    x = torch.tensor(S.random_image(n, 5), dtype=torch.float32, device="cuda")
+    f0 = torch.tensor(P.motion.fields[0], device="cuda", requires_grad=True)
+    l0 = (mc.project_gate(ctx, 0, x, f0) ** 2).sum()          # graph on the first field
+    ctx.set_field(0, torch.tensor(F1[0], device="cuda"))       # replaced outside autograd
+    l0.backward()
+    x64 = x.cpu().numpy().astype(np.float64)
+    r = 2.0 * O.Ai(x64, O.Problem(P.geom, O.Motion(fields=P.motion.fields[:1]), np.zeros(1), 1.0), 0)
+    ref = O.warp_field_vjp(x.cpu().numpy(), O.At(r, P.geom), P.motion.fields[0], n)
+    assert rel_l2(f0.grad.cpu().numpy(), ref) <= 1e-4
+    y_now = ctx.forward(0, x).cpu().numpy()
+    y_ref = O.Ai(x64, O.Problem(P.geom, O.Motion(fields=F1[:1]), np.zeros(1), 1.0), 0)
+    assert rel_l2(y_now, y_ref) <= 1e-5
+    ctx.close()

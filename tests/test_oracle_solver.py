@@ -188,3 +188,50 @@ def test_theorem_kappas():
     nrm = np.array([2.0, 3.0, 2.5, 10.0])
     kS, kP = O.theorem_kappas(nrm, 0.5, 3)
     assert kS == 3.0 / 1.5 and kP == 10.0 / 1.5
+
+
+def test_spdhg_nonuniform_sampling_reaches_xstar(small70):
+    """Serial sampling with P(i) = p_i (Algorithm 1 step (ii)): the increment
+    weighted by theta/p_i and steps of the uniform rule with n = 1/min p_i
+    (omega tau sigma ||A_i||^2 = min p <= p_i) still reach x* and y*; the
+    draw follows p."""
+    P, xs, ys, nrm = small70
+    N = P.N
+    p = np.array([0.4, 0.3, 0.2, 0.1])
+    st = O.step_sizes(nrm[:N].max(), P.alpha, N, 1.0 / p.min())
+    assert abs(st.omega * st.tau * st.sigma[0] * nrm[:N].max() - p.min()) < 1e-12
+    r = O.spdhg(P, 260, st, seed=11, p=p, x_star=xs, y_star=ys)
+    assert r.trace[-1][0] < 1e-9
+    assert np.linalg.norm(r.y - ys) <= 1e-7 * np.linalg.norm(ys)
+    freq = np.bincount(r.gates, minlength=N) / len(r.gates)
+    np.testing.assert_allclose(freq, p, atol=0.04)
+
+
+def test_make_problem_noise_scale():
+    """d_i - A_i x_true = eps_i with eps_i ~ N(0, sigma^2 / N) i.i.d. per bin
+    and sigma = 1% of the largest clean value over ALL gates and bins
+    (Sec. II-A; the variance sigma^2/N of the configurations).  Each gate's
+    empirical variance must match sigma^2/N within a 5-sigma chi^2 bound; the
+    gates' own maxima differ by far more than that bound, so a per-gate
+    maximum, or sigma in place of sigma/sqrt(N), fails."""
+    n, na, nb, N = 32, 60, 47, 4
+    g = O.Geometry(n, na, nb)
+    rig = np.array([[0.0, 0.0, 0.0], [0.1, 9.0, 0.0], [-0.2, -10.0, 6.0], [0.05, 0.0, -11.0]])
+    m = O.Motion(rigid=rig)
+    xt = np.zeros((n, n))
+    xt[4:12, 20:28] = 1.0          # bright block near one edge: shifts cut it differently
+    xt[16:30, 4:18] = 0.3
+    eps = S.noise(N, na, nb, seed=77)
+    P = O.make_problem(g, m, xt, eps, alpha=1.0, noise_level=0.01)
+    clean = np.stack([O.A(O.D(xt, m, i, n), g) for i in range(N)])
+    sigma = 0.01 * clean.max()
+    var_expected = sigma ** 2 / N
+    M = na * nb
+    bound = 5.0 * math.sqrt(2.0 / M)
+    per_gate_max = clean.reshape(N, -1).max(axis=1)
+    # the pin discriminates: per-gate maxima differ from the global one
+    assert per_gate_max.min() < (1.0 - 4 * bound) * per_gate_max.max()
+    for i in range(N):
+        r = (P.d[i] - clean[i]).ravel()
+        v = float(np.mean(r * r))
+        assert abs(v / var_expected - 1.0) <= bound, (i, v / var_expected)

@@ -7,9 +7,12 @@ pool); this entry point keeps all of its scratch in a fixed array built into
 the library.  Two calls in a row (different geometry and motion) must both
 match the existing entry points, which checks that the shared scratch is
 reset between calls; sizes beyond the fixed array are refused on the host.
-This file is collected last on purpose.
+The entry point is also checked on its own against the FP64 oracle of A D
+(Sec. II-A), and its companion mc_forward_static_status must report a
+device-side wait that ran out.  This file is collected last on purpose.
 """
 import ctypes
+import os
 
 import numpy as np
 import pytest
@@ -88,3 +91,51 @@ def test_static_forward_refuses_oversize_and_host_arrays(mc):
     st = mc.lib().mc_forward_static(ctypes.byref(geom), None, xh.ctypes.data, out.data_ptr(), None,
                                     err, len(err))
     assert st == -1 and "device memory" in err.value.decode()
+
+
+def status(mc):
+    from paper_2410_10503_gb300 import _native as N  # noqa: F401
+    err = ctypes.create_string_buffer(256)
+    st = mc.lib().mc_forward_static_status(torch.cuda.current_stream().cuda_stream, err, len(err))
+    return st, err.value.decode()
+
+
+def test_static_forward_matches_oracle(mc):
+    """A D x of the FP64 oracle (rigid motion and none), independent of the
+    context path; <= 1e-5 relative L2 as for every float32 operator."""
+    import oracle as O
+    n, na, nb = 48, 60, 53
+    g = O.Geometry(n, na, nb)
+    rig = S.rigid_motion(3, 7.0, 4.0, 31)
+    xh = S.random_image(n, 32)
+    x = torch.as_tensor(xh, dtype=torch.float32, device="cuda")
+    for rigid in (rig[2], None):
+        st, msg, out = call_static(mc, n, na, nb, rigid, x)
+        assert st == 0, msg
+        x64 = x.cpu().numpy().astype(np.float64)
+        ref = O.A(x64, g) if rigid is None else O.Ai(x64, O.Problem(g, O.Motion(rigid=rig), None, 1.0), 2)
+        assert rel_l2(out.cpu().numpy(), ref) <= TOL
+        assert status(mc) == (0, "")
+
+
+def test_static_status_reports_a_wait_that_ran_out(mc):
+    """With the test hook the projection's waits run out: the call itself
+    returns MC_OK (the failure happens on the device), the status call
+    reports MC_ETIMEOUT, and the next call without the hook is correct
+    again."""
+    n, na, nb = 64, 60, 64
+    ctx = mc.Context(n, na, nb, 1, rigid=np.zeros((1, 3)))
+    x = torch.as_tensor(S.phantom(n, 6, 5, 3.0, 16.0), dtype=torch.float32, device="cuda")
+    os.environ["MC_STATIC_TEST_STALL"] = "1"
+    try:
+        st, msg, _ = call_static(mc, n, na, nb, None, x)
+        assert st == 0, msg
+        st, msg = status(mc)
+        assert st == -4 and "ran out" in msg
+    finally:
+        del os.environ["MC_STATIC_TEST_STALL"]
+    st, msg, out = call_static(mc, n, na, nb, None, x)
+    assert st == 0, msg
+    assert status(mc) == (0, "")
+    assert rel_l2(out.cpu().numpy(), ctx.project(x).cpu().numpy()) <= TOL
+    ctx.close()
