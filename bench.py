@@ -312,11 +312,13 @@ def run_ours(args, W):
         "hbm_peak_gbs_measured": hbm_peak, "wall_s": round(wall, 3),
     }
     if args.convergence_epochs > 0:
-        out["time_to_1e-3"] = convergence_legs(ctx, stream, d, W, norms, sd, args.convergence_epochs)
+        out["time_to_1e-3"] = convergence_legs(ctx, stream, d, W, norms, sd, args.convergence_epochs,
+                                               args.alpha_epochs)
     if args.storage_epochs > 0:
         out["storage_rbf512"] = storage_legs(args.storage_epochs)
     if args.batch_slices > 0:
-        out["batch_mixed_slices"] = batch_legs(args.batch_slices, args.batch_epochs)
+        out["batch_mixed_slices"] = batch_legs(args.batch_slices, args.batch_epochs, args.batch_seq_epochs,
+                                               not args.batch_no_autotune)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
         out["cpu_baseline_more"] = cpu_baseline_more(W)
@@ -357,57 +359,76 @@ def run_ncu_case(args, W):
     print(json.dumps({"ncu_case": W.name, "subsets": args.subsets, "epochs": args.warmup + args.steps}))
 
 
-def time_to_tol(ctx, stream, which, tol, max_epochs, seed, graph=True):
+def time_to_tol(ctx, stream, which, tol, max_epochs, seed, graph=True, chunk=1):
     """Epochs (SPDHG: N iterations; PDHG: 1 iteration) from a zero start until
-    ||x - x*|| / ||x*|| <= tol, timed with CUDA events per epoch (trace
-    reductions included); returns a dict with epochs (None if not reached),
-    seconds to the crossing (or to max_epochs) and the last relative error."""
+    ||x - x*|| / ||x*|| <= tol, timed with CUDA events (trace reductions
+    included); returns a dict with epochs (None if not reached), seconds to the
+    crossing (or to max_epochs) and the last relative error.  Epochs run in
+    calls of `chunk` epochs, each timed by its own events; the crossing's time
+    is the chunks before it plus the crossing chunk's time prorated to the
+    crossing epoch (epochs of one run cost the same), exact for chunk = 1."""
     import torch
     ctx.reset()
     ctx.set_option(1, 1 if graph else 0)
     tot = 0.0
     rel = float("nan")
+    done = 0
     with torch.cuda.stream(stream):
-        for e in range(1, max_epochs + 1):
+        while done < max_epochs:
+            m = min(chunk, max_epochs - done)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
             if which == "spdhg":
-                _, tr = ctx.spdhg_run(1, seed=seed, x_out=False, trace=True)
+                _, tr = ctx.spdhg_run(m, seed=seed, x_out=False, trace=True)
             else:
-                _, tr = ctx.pdhg_run(1, x_out=False, trace=True)
+                _, tr = ctx.pdhg_run(m, x_out=False, trace=True)
             b.record(stream)
             b.synchronize()
-            tot += a.elapsed_time(b) / 1e3
-            rel = float(tr[0, 0])
-            if rel <= tol:
+            t = a.elapsed_time(b) / 1e3
+            hit = np.nonzero(tr[:, 0] <= tol)[0]
+            if len(hit):
+                e = int(hit[0]) + 1
                 ctx.set_option(1, 1)
-                return {"epochs": e, "seconds": round(tot, 6), "rel_err": rel}
+                return {"epochs": done + e, "seconds": round(tot + t * e / m, 6), "rel_err": float(tr[e - 1, 0])}
+            tot += t
+            done += m
+            rel = float(tr[-1, 0])
     ctx.set_option(1, 1)
     return {"epochs": None, "seconds_for_max_epochs": round(tot, 6), "max_epochs": max_epochs,
             "rel_err": rel}
 
 
-def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs):
+def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs, alpha_epochs):
     """Time to 1e-3 relative distance to x* for graph-replayed SPDHG, SPDHG
     with plain launches and PDHG, in the paper's regime (alpha such that
-    ||A||^2 / alpha = 70, Sec. III) and at the workload's own alpha; in the
-    paper's regime also SPDHG over gates x S angle subsets, S = 2, 4, 8."""
+    ||A||^2 / alpha = 70, Sec. III; at most max_epochs, timed epoch by epoch)
+    and at the workload's own alpha (at most alpha_epochs, timed in chunks of
+    100 epochs); in the paper's regime also SPDHG over gates x S angle
+    subsets, S = 2, 4, 8.  x* by float32 CG to a relative residual of 1e-6
+    (paper regime) or 1e-9 (the workload's alpha, where the normal operator's
+    condition number is ~3.5e7)."""
     import torch
     out = {}
     nA = float(np.max(norms[:W.n_gates]))
-    for label, alpha, cg_iters in [("paper_regime_kappa70", nA / 70.0, 400), ("workload_alpha", W.alpha, 300)]:
+    for label, alpha, cg_iters, cg_tol, cap, chunk in [
+            ("paper_regime_kappa70", nA / 70.0, 400, 1e-6, max_epochs, 1),
+            ("workload_alpha", W.alpha, 2000, 1e-9, alpha_epochs, 100)]:
+        if cap <= 0:
+            continue
         ctx.set_data(d, alpha)
         ctx.set_norms(norms)
         x_star = torch.empty((W.n, W.n), dtype=torch.float32, device="cuda")
-        _, iters, rel = ctx.solve_normal(max_iter=cg_iters, tol=1e-6, x_out=x_star)
+        _, iters, rel = ctx.solve_normal(max_iter=cg_iters, tol=cg_tol, x_out=x_star)
         ctx.set_reference(x_star)
         leg = {"alpha": alpha, "kappa": nA / alpha,
                "kappa_spdhg": ctx.steps()["kappa"], "kappa_pdhg": ctx.steps(pdhg=True)["kappa"],
-               "x_star_cg": {"iterations": iters, "rel_residual": rel}}
-        leg["spdhg_graph"] = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], True)
-        leg["spdhg_plain"] = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], False)
-        leg["pdhg_graph"] = time_to_tol(ctx, stream, "pdhg", 1e-3, max_epochs, sd["gates"], True)
+               "x_star_cg": {"iterations": iters, "rel_residual": rel},
+               "rate_bound_per_epoch": {"spdhg": _rate(ctx.steps()["kappa"], W.n_gates),
+                                        "pdhg": _rate(ctx.steps(pdhg=True)["kappa"], 1)}}
+        leg["spdhg_graph"] = time_to_tol(ctx, stream, "spdhg", 1e-3, cap, sd["gates"], True, chunk)
+        leg["spdhg_plain"] = time_to_tol(ctx, stream, "spdhg", 1e-3, cap, sd["gates"], False, chunk)
+        leg["pdhg_graph"] = time_to_tol(ctx, stream, "pdhg", 1e-3, cap, sd["gates"], True, chunk)
         if label == "paper_regime_kappa70":
             # sampling over gates x angle subsets (Sec. IV): same objective and x*,
             # blocks of 1/S of the angles, N S iterations per epoch
@@ -425,6 +446,12 @@ def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs):
     ctx.set_data(d, W.alpha)
     ctx.set_norms(norms)
     return out
+
+
+def _rate(kappa, n):
+    """l(kappa, n) = (1 - 2 n^-1 (1 + sqrt(1 + kappa))^-1)^n, the Theorem's
+    per-epoch contraction (Sec. II-B)."""
+    return (1.0 - 2.0 / (n * (1.0 + math.sqrt(1.0 + kappa)))) ** n
 
 
 def storage_legs(max_epochs, steps=20):
@@ -483,16 +510,21 @@ def storage_legs(max_epochs, steps=20):
     return out
 
 
-def batch_legs(count, epochs):
-    """Independent slices of mixed size (mc_synth.slice_batch: sides 256-1024,
-    angles 1.4 side, bins side + 17, 4-32 gates, rigid and dense-field
-    motion), each in its own context with autotuned launch shapes: `epochs`
-    SPDHG epochs per slice run one slice after another (graph replay) and as
-    one batched run (mc_batch_spdhg_run, all slices' streams at once);
-    throughput in A_i + A_i^* pairs per second of the whole batch."""
+def batch_legs(count, epochs, seq_epochs, autotune=True):
+    """The batched-slices workload: `count` independent slices of mixed size
+    (mc_synth.slice_batch: sides 256-1024, angles round(1.4 side), bins
+    side + 17, gates U{4..32}, rigid and dense-field motion alternating;
+    data A_i x + 1% noise), each in its own context with autotuned launch
+    shapes.  Timed: `epochs` SPDHG epochs of every slice as merged batched
+    iterations (mc_batch_run: one launch per stage over all slices in flight,
+    graph-replayed), and the same slices one after another through their own
+    epoch graphs (mc_spdhg_run, `seq_epochs` epochs each: the same
+    iterations, so pairs/s compare directly); throughput in A_i + A_i^* pairs
+    per second of the whole batch."""
     import torch
 
     import paper_2410_10503_gb300 as mc
+    t_setup = time.perf_counter()
     ws = S.slice_batch(count)
     ctxs, seeds, tunes = [], [], []
     for W in ws:
@@ -509,29 +541,46 @@ def batch_legs(count, epochs):
         for i in range(W.n_gates):
             ctx.forward(i, xt, out=d[i])
         torch.cuda.synchronize()
+        sigma = W.noise_level * float(d.max())
+        g = torch.Generator(device="cuda").manual_seed(sd["noise"])
+        d += torch.randn(d.shape, generator=g, device="cuda") * (sigma / math.sqrt(W.n_gates))
         ctx.set_data(d, W.alpha)
         ctx.set_norms(ctx.norms(max_iter=12, tol=1e-4) * 1.05)
-        tunes.append(ctx.autotune(reps=3))
+        if autotune:
+            tunes.append(ctx.autotune(reps=2))
         ctxs.append(ctx)
         seeds.append(sd["gates"])
+        del d, xt
+    setup_s = time.perf_counter() - t_setup
     pairs = epochs * sum(W.n_gates for W in ws)
-    for c, sdg in zip(ctxs, seeds):                 # capture every slice's epoch graph
+    batch = mc.Batch(ctxs)
+    batch.run(1, seeds)                              # captures every phase's graphs
+    for c, sdg in zip(ctxs, seeds):                  # and every slice's own epoch graph
         c.spdhg_run(1, seed=sdg, x_out=False)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    batch.run(epochs, seeds)
+    bat_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
     for c, sdg in zip(ctxs, seeds):
-        c.spdhg_run(epochs, seed=sdg, x_out=False)
+        c.spdhg_run(seq_epochs, seed=sdg, x_out=False)
         c.stream.synchronize()
     seq_s = time.perf_counter() - t0
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    mc.batch_spdhg_run(ctxs, epochs, seeds)
-    bat_s = time.perf_counter() - t0
-    out = {"slices": [f"{W.n}^2 {W.n_angles}x{W.n_bins} N={W.n_gates} {W.motion}" for W in ws],
+    seq_pairs = seq_epochs * sum(W.n_gates for W in ws)
+    sizes = sorted({W.n for W in ws})
+    out = {"workload": f"{count} slices, sides {sizes} (angles round(1.4 side), bins side + 17), gates U{{4..32}} "
+                       f"(total {sum(W.n_gates for W in ws)}), rigid and dense-field motion alternating, "
+                       f"alpha 1e-3, 1% noise",
            "epochs_per_slice": epochs, "pairs": pairs,
-           "one_after_another_pairs_per_s": round(pairs / seq_s, 1),
-           "batched_pairs_per_s": round(pairs / bat_s, 1),
-           "autotuned": tunes}
+           "batched_merged": {"seconds": round(bat_s, 3), "pairs_per_s": round(pairs / bat_s, 1),
+                              "launches_per_batched_iteration": "draw + warp + forward per lines-per-chunk "
+                                                                "class + backprojection per rows-per-thread "
+                                                                "class + transpose warp, over all slices in flight"},
+           "one_after_another": {"epochs_per_slice": seq_epochs, "seconds": round(seq_s, 3),
+                                 "pairs_per_s": round(seq_pairs / seq_s, 1)},
+           "setup_s": round(setup_s, 1), "autotuned": bool(autotune)}
+    out["speedup_merged_over_one_after_another"] = round((pairs / bat_s) / (seq_pairs / seq_s), 3)
+    batch.close()
     for c in ctxs:
         c.close()
     return out
@@ -716,11 +765,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--convergence-epochs", type=int, default=100,
                     help="epoch cap of the time-to-1e-3 legs (0 skips them)")
+    ap.add_argument("--alpha-epochs", type=int, default=60000,
+                    help="epoch cap of the time-to-1e-3 legs at the workload's own alpha (0: skip)")
     ap.add_argument("--storage-epochs", type=int, default=100,
                     help="epoch cap of the rbf512 float32/binary16/bfloat16 storage legs (0 skips)")
-    ap.add_argument("--batch-slices", type=int, default=10,
+    ap.add_argument("--batch-slices", type=int, default=64,
                     help="independent mixed-size slices of the batched leg (0 skips)")
-    ap.add_argument("--batch-epochs", type=int, default=3)
+    ap.add_argument("--batch-epochs", type=int, default=100)
+    ap.add_argument("--batch-seq-epochs", type=int, default=10,
+                    help="epochs per slice of the one-after-another comparison (a bounded sample)")
+    ap.add_argument("--batch-no-autotune", action="store_true")
     ap.add_argument("--l1-peak-gbs", type=float, default=152 * 128 * 2.07)
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling driver: set up the workload, then only warm-up + timed "

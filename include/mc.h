@@ -292,9 +292,11 @@ mc_status mc_spdhg_run(mc_ctx* ctx, int32_t epochs, const mc_sampling* sampling,
                        float* x_out, double* trace);
 
 /* Many independent slices (one context each, e.g. different sizes, gate
- * counts and motion kinds): run `epochs` SPDHG epochs on every context,
- * enqueuing epoch e of every slice before epoch e + 1 of any, each on its
- * own context stream, so small slices' launches overlap with large ones.
+ * counts and motion kinds), without a batch object: run `epochs` SPDHG epochs
+ * on every context, enqueuing epoch e of every slice (its own epoch graph)
+ * before epoch e + 1 of any, each on its own context stream, so small slices'
+ * launches overlap with large ones (mc_batch_run instead merges the slices'
+ * launches).
  * Per context the result equals `epochs` calls of mc_spdhg_run with
  * sampling[i] (same gate draws, same iterates).  sampling: count entries.
  * All contexts must live on one device and have data and step sizes.
@@ -303,6 +305,43 @@ mc_status mc_spdhg_run(mc_ctx* ctx, int32_t epochs, const mc_sampling* sampling,
  * mc_last_error holds the message. */
 mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
                              const mc_sampling* sampling, int32_t* failed);
+
+/* Batched SPDHG over many independent slices in ONE launch per stage.
+ *
+ * SPDHG's cost per iteration does not grow with N (Sec. II-A), so a slice's
+ * iteration is a few small launches; slices of uneven sizes and gate counts
+ * (each its own context: geometry, gates, motion kind) are therefore advanced
+ * together.  One batched iteration runs one SPDHG iteration (Algorithm 1) of
+ * every slice still in flight as five stages, each ONE launch over the blocks
+ * of all those slices: the gate draw (each slice's Philox counter and epoch
+ * position on the device), the warp D_i, the Joseph forward with the fused
+ * dual update, the backprojection and the transpose warp with the fused
+ * z / zbar / prox update.  The forward and the backprojection are compiled
+ * per launch shape, so slices with different lines per chunk or rows per
+ * thread (mc_autotune) add one launch of that stage per distinct shape.
+ * Block lists put the slices with the most work per block first.  Each
+ * batched iteration is captured once as a CUDA graph per set of slices in
+ * flight and parity of the iteration index, and replayed.
+ *
+ * mc_batch_create groups `count` contexts (same device, angle subsets = 1),
+ * orders work on cuda_stream (NULL: a stream of the batch's own) and keeps
+ * pointers to the contexts: destroy the batch before any of them.
+ * mc_batch_run runs `epochs` SPDHG epochs of every slice (slice i: epochs x
+ * N_i iterations, sampling[i] as in mc_spdhg_run, p included); slices with
+ * fewer gates finish first and leave the launches.  Per slice the result is
+ * bit-identical to mc_spdhg_run(ctx_i, epochs, &sampling[i], ...) from the
+ * same state (same draws, same arithmetic), and the contexts' iterates,
+ * iteration counters and duals continue from there.  The call waits for each
+ * context's pending work first and returns when the batch has finished (every
+ * slice's error word checked).  On failure *failed (nullable) is the slice
+ * index, mc_batch_last_error(b) holds the message.  Errors: MC_EINVAL,
+ * MC_ESTATE (a slice without data or step sizes), MC_ENOMEM, MC_ECUDA,
+ * MC_ETIMEOUT. */
+typedef struct mc_batch mc_batch;
+mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream, mc_batch** out);
+mc_status mc_batch_run(mc_batch* b, int32_t epochs, const mc_sampling* sampling, int32_t* failed);
+const char* mc_batch_last_error(const mc_batch* b);
+void mc_batch_destroy(mc_batch* b);
 
 /* Run `epochs` iterations of PDHG (p_i = 1, every gate each iteration,
  * zbar^{k+1} = z^{k+1} + theta sum_i A_i^*(y_i^{k+1} - y_i^k)), continuing from

@@ -23,7 +23,7 @@ import numpy as np
 
 from . import _native as N
 
-__all__ = ["Context", "MCError", "lib", "version", "project_gate", "batch_spdhg_run"]
+__all__ = ["Context", "Batch", "MCError", "lib", "version", "project_gate", "batch_spdhg_run", "shared_load_peak"]
 
 try:  # torch is plumbing here (device memory, streams); optional for host arrays
     import torch
@@ -460,3 +460,57 @@ def batch_spdhg_run(contexts, epochs: int, seeds, streams=None, ps=None):
     if st != 0:
         who = contexts[failed.value] if 0 <= failed.value < count else contexts[0]
         raise MCError(st, L.mc_last_error(who._h).decode())
+
+
+class Batch:
+    """Slices advanced together, one launch per stage of an SPDHG iteration
+    over all of them (mc_batch_create / mc_batch_run).  Keeps the contexts
+    alive; close() (or the context manager) releases the batch."""
+
+    def __init__(self, contexts, stream: Optional[int] = None):
+        L = lib()
+        self._L = L
+        self.contexts = list(contexts)
+        count = len(self.contexts)
+        arr = (ctypes.c_void_p * count)(*[c._h for c in self.contexts])
+        out = ctypes.c_void_p()
+        st = L.mc_batch_create(arr, count, ctypes.c_void_p(stream) if stream else None, ctypes.byref(out))
+        if st != 0:
+            msg = L.mc_last_error(self.contexts[0]._h).decode() if count else ""
+            raise MCError(st, msg or "mc_batch_create failed")
+        self._h = out.value
+
+    def run(self, epochs: int, seeds, streams=None, ps=None):
+        """`epochs` SPDHG epochs of every slice; per slice identical to
+        ctx.spdhg_run(epochs, seed, stream, p=p)."""
+        count = len(self.contexts)
+        streams = [0] * count if streams is None else streams
+        ps = [None] * count if ps is None else ps
+        one = [c._sampling(s, t, p) for c, s, t, p in zip(self.contexts, seeds, streams, ps)]
+        smp = (N.mc_sampling * count)(*[N.mc_sampling(o.seed, o.stream, o.p) for o in one])
+        if torch is not None and torch.cuda.is_available():
+            cur = torch.cuda.current_stream()
+            for c in self.contexts:
+                if c._stream is not None and c._stream != cur:
+                    c._stream.wait_stream(cur)
+        failed = ctypes.c_int32(-1)
+        st = self._L.mc_batch_run(self._h, int(epochs), smp, ctypes.byref(failed))
+        if st != 0:
+            raise MCError(st, self._L.mc_batch_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.mc_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -55,6 +55,10 @@ SIGNATURES = {
     "mc_solve_normal": (_I32, [_VP, _I32, _D, _VP, _VP]),
     "mc_spdhg_run": (_I32, [_VP, _I32, ctypes.POINTER(mc_sampling), _VP, _VP]),
     "mc_pdhg_run": (_I32, [_VP, _I32, _VP, _VP]),
+    "mc_batch_create": (_I32, [_VP, _I32, _VP, ctypes.POINTER(_VP)]),
+    "mc_batch_run": (_I32, [_VP, _I32, _VP, _VP]),
+    "mc_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "mc_batch_destroy": (None, [_VP]),
     "mc_batch_spdhg_run": (_I32, [_VP, _I32, _I32, _VP, _VP]),
     "mc_draw_gates": (_I32, [_VP, ctypes.POINTER(mc_sampling), _U64, _I32, _VP]),
     "mc_objective": (_I32, [_VP, _VP, _VP]),

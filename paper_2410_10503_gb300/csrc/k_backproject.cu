@@ -157,20 +157,17 @@ __device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long
 #endif
 
 template <int PJ, bool SUB>
-__global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
+__device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int slot)
 {
-    pdl_wait();
-    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);                             // [kGroups][kRing]
     AngSlot* s_slot = reinterpret_cast<AngSlot*>(smem + 128);                       // [kGroups][kRing][kBatch]
     float2* s_win = reinterpret_cast<float2*>(smem + 128 + kGroups * kRing * kBatch * sizeof(AngSlot));
     const int wl = a.wl;
     const int n = a.n;
-    const int slot = blockIdx.z;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int c0 = blockIdx.x * 32, c = c0 + lane;
-    const int r0 = blockIdx.y * PJ;
+    const int c0 = bx * 32, c = c0 + lane;
+    const int r0 = by * PJ;
     const float h = 0.5f * (float)(n - 1);
     const float le = (float)min(lane, n - 1 - c0);       // column offset in the tile (clamped at the edge)
     const float2* dys = a.dy + slot * a.dy_stride;
@@ -245,8 +242,8 @@ __global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
 #pragma unroll
             for (int j = 0; j < PJ; j += 2) {
                 float dx, dy;
-                float2 y0, y1;
 #ifdef MC_CHECKED
+                float2 y0, y1;
                 // the same arithmetic in C++, each pair index checked against
                 // the angle's window (0 <= offset <= WL - 1)
                 const float2 b2 = __ffma2_rn(make_float2((float)j, (float)(j + 1)), make_float2(sn, sn),
@@ -263,6 +260,7 @@ __global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
                 if (o0 >= 0 && o0 <= wl - 1) y0 = win[o0]; else atomicExch(a.err, kErrBounds);
                 if (o1 >= 0 && o1 <= wl - 1) y1 = win[o1]; else atomicExch(a.err, kErrBounds);
 #else
+                float2 y0, y1;
                 bp_two_rows(jj[j / 2], sn2, fr2, mm, row, dx, dy, y0, y1);
 #endif
                 acc[j] = fmaf(__saturatef(fmaf(-dx, m, 1.0f)), y0.x,
@@ -289,6 +287,27 @@ __global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
     }
 }
 
+template <int PJ, bool SUB>
+__global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    bp_block<PJ, SUB>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched: the tiles of every slice of the launch (all angles, one slot).
+template <int PJ>
+__global__ void __launch_bounds__(256, 4) k_backproject_batch(const BpArgs* __restrict__ args,
+                                                              const BatchBlock* __restrict__ map)
+{
+    pdl_wait();
+    pdl_trigger();
+    const BatchBlock m = map[blockIdx.x];
+    const BpArgs& a = args[m.slice];
+    const int tx = (a.n + 31) / 32;
+    bp_block<PJ, false>(a, m.block % tx, m.block / tx, 0);
+}
+
 }  // namespace
 
 int backproject_window(int pj) { return ((int)std::ceil(std::sqrt(31.0 * 31.0 + (pj - 1.0) * (pj - 1.0))) + 7) & ~1; }
@@ -309,10 +328,27 @@ cudaError_t backproject_prepare()
 #define MC_BP_ATTR(P, B)                                                                   \
     if (e == cudaSuccess)                                                                 \
         e = cudaFuncSetAttribute(k_backproject<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)backproject_smem_bytes(P));                         \
+    if (e == cudaSuccess && !B)                                                           \
+        e = cudaFuncSetAttribute(k_backproject_batch<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)backproject_smem_bytes(P));
     MC_BP_INSTANCES(MC_BP_ATTR)
 #undef MC_BP_ATTR
     return e;
+}
+
+int backproject_tiles(int n, int pj) { return ((n + 31) / 32) * ((n + pj - 1) / pj); }
+
+cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
+                                     cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = backproject_smem_bytes(pj);
+#define MC_BPB_LAUNCH(P, B)                                                              \
+    if (!B && pj == P) return pdl_launch(k_backproject_batch<P>, dim3(nblocks), dim3(256), smem, s, args, map);
+    MC_BP_INSTANCES(MC_BPB_LAUNCH)
+#undef MC_BPB_LAUNCH
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_backproject(const BpArgs& a_in, cudaStream_t s)

@@ -130,12 +130,12 @@ __device__ __forceinline__ void prefetch_span(const void* base, size_t bytes, in
         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
 }
 
-__device__ __forceinline__ void prefetch_csr(const FwdArgs& a, int gate)
+__device__ __forceinline__ void prefetch_csr(const FwdArgs& a, int gate, int part, int parts)
 {
     const size_t n2 = (size_t)a.n * a.n;
     const int* rp = a.pf_rowptr + (size_t)gate * (n2 + 1);
-    prefetch_span(rp, (n2 + 1) * sizeof(int), blockIdx.x, gridDim.x);
-    prefetch_span(a.pf_ent + a.pf_ent_off[gate], (size_t)__ldg(rp + n2) * sizeof(int2), blockIdx.x, gridDim.x);
+    prefetch_span(rp, (n2 + 1) * sizeof(int), part, parts);
+    prefetch_span(a.pf_ent + a.pf_ent_off[gate], (size_t)__ldg(rp + n2) * sizeof(int2), part, parts);
 }
 
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up (unless the launch sets one)
@@ -251,11 +251,12 @@ struct SlotRec {
 // epilogue.  Items then hold several times more ray groups and stream only
 // their band of the image, where an unbanded subset item would stream the
 // whole image for a few groups.
+// One block's work: items bx * ipb .. of the launch's item table for gate
+// slot `slot`; nbx = blocks sharing the table (the CSR prefetch is split
+// among them).
 template <int RPT, int LC, bool BANDED>
-__global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
+__device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot, int nbx)
 {
-    pdl_wait();
-    pdl_trigger();
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kStages;
@@ -265,14 +266,13 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     float2* stage0 = reinterpret_cast<float2*>(smem + 128);
     const size_t stage_pairs = (size_t)LC * a.P;   // one chunk: LC whole lines
 
-    const int slot = blockIdx.y;
     const int n = a.n, nb = a.nb;
     const int nch = layout_lines(n) / LC;        // the layouts hold whole chunks (zero lines past n)
     // this launch's item table: all angles, or the drawn block's angle subset
     const int sub = sel_subset(a.sel, slot);
     const RayItem* items = a.sub_off ? a.items + a.sub_off[sub] : a.items;
     const int n_items = a.sub_off ? a.sub_off[sub + 1] - a.sub_off[sub] : a.n_items;
-    const int it0 = blockIdx.x * a.ipb;
+    const int it0 = bx * a.ipb;
     const int n_it = min(a.ipb, n_items - it0);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -340,7 +340,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
         }
         // off the ring's critical path: prefetch the CSR the iteration's
         // transpose warp will read (a.pf_rowptr is set for one-slot SPDHG launches)
-        if (lane == 1 && a.pf_rowptr && a.n_slots == 1) prefetch_csr(a, sel_gate(a.sel, slot));
+        if (lane == 1 && a.pf_rowptr && a.n_slots == 1) prefetch_csr(a, sel_gate(a.sel, slot), bx, nbx);
         return;
     }
 
@@ -525,6 +525,26 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
     }
 }
 
+template <int RPT, int LC, bool BANDED>
+__global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    forward_block<RPT, LC, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x);
+}
+
+// Batched: the blocks of every slice of the launch, each on its slice's item
+// table with its slice's arguments (all angles, one slot, no bands).
+template <int RPT, int LC>
+__global__ void __launch_bounds__(kBlock, 1) k_forward_batch(const FwdArgs* __restrict__ args,
+                                                             const BatchBlock* __restrict__ map)
+{
+    pdl_wait();
+    pdl_trigger();
+    const BatchBlock m = map[blockIdx.x];
+    forward_block<RPT, LC, false>(args[m.slice], m.block, 0, m.nblocks);
+}
+
 // Sum of the bands' partial ray sums in band order, then the epilogue of
 // k_forward (store, or the dual update of Algorithm 1 (ii)); one thread per
 // ray of the launch's angle subset.
@@ -594,6 +614,9 @@ cudaError_t forward_prepare(int max_smem)
                                  max_smem);                                                       \
     if (e == cudaSuccess)                                                                         \
         e = cudaFuncSetAttribute(k_forward<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                 max_smem);                                                       \
+    if (e == cudaSuccess)                                                                         \
+        e = cudaFuncSetAttribute(k_forward_batch<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                  max_smem);
     MC_FWD_INSTANCES(MC_SET_ATTR)
 #undef MC_SET_ATTR
@@ -619,6 +642,19 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
     }
     MC_FWD_INSTANCES(MC_LAUNCH)
 #undef MC_LAUNCH
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt, int lc,
+                                 int smem_pairs, cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    const size_t smem = 128 + kStages * (size_t)smem_pairs * sizeof(float2);
+#define MC_LAUNCH_B(R, L)                                                                   \
+    if (rpt == R && lc == L)                                                                 \
+        return pdl_launch(k_forward_batch<R, L>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+    MC_FWD_INSTANCES(MC_LAUNCH_B)
+#undef MC_LAUNCH_B
     return cudaErrorInvalidValue;
 }
 

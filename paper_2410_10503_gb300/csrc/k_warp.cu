@@ -37,17 +37,14 @@ __device__ __forceinline__ float warp_sample(const float* __restrict__ x, int n,
 // line's data, (0, w[0]), is written by the tile that holds position 0.
 constexpr int kWarpTileRows = 30;
 
-__global__ void __launch_bounds__(1024) k_warp_layouts(WarpArgs a)
+__device__ __forceinline__ void warp_layouts_block(const WarpArgs& a, int bx, int by, int slot)
 {
-    pdl_wait();
-    pdl_trigger();
     __shared__ float w_s[kWarpTileRows + 1][34];
-    const int slot = blockIdx.z;
     const int gate = sel_gate(a.sel, slot);
     const int n = a.n;
     const RigidGate* rg = a.rigid ? a.rigid + gate : nullptr;
     const float* field = a.field ? a.field + (size_t)gate * 2 * n * n : nullptr;
-    const int r_t = blockIdx.y * kWarpTileRows, c_t = blockIdx.x * 32;
+    const int r_t = by * kWarpTileRows, c_t = bx * 32;
     const int tid = threadIdx.x;
     {
         // thread -> sample: tile (rows 0..29, columns 0..31), then the halo
@@ -89,6 +86,25 @@ __global__ void __launch_bounds__(1024) k_warp_layouts(WarpArgs a)
     }
 }
 
+__global__ void __launch_bounds__(1024) k_warp_layouts(WarpArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    warp_layouts_block(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Batched: the tiles of every slice of the launch, one slice's tile per block.
+__global__ void __launch_bounds__(1024) k_warp_layouts_batch(const WarpArgs* __restrict__ args,
+                                                             const BatchBlock* __restrict__ map)
+{
+    pdl_wait();
+    pdl_trigger();
+    const BatchBlock m = map[blockIdx.x];
+    const WarpArgs& a = args[m.slice];
+    const int tx = (a.n + 31) / 32;
+    warp_layouts_block(a, m.block % tx, m.block / tx, 0);
+}
+
 // Plain mode: w = D x as an n x n image.
 __global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
 {
@@ -111,6 +127,14 @@ cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
 {
     dim3 grid((a.n + 31) / 32, (a.n + kWarpTileRows - 1) / kWarpTileRows, a.n_slots), block(1024);
     return pdl_launch(k_warp_layouts, grid, block, 0, s, a);
+}
+
+int warp_layout_tiles(int n) { return ((n + 31) / 32) * ((n + kWarpTileRows - 1) / kWarpTileRows); }
+
+cudaError_t launch_warp_layouts_batch(const WarpArgs* args, const BatchBlock* map, int nblocks, cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    return pdl_launch(k_warp_layouts_batch, dim3(nblocks), dim3(1024), 0, s, args, map);
 }
 
 cudaError_t launch_warp_plain(const WarpArgs& a, cudaStream_t s)
@@ -312,12 +336,10 @@ cudaError_t launch_field_vjp(int n, const float* field, const float* x, const fl
 
 // ---- K5 (+K7) -------------------------------------------------------------
 template <bool UPDATE>
-__global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
+__device__ __forceinline__ void warp_adjoint_block(const WarpAdjArgs& a, int bx)
 {
-    pdl_wait();
-    pdl_trigger();
     const int n2 = a.n * a.n;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = bx * 256 + threadIdx.x;
     if (q >= n2) return;
     // the update's own operands first: their loads overlap the CSR chain
     float z0 = 0.0f, x0 = 0.0f;
@@ -360,6 +382,24 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
     }
 }
 
+template <bool UPDATE>
+__global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
+{
+    pdl_wait();
+    pdl_trigger();
+    warp_adjoint_block<UPDATE>(a, blockIdx.x);
+}
+
+// Batched: 256 pixels of one slice per block, every slice of the launch.
+__global__ void __launch_bounds__(256) k_warp_adjoint_update_batch(const WarpAdjArgs* __restrict__ args,
+                                                                   const BatchBlock* __restrict__ map)
+{
+    pdl_wait();
+    pdl_trigger();
+    const BatchBlock m = map[blockIdx.x];
+    warp_adjoint_block<true>(args[m.slice], m.block);
+}
+
 cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s)
 {
     const int n2 = a.n * a.n;
@@ -370,6 +410,15 @@ cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s)
 {
     const int n2 = a.n * a.n;
     return pdl_launch(k_warp_adjoint<true>, dim3((n2 + 255) / 256), dim3(256), 0, s, a);
+}
+
+int warp_adjoint_blocks(int n) { return (n * n + 255) / 256; }
+
+cudaError_t launch_warp_adjoint_update_batch(const WarpAdjArgs* args, const BatchBlock* map, int nblocks,
+                                             cudaStream_t s)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    return pdl_launch(k_warp_adjoint_update_batch, dim3(nblocks), dim3(256), 0, s, args, map);
 }
 
 }  // namespace mcg

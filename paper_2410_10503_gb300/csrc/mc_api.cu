@@ -2246,3 +2246,405 @@ mc_status mc_iteration(mc_ctx* c, uint64_t* out)
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Batched SPDHG over many slices: one launch per stage of an iteration spans
+// every slice in flight (per class of launch shape), replayed as CUDA graphs.
+// ============================================================================
+namespace {
+
+// The launches of one batched iteration for the slices 0 .. A-1 of the
+// batch's order (those still running): block maps per stage and class, and
+// the captured graph of each parity of the iteration index.
+struct BatchPhase {
+    BatchBlock* d_map = nullptr;             // every map of the phase, one allocation
+    int n_warp = 0, n_wadj = 0;
+    size_t off_warp = 0, off_wadj = 0;
+    struct Fwd { int lc, rpt, smem_pairs, n; size_t off; };
+    struct Bp { int pj, n; size_t off; };
+    std::vector<Fwd> fwd;
+    std::vector<Bp> bp;
+    cudaGraphExec_t g[2] = {nullptr, nullptr};
+};
+
+}  // namespace
+
+struct mc_batch {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string err;
+    std::vector<mc_ctx*> ctx;                // caller's order
+    std::vector<int> order;                  // slices by iterations per epoch, descending
+    // per-slice argument tables in the order above ([2]: parity of the iteration)
+    WarpArgs* d_warp[2] = {nullptr, nullptr};
+    FwdArgs* d_fwd = nullptr;
+    BpArgs* d_bp = nullptr;
+    WarpAdjArgs* d_wadj[2] = {nullptr, nullptr};
+    BatchDraw* d_draw = nullptr;
+    int* d_pos = nullptr;
+    std::vector<BatchPhase> phase;           // [A - 1] for A slices in flight, built on demand
+    std::vector<cudaEvent_t> ev;             // one per slice (hand-off between streams) + 1
+};
+
+namespace {
+
+mc_status bfail(mc_batch* b, mc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return st;
+}
+
+#define BCK(call)                                                                          \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return bfail(b, MC_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+    } while (0)
+
+void batch_free(mc_batch* b)
+{
+    for (auto& ph : b->phase) {
+        for (auto& g : ph.g)
+            if (g) cudaGraphExecDestroy(g);
+        if (ph.d_map) cudaFree(ph.d_map);
+    }
+    b->phase.clear();
+    for (void* p : {(void*)b->d_warp[0], (void*)b->d_warp[1], (void*)b->d_fwd, (void*)b->d_bp,
+                    (void*)b->d_wadj[0], (void*)b->d_wadj[1], (void*)b->d_draw, (void*)b->d_pos})
+        if (p) cudaFree(p);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    b->ev.clear();
+}
+
+template <class T>
+mc_status balloc(mc_batch* b, T** p, size_t count)
+{
+    void* q = nullptr;
+    const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count * sizeof(T), 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, MC_ENOMEM, "cudaMalloc failed: %s", cudaGetErrorString(e));
+    }
+    *p = static_cast<T*>(q);
+    return MC_OK;
+}
+
+// Fill the per-slice argument tables from the contexts' current state (step
+// sizes, storage, sampling, parity of x): exactly the arguments the
+// one-slice epoch of enqueue_spdhg_epoch gives its kernels, with the drawn
+// gate read through the slice's epoch position.
+mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
+{
+    const int B = (int)b->order.size();
+    std::vector<WarpArgs> w[2];
+    std::vector<WarpAdjArgs> wa[2];
+    std::vector<FwdArgs> f(B);
+    std::vector<BpArgs> bp(B);
+    std::vector<BatchDraw> dr(B);
+    for (int t = 0; t < 2; ++t) { w[t].resize(B); wa[t].resize(B); }
+    for (int q = 0; q < B; ++q) {
+        mc_ctx* c = b->ctx[b->order[q]];
+        const GateSel sel{c->d_gates, -1, 1, b->d_pos + q};
+        const bool nonuni = !c->p_steps.empty();
+        for (int t = 0; t < 2; ++t) {
+            WarpArgs& a = w[t][q];
+            a = WarpArgs{};
+            a.x = c->d_x[c->cur ^ t]; a.n = c->n;
+            a.rigid = c->d_rigid; a.field = c->d_field; a.identity = 0;
+            a.sel = sel; a.n_slots = 1;
+            a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+            WarpAdjArgs& u = wa[t][q];
+            u = wadj_args(c, sel, 1, c->d_b);
+            u.z = c->d_z; u.x_in = c->d_x[c->cur ^ t]; u.x_out = c->d_x[c->cur ^ t ^ 1];
+            u.coef = (float)(c->sS.theta * c->N);
+            u.coef_tab = nonuni ? c->d_coef : nullptr;
+            u.tau = (float)c->sS.tau;
+            u.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sS.tau * c->alpha));
+        }
+        FwdArgs& a = f[q];
+        a = FwdArgs{};
+        a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+        a.ang = c->d_fang; a.groups = c->d_groups; a.items = c->d_items; a.n_items = c->n_items;
+        a.ipb = c->ipb; a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
+        a.sel = sel; a.n_slots = 1; a.wait_limit = 1u << 24;
+        a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb; a.err = c->d_err;
+        a.mode = 1; a.d = c->d_d; a.y = c->d_y;
+        a.sigma = (float)c->sS.sigma;
+        a.inv_den = (float)(1.0 / (1.0 + c->sS.sigma * c->N / 2.0));
+        a.pf_rowptr = c->d_rowptr; a.pf_ent = c->d_ent; a.pf_ent_off = c->d_ent_off;
+        a.store = c->store; a.dh = c->d_dh; a.yh = c->d_yh;
+        BpArgs& g = bp[q];
+        g = BpArgs{};
+        g.sel = sel;
+        g.dy = c->d_dy; g.dy_stride = c->dy_stride; g.Pb = c->Pb; g.Gb = c->Gb;
+        g.ang = c->d_bang; g.n = c->n; g.na = c->na; g.nb = c->nb; g.n_slots = 1;
+        g.pj = c->pj; g.out = c->d_b; g.err = c->d_err; g.wl = backproject_window(c->pj);
+        if (g.wl > g.Pb) return bfail(b, MC_EINVAL, "slice %d: backprojection window wider than its dual layout",
+                                      b->order[q]);
+        const mc_sampling& sm = sampling[b->order[q]];
+        dr[q] = BatchDraw{sm.seed, sm.stream, c->N, c->d_k, nonuni ? c->d_thr : nullptr, c->d_gates, b->d_pos + q};
+    }
+    for (int t = 0; t < 2; ++t) {
+        BCK(cudaMemcpy(b->d_warp[t], w[t].data(), B * sizeof(WarpArgs), cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(b->d_wadj[t], wa[t].data(), B * sizeof(WarpAdjArgs), cudaMemcpyHostToDevice));
+    }
+    BCK(cudaMemcpy(b->d_fwd, f.data(), B * sizeof(FwdArgs), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_bp, bp.data(), B * sizeof(BpArgs), cudaMemcpyHostToDevice));
+    BCK(cudaMemcpy(b->d_draw, dr.data(), B * sizeof(BatchDraw), cudaMemcpyHostToDevice));
+    return MC_OK;
+}
+
+// Block maps of the iteration with slices order[0 .. A-1] in flight.  Each
+// stage lists every such slice's blocks (the same blocks as its one-slice
+// launch), slices with more work per block first so that the block scheduler
+// ends the launch with the small ones; the forward and the backprojection
+// get one launch per class of their template shape (lines per chunk, rows
+// per thread).
+mc_status batch_phase(mc_batch* b, int A)
+{
+    BatchPhase& ph = b->phase[A - 1];
+    if (ph.d_map) return MC_OK;
+    std::vector<int> q(A);
+    for (int i = 0; i < A; ++i) q[i] = i;
+    auto C = [&](int i) { return b->ctx[b->order[i]]; };
+    std::vector<BatchBlock> all;
+    auto add = [&](std::vector<int> qs, auto blocks_of, auto work_of) {
+        std::stable_sort(qs.begin(), qs.end(), [&](int x, int y) { return work_of(x) > work_of(y); });
+        const size_t off = all.size();
+        for (int i : qs) {
+            const int nbk = blocks_of(i);
+            for (int k = 0; k < nbk; ++k) all.push_back(BatchBlock{i, k, nbk, 0});
+        }
+        return std::make_pair(off, (int)(all.size() - off));
+    };
+    // warp: tiles of 32 x 30 pixels, equal work
+    {
+        auto r = add(q, [&](int i) { return warp_layout_tiles(C(i)->n); }, [&](int) { return 0.0; });
+        ph.off_warp = r.first; ph.n_warp = r.second;
+    }
+    // forward: per lines-per-chunk class; a block's work ~ samples / blocks
+    std::vector<int> lcs;
+    for (int i : q) if (std::find(lcs.begin(), lcs.end(), C(i)->lc) == lcs.end()) lcs.push_back(C(i)->lc);
+    for (int lc : lcs) {
+        std::vector<int> qs;
+        int rpt = 2, pairs = 0;
+        for (int i : q)
+            if (C(i)->lc == lc) {
+                qs.push_back(i);
+                rpt = std::max(rpt, C(i)->rpt);
+                pairs = std::max(pairs, lc * C(i)->P);
+            }
+        auto blocks = [&](int i) { return (C(i)->n_items + C(i)->ipb - 1) / C(i)->ipb; };
+        auto r = add(qs, blocks, [&](int i) {
+            const mc_ctx* c = C(i);
+            return (double)c->na * c->n * c->n / blocks(i);
+        });
+        ph.fwd.push_back(BatchPhase::Fwd{lc, rpt, pairs, r.second, r.first});
+    }
+    // backprojection: per rows-per-thread class; a tile's work ~ angles
+    std::vector<int> pjs;
+    for (int i : q) if (std::find(pjs.begin(), pjs.end(), C(i)->pj) == pjs.end()) pjs.push_back(C(i)->pj);
+    for (int pj : pjs) {
+        std::vector<int> qs;
+        for (int i : q) if (C(i)->pj == pj) qs.push_back(i);
+        auto r = add(qs, [&](int i) { return backproject_tiles(C(i)->n, pj); },
+                     [&](int i) { return (double)C(i)->na; });
+        ph.bp.push_back(BatchPhase::Bp{pj, r.second, r.first});
+    }
+    // transpose warp and update: 256 pixels per block
+    {
+        auto r = add(q, [&](int i) { return warp_adjoint_blocks(C(i)->n); }, [&](int) { return 0.0; });
+        ph.off_wadj = r.first; ph.n_wadj = r.second;
+    }
+    if (balloc(b, &ph.d_map, all.size()) != MC_OK) return MC_ENOMEM;
+    BCK(cudaMemcpy(ph.d_map, all.data(), all.size() * sizeof(BatchBlock), cudaMemcpyHostToDevice));
+    return MC_OK;
+}
+
+// Enqueue one batched iteration (parity t of the iteration index) for the
+// slices of phase A on the batch's stream.
+mc_status batch_enqueue(mc_batch* b, int A, int t)
+{
+    BatchPhase& ph = b->phase[A - 1];
+    cudaStream_t s = b->stream;
+    BCK(launch_draw_batch(b->d_draw, A, s));
+    BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
+    for (const auto& f : ph.fwd)
+        BCK(launch_forward_batch(b->d_fwd, ph.d_map + f.off, f.n, f.rpt, f.lc, f.smem_pairs, s));
+    for (const auto& g : ph.bp) BCK(launch_backproject_batch(b->d_bp, ph.d_map + g.off, g.n, g.pj, s));
+    BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, s));
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream, mc_batch** out)
+{
+    if (!out || !ctxs || count < 1) return MC_EINVAL;
+    *out = nullptr;
+    mc_batch* b = new mc_batch();
+    for (int i = 0; i < count; ++i) {
+        mc_ctx* c = ctxs[i];
+        if (!c) { delete b; return MC_EINVAL; }
+        if (i == 0) b->dev = c->dev;
+        if (c->dev != b->dev) { delete b; return fail(c, MC_EINVAL, "batch contexts must share one device"); }
+        if (c->S != 1) { delete b; return fail(c, MC_EINVAL, "batched runs sample gates only (subsets = 1)"); }
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == c) { delete b; return fail(c, MC_EINVAL, "a context appears twice in the batch"); }
+        b->ctx.push_back(c);
+    }
+    mc_status st = MC_OK;
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) == cudaSuccess) {
+        b->own_stream = true;
+    } else {
+        cudaGetLastError();
+        delete b;
+        return MC_ECUDA;
+    }
+    // slices by iterations per epoch (N), then by size: the slices in flight
+    // are always a prefix of this order
+    for (int i = 0; i < count; ++i) b->order.push_back(i);
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        const mc_ctx *p = b->ctx[x], *q = b->ctx[y];
+        if (p->N != q->N) return p->N > q->N;
+        return (double)p->na * p->n * p->n > (double)q->na * q->n * q->n;
+    });
+    for (int t = 0; t < 2 && st == MC_OK; ++t) {
+        st = balloc(b, &b->d_warp[t], count);
+        if (st == MC_OK) st = balloc(b, &b->d_wadj[t], count);
+    }
+    if (st == MC_OK) st = balloc(b, &b->d_fwd, count);
+    if (st == MC_OK) st = balloc(b, &b->d_bp, count);
+    if (st == MC_OK) st = balloc(b, &b->d_draw, count);
+    if (st == MC_OK) st = balloc(b, &b->d_pos, count);
+    b->phase.resize(count);
+    for (int i = 0; i <= count && st == MC_OK; ++i) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            st = MC_ECUDA;
+        } else {
+            b->ev.push_back(e);
+        }
+    }
+    if (st != MC_OK) {
+        batch_free(b);
+        if (b->own_stream) cudaStreamDestroy(b->stream);
+        delete b;
+        return st;
+    }
+    *out = b;
+    return MC_OK;
+}
+
+const char* mc_batch_last_error(const mc_batch* b) { return b ? b->err.c_str() : ""; }
+
+void mc_batch_destroy(mc_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+mc_status mc_batch_run(mc_batch* b, int32_t epochs, const mc_sampling* sampling, int32_t* failed)
+{
+    if (failed) *failed = -1;
+    if (!b) return MC_EINVAL;
+    if (!sampling) return bfail(b, MC_EINVAL, "sampling is NULL");
+    if (epochs < 0) return bfail(b, MC_EINVAL, "epochs must be >= 0");
+    const int B = (int)b->ctx.size();
+    for (int i = 0; i < B; ++i) {
+        mc_ctx* c = b->ctx[i];
+        mc_status st = MC_OK;
+        if (!c->have_data || !c->steps_ok)
+            st = fail(c, MC_ESTATE, "runs need mc_set_data and mc_norms/mc_set_norms first");
+        else if (c->S != 1)
+            st = fail(c, MC_EINVAL, "batched runs sample gates only (subsets = 1)");
+        if (st == MC_OK) st = apply_sampling(c, &sampling[i]);
+        if (st != MC_OK) {
+            if (failed) *failed = i;
+            return bfail(b, st, "slice %d: %s", i, c->err.c_str());
+        }
+    }
+    if (epochs == 0) return MC_OK;
+    // the batch's stream starts after every slice's own pending work
+    for (int i = 0; i < B; ++i) {
+        BCK(cudaEventRecord(b->ev[i], b->ctx[i]->stream));
+        BCK(cudaStreamWaitEvent(b->stream, b->ev[i], 0));
+    }
+    // the tables are read by the graphs at run time: no graph is recaptured
+    // for new step sizes, seeds or sampling
+    BCK(cudaStreamSynchronize(b->stream));
+    TRY(batch_tables(b, sampling));
+    // epoch positions: the first iteration of every slice starts an epoch
+    std::vector<int> pos(B);
+    std::vector<long long> iters(B);
+    for (int q = 0; q < B; ++q) {
+        mc_ctx* c = b->ctx[b->order[q]];
+        pos[q] = c->N - 1;
+        iters[q] = (long long)epochs * c->N;
+    }
+    BCK(cudaMemcpyAsync(b->d_pos, pos.data(), B * sizeof(int), cudaMemcpyHostToDevice, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));           // pos copied from the host vector
+    long long done = 0;
+    int A = B;
+    while (A > 0) {
+        // the iterations in which exactly the first A slices are in flight
+        const long long end = iters[A - 1];
+        if (end > done) {
+            TRY(batch_phase(b, A));
+            BatchPhase& ph = b->phase[A - 1];
+            for (long long it = done; it < end; ++it) {
+                const int t = (int)(it & 1);
+                if (!ph.g[t]) {
+                    cudaGraph_t g = nullptr;
+                    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+                    const mc_status st = batch_enqueue(b, A, t);
+                    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+                    if (st != MC_OK) { if (g) cudaGraphDestroy(g); return st; }
+                    if (e != cudaSuccess) return bfail(b, MC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+                    const cudaError_t e2 = cudaGraphInstantiate(&ph.g[t], g, 0);
+                    cudaGraphDestroy(g);
+                    if (e2 != cudaSuccess)
+                        return bfail(b, MC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
+                }
+                BCK(cudaGraphLaunch(ph.g[t], b->stream));
+            }
+            done = end;
+        }
+        --A;
+    }
+    // every slice's own stream continues after the batch
+    BCK(cudaEventRecord(b->ev[B], b->stream));
+    for (int i = 0; i < B; ++i) BCK(cudaStreamWaitEvent(b->ctx[i]->stream, b->ev[B], 0));
+    BCK(cudaStreamSynchronize(b->stream));
+    for (int q = 0; q < B; ++q) {
+        mc_ctx* c = b->ctx[b->order[q]];
+        c->k_host += (uint64_t)iters[q];
+        c->cur ^= (int)(iters[q] & 1);
+    }
+    for (int i = 0; i < B; ++i) {
+        mc_ctx* c = b->ctx[i];
+        mc_status st = check_err_word(c);
+        if (st == MC_OK) st = finish(c);
+        if (st != MC_OK) {
+            if (failed) *failed = i;
+            return bfail(b, st, "slice %d: %s", i, c->err.c_str());
+        }
+    }
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -16,12 +16,35 @@ struct GateSel {
     const int* list;
     int fixed;
     int subsets;
+    const int* pos;            // non-null (batched runs): the slot's entry of list is
+                               // list[*pos], the slice's iteration within its epoch
 };
 
 __device__ __forceinline__ int sel_block(const GateSel& s, int slot)
 {
-    return s.list ? s.list[slot] : (s.fixed >= 0 ? s.fixed : slot);
+    return s.list ? s.list[s.pos ? *s.pos : slot] : (s.fixed >= 0 ? s.fixed : slot);
 }
+
+// Batched launches over many independent slices (one context each): block b
+// of the launch works on block `block` (of `nblocks`) of slice `slice`, with
+// that slice's arguments args[slice].
+struct BatchBlock {
+    int slice, block, nblocks, pad;
+};
+
+// The gate draw of one slice in a batched iteration (k_draw_batch): the
+// slice's position in its epoch advances by one (mod n_blocks); at position 0
+// the epoch's n_blocks gates are drawn from the slice's counter as the
+// one-slice draw does.
+struct BatchDraw {
+    uint64_t seed;
+    uint32_t stream;
+    int n_blocks;
+    unsigned long long* kctr;
+    const unsigned long long* thr;
+    int* gates;
+    int* pos;
+};
 
 __device__ __forceinline__ int sel_gate(const GateSel& s, int slot)
 {
@@ -50,6 +73,9 @@ struct WarpArgs {
     float* out;                // plain mode: n*n per slot
 };
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s);
+// batched: block b computes tile map[b].block of slice map[b].slice (one slot)
+cudaError_t launch_warp_layouts_batch(const WarpArgs* args, const BatchBlock* map, int nblocks, cudaStream_t s);
+int warp_layout_tiles(int n);
 cudaError_t launch_warp_plain(const WarpArgs& a, cudaStream_t s);
 
 // ---- K2: per-gate CSR of D_i^T --------------------------------------------
@@ -88,6 +114,9 @@ struct WarpAdjArgs {
 };
 cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s);
 cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s);
+cudaError_t launch_warp_adjoint_update_batch(const WarpAdjArgs* args, const BatchBlock* map, int nblocks,
+                                             cudaStream_t s);
+int warp_adjoint_blocks(int n);
 
 // ---- K3 (+K6): Joseph forward projection ------------------------------------
 struct FwdArgs {
@@ -133,6 +162,12 @@ struct FwdArgs {
     int stall;                 // 1: the producer issues no copies (tests the waits' failure path)
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
+// batched (all angles, one slot per slice, no bands): block b runs block
+// map[b].block of slice map[b].slice's item table; every slice of the launch
+// has lines per chunk lc and at most rpt group slots per warp; smem_pairs =
+// the largest lc x P of the launch's slices
+cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt, int lc,
+                                 int smem_pairs, cudaStream_t s);
 int forward_groups_per_block(int rpt);
 int forward_consumer_warps();         // consumer warps per block
 int forward_ring_stages();            // chunks in flight (the drift between warps)
@@ -155,9 +190,17 @@ struct BpArgs {
     int wl;                    // staged window length (pairs), set by the launcher
 };
 cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
+// batched (all angles, one slot per slice): every slice of the launch has pj
+// rows per thread; block b works on tile map[b].block of slice map[b].slice
+cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
+                                     cudaStream_t s);
+int backproject_tiles(int n, int pj);
+int backproject_window(int pj);
 cudaError_t backproject_prepare();
 
 // ---- misc -------------------------------------------------------------------
+// one block per slice of a batched iteration (see BatchDraw)
+cudaError_t launch_draw_batch(const BatchDraw* d, int count, cudaStream_t s);
 // thr: null for uniform sampling, else N cumulative thresholds (see k_draw_gates)
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
                               uint64_t k0, int count, int n_gates, const unsigned long long* thr, int* out,

@@ -90,3 +90,82 @@ def test_batch_reports_the_failing_slice(mc, slices):
     bad.set_data(P.d.astype(np.float32), P.alpha)            # no norms: no step sizes
     with pytest.raises(mc.MCError, match="norms"):
         mc.batch_spdhg_run([good, bad], 1, seeds=[1, 2])
+
+
+# ---- mc_batch: one launch per stage over all slices --------------------------
+@pytest.fixture(scope="module")
+def merged_slices():
+    """Four slices of different sizes, gate counts and motion kinds (gate
+    sampling only), plus a larger slice whose forward and backprojection take
+    other launch shapes (4 lines per chunk; its own rows per thread)."""
+    ws = S.slice_batch(4, seed=6200, sides=(48, 64, 40, 56))
+    out = []
+    for j, W in enumerate(ws):
+        W = W.scaled(n_gates=3 + j)
+        P, sd = slice_problem(W)
+        out.append((W, P, sd, O.gate_norms2(P, 30, 1e-12)))
+    return out
+
+
+def big_slice(mc):
+    """n = 560 (4 lines per chunk), 60 angles, rigid, 3 gates: compared with
+    its own run only (no oracle at this size)."""
+    W = S.WORKLOADS["rigid128"].scaled(n=560, n_angles=60, n_bins=577, n_gates=3, n_ellipses=12,
+                                       axis_lo=10.0, axis_hi=60.0)
+    sd = S.seeds(W.cid)
+    rig = S.rigid_motion(3, 4.0, 3.0, sd["motion"])
+    ctx = mc.Context(W.n, W.n_angles, W.n_bins, 3, rigid=rig)
+    xt = torch.as_tensor(S.phantom(W.n, 12, sd["phantom"], 10.0, 60.0), dtype=torch.float32, device="cuda")
+    d = torch.stack([ctx.forward(i, xt) for i in range(3)])
+    ctx.set_data(d, 1e-2)
+    ctx.set_norms(np.array([2.0e4, 2.0e4, 2.0e4, 6.0e4]))
+    return ctx, d, rig
+
+
+
+
+def test_merged_batch_equals_separate_runs_and_oracle(mc, merged_slices):
+    E = 4
+    ctxs = [make_ctx(mc, P, nrm) for _, P, _, nrm in merged_slices]
+    big, d_big, rig_big = big_slice(mc)
+    ctxs.append(big)
+    seeds = [sd["gates"] for _, _, sd, _ in merged_slices] + [777]
+    n3 = merged_slices[3][1].N                        # slice 3 samples its gates non-uniformly
+    ps = [None, None, None, np.linspace(1.0, 2.0, n3) / np.linspace(1.0, 2.0, n3).sum(), None]
+    with mc.Batch(ctxs) as b:
+        b.run(2, seeds, ps=ps)            # two runs in a row continue the state
+        b.run(E - 2, seeds, ps=ps)
+    for j, ((W, P, sd, nrm), ctx) in enumerate(zip(merged_slices, ctxs)):
+        assert ctx.iteration() == E * P.N
+        own = make_ctx(mc, P, nrm)
+        x_own, _ = own.spdhg_run(E, seed=sd["gates"], p=ps[j])
+        x_b, _ = ctx.spdhg_run(0, seed=sd["gates"], p=ps[j])
+        np.testing.assert_array_equal(x_b, x_own)
+        own.close()
+    own = mc.Context(560, 60, 577, 3, rigid=rig_big)
+    own.set_data(d_big, 1e-2)
+    own.set_norms(np.array([2.0e4, 2.0e4, 2.0e4, 6.0e4]))
+    x_own, _ = own.spdhg_run(E, seed=777)
+    x_b, _ = big.spdhg_run(0, seed=777)
+    np.testing.assert_array_equal(x_b, x_own)
+    # one slice against the FP64 oracle
+    W, P, sd, nrm = merged_slices[1]
+    ref = O.spdhg(P, E, O.step_sizes(nrm[:P.N].max(), P.alpha, P.N, P.N), seed=sd["gates"])
+    x1, _ = ctxs[1].spdhg_run(0, seed=sd["gates"])
+    assert rel_l2(x1, ref.x) <= 1e-4
+    for c in ctxs:
+        c.close()
+
+
+def test_merged_batch_reports_the_failing_slice(mc, merged_slices):
+    W, P, sd, nrm = merged_slices[0]
+    good = make_ctx(mc, P, nrm)
+    bad = mc.Context(P.geom.n, P.geom.na, P.geom.nb, P.N, rigid=P.motion.rigid
+                     if P.motion.rigid is not None else np.zeros((P.N, 3)))
+    bad.set_data(P.d.astype(np.float32), P.alpha)            # no norms: no step sizes
+    with mc.Batch([good, bad]) as b:
+        with pytest.raises(mc.MCError, match="slice 1"):
+            b.run(1, seeds=[1, 2])
+    sub = make_ctx(mc, P, O.block_norms2(P, 2, iters=10, tol=1e-8), subsets=2)
+    with pytest.raises(mc.MCError):
+        mc.Batch([good, sub])
