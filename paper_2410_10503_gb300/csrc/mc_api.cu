@@ -7,6 +7,7 @@
 // is one of the kernels in k_*.cu.
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -14,6 +15,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mc.h"
@@ -893,29 +895,58 @@ double load_wavefronts(const mc_ctx* c, int k)
     return 1.0 + std::min(1.0, 15.0 * (std::fabs(c->inv_k[k]) - 1.0));
 }
 
+// Run body(i) for i in [0, count) on the host's cores (items of a plan are
+// independent); the results do not depend on the number of threads.
+template <class F>
+void parallel_for(size_t count, F&& body)
+{
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nt = (unsigned)std::min<size_t>(hw, count);
+    if (nt <= 1) {
+        for (size_t i = 0; i < count; ++i) body(i);
+        return;
+    }
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> pool;
+    pool.reserve(nt);
+    for (unsigned t = 0; t < nt; ++t)
+        pool.emplace_back([&] {
+            for (size_t i = next++; i < count; i = next++) body(i);
+        });
+    for (auto& th : pool) th.join();
+}
+
 void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vector<RayItem>& items, int& rpt,
                    std::vector<double>* item_time = nullptr)
 {
     const int W = forward_consumer_warps(), half = forward_ring_stages() - 1;
     const int nch = layout_lines(c->n) / lc;
-    std::vector<std::vector<float>> win;        // windowed cost per group of the item
-    std::vector<float> cost, load, total, top, wsum;
-    std::vector<int> idx;
-    std::vector<std::vector<int>> lists(W);
-    std::vector<int2> out;
-    out.reserve(groups.size() + items.size() * W);
-    int most = 1;
-    for (RayItem& it : items) {
+    struct Deal {
+        std::vector<std::vector<int>> lists;
+        double T = 0.0;
+    };
+    std::vector<Deal> deals(items.size());
+    parallel_for(items.size(), [&](size_t ii) {
+        const RayItem& it = items[ii];
+        std::vector<std::vector<float>> win;        // windowed cost per group of the item
+        std::vector<float> cost, load, total, top, wsum;
+        std::vector<int> idx;
+        std::vector<std::vector<int>>& lists = deals[ii].lists;
+        lists.assign(W, {});
         const int m = it.end - it.begin;
         win.assign(m, std::vector<float>(nch, 0.0f));
         total.assign(m, 0.0f);
+        std::vector<int> g_lo(m, nch), g_hi(m, -1);  // window range of each group
         for (int g = 0; g < m; ++g) {
             const int2 grp = groups[it.begin + g];
             group_chunk_costs(c, grp.x, grp.y, lc, cost);
             for (int ch = 0; ch < nch; ++ch) {
                 if (cost[ch] == 0.0f) continue;
                 total[g] += cost[ch];
-                for (int q = std::max(0, ch - half); q <= std::min(nch - 1, ch + half); ++q) win[g][q] += cost[ch];
+                const int q0 = std::max(0, ch - half), q1 = std::min(nch - 1, ch + half);
+                g_lo[g] = std::min(g_lo[g], q0);
+                g_hi[g] = std::max(g_hi[g], q1);
+                for (int q = q0; q <= q1; ++q) win[g][q] += cost[ch];
             }
         }
         idx.resize(m);
@@ -925,14 +956,15 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vect
         load.assign((size_t)W * nch, 0.0f);
         top.assign(nch, 0.0f);
         wsum.assign(W, 0.0f);
-        for (auto& L : lists) L.clear();
         for (int g : idx) {
             int best_w = -1;
             float best = 0.0f;
             for (int w = 0; w < W; ++w) {
                 if ((int)lists[w].size() >= cap) continue;
+                // outside the group's window its cost is zero and a warp's load
+                // never exceeds the top: those chunks add nothing
                 float rise = 0.0f;
-                for (int ch = 0; ch < nch; ++ch)
+                for (int ch = g_lo[g]; ch <= g_hi[g]; ++ch)
                     rise += std::max(0.0f, load[(size_t)w * nch + ch] + win[g][ch] - top[ch]);
                 if (best_w < 0 || rise < best || (rise == best && wsum[w] < wsum[best_w])) {
                     best = rise;
@@ -941,15 +973,12 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vect
             }
             lists[best_w].push_back(g);
             wsum[best_w] += total[g];
-            for (int ch = 0; ch < nch; ++ch) {
+            for (int ch = g_lo[g]; ch <= g_hi[g]; ++ch) {
                 float& l = load[(size_t)best_w * nch + ch];
                 l += win[g][ch];
                 top[ch] = std::max(top[ch], l);
             }
         }
-        int L = 0;
-        for (const auto& l : lists) L = std::max(L, (int)l.size());
-        most = std::max(most, L);
         if (item_time) {
             // the block's time in a model of the ring: a warp may start chunk ch
             // once every warp has released chunk ch - kStages; a group's chunk
@@ -975,8 +1004,19 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vect
                     if (ch == nch - 1) T = std::max(T, done[(size_t)w * nch + ch]);
                 }
             }
-            item_time->push_back(T);
+            deals[ii].T = T;
         }
+    });
+    std::vector<int2> out;
+    out.reserve(groups.size() + items.size() * W);
+    int most = 1;
+    for (size_t ii = 0; ii < items.size(); ++ii) {
+        RayItem& it = items[ii];
+        const auto& lists = deals[ii].lists;
+        int L = 0;
+        for (const auto& l : lists) L = std::max(L, (int)l.size());
+        most = std::max(most, L);
+        if (item_time) item_time->push_back(deals[ii].T);
         const int begin = (int)out.size();
         for (int sl = 0; sl < L; ++sl)
             for (int w = 0; w < W; ++w)
