@@ -427,7 +427,14 @@ def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs, alpha_epochs):
                "rate_bound_per_epoch": {"spdhg": _rate(ctx.steps()["kappa"], W.n_gates),
                                         "pdhg": _rate(ctx.steps(pdhg=True)["kappa"], 1)}}
         leg["spdhg_graph"] = time_to_tol(ctx, stream, "spdhg", 1e-3, cap, sd["gates"], True, chunk)
-        leg["spdhg_plain"] = time_to_tol(ctx, stream, "spdhg", 1e-3, cap, sd["gates"], False, chunk)
+        if chunk == 1:
+            leg["spdhg_plain"] = time_to_tol(ctx, stream, "spdhg", 1e-3, cap, sd["gates"], False, chunk)
+        # the same SPDHG iterates through the three launch paths (plain launches,
+        # graph-replayed epochs, merged batched iterations: bit-identical), timed
+        # per epoch without the trace on a 1000-epoch sample, times the epochs
+        leg["spdhg_same_iterates_no_trace"] = {
+            how: projected_time(ctx, stream, how, leg["spdhg_graph"], sd["gates"], 1000)
+            for how in ("graph", "plain", "batched")}
         leg["pdhg_graph"] = time_to_tol(ctx, stream, "pdhg", 1e-3, cap, sd["gates"], True, chunk)
         if label == "paper_regime_kappa70":
             # sampling over gates x angle subsets (Sec. IV): same objective and x*,
@@ -445,6 +452,49 @@ def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs, alpha_epochs):
         out[label] = leg
     ctx.set_data(d, W.alpha)
     ctx.set_norms(norms)
+    return out
+
+
+def projected_time(ctx, stream, how, graph_leg, seed, sample_epochs):
+    """Time to the tolerance of an SPDHG path whose iterates equal the graph
+    run's bit for bit (graph replay, plain launches, or the merged batched path
+    with this one slice): the graph run's epochs times this path's time per
+    epoch, measured on `sample_epochs` epochs without the trace, so that the
+    three paths compare on one basis."""
+    import torch
+
+    import paper_2410_10503_gb300 as mc
+    ctx.reset()
+    out = {"sample_epochs": sample_epochs}
+    if how in ("plain", "graph"):
+        ctx.set_option(1, 1 if how == "graph" else 0)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ctx.spdhg_run(2, seed=seed, x_out=False)
+            stream.synchronize()
+            t0 = time.perf_counter()
+            ctx.spdhg_run(sample_epochs, seed=seed, x_out=False)
+            stream.synchronize()
+            per_epoch = (time.perf_counter() - t0) / sample_epochs
+        ctx.set_option(1, 1)
+        out["timing"] = "host clock around mc_spdhg_run of the sample and a stream synchronisation (no trace)"
+    else:
+        batch = mc.Batch([ctx])
+        batch.run(2, [seed])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        batch.run(sample_epochs, [seed])
+        per_epoch = (time.perf_counter() - t0) / sample_epochs
+        batch.close()
+        out["timing"] = "host clock around mc_batch_run (returns after the batch finished; no trace)"
+    out["seconds_per_epoch"] = round(per_epoch, 7)
+    ctx.reset()
+    e = graph_leg.get("epochs")
+    out["epochs"] = e
+    if e is not None:
+        out["seconds"] = round(e * per_epoch, 6)
+    else:
+        out["seconds_for_max_epochs"] = round(graph_leg["max_epochs"] * per_epoch, 6)
     return out
 
 
