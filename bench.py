@@ -244,27 +244,60 @@ def run_ours(args, W):
     kernels = {k: {"launches": c, "avg_us": (ms * 1e3 / c) if c else None} for k, (c, ms) in prof.items()}
 
     # ---- end to end through the C ABI with host buffers: every step uploads
-    # its gated data from pinned memory, runs one epoch and reads x back; the
-    # upload of step k + 1 is staged while step k runs (mc_stage_data, then
-    # mc_commit_data), the first upload inside the timed region as well
+    # its gated data from pinned memory, runs one epoch and reads x back to
+    # pinned memory.  Steps are pipelined as a streaming caller would: the
+    # upload of step k + 1 is staged while step k runs (mc_stage_data) and
+    # committed (mc_commit_data) right after step k is enqueued, and x_k is
+    # copied to the host asynchronously and waited for one step later; the
+    # first upload and the last read-back are inside the timed region.
     d_host = d.cpu().pin_memory()
-    x_host = torch.empty((W.n, W.n), dtype=torch.float32).pin_memory()
-    for _ in range(2):
+    x_host = [torch.empty((W.n, W.n), dtype=torch.float32).pin_memory() for _ in range(2)]
+    x_dev = torch.empty((W.n, W.n), dtype=torch.float32, device="cuda")
+    cs = ctx.stream
+
+    def e2e_steps(steps, sync_each):
         ctx.stage_data(d_host)
         ctx.commit_data(W.alpha)
-        ctx.spdhg_run(1, seed=sd["gates"], x_out=x_host)
+        evs = []
+        for k in range(steps):
+            if sync_each:
+                if k + 1 < steps:
+                    ctx.stage_data(d_host)
+                ctx.spdhg_run(1, seed=sd["gates"], x_out=x_host[0])
+                if k + 1 < steps:
+                    ctx.commit_data(W.alpha)
+                continue
+            if k + 1 < steps:
+                ctx.stage_data(d_host)
+            ctx.spdhg_run(1, seed=sd["gates"], x_out=x_dev)
+            with torch.cuda.stream(cs):
+                x_host[k % 2].copy_(x_dev, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(cs)
+            evs.append(ev)
+            if k + 1 < steps:
+                ctx.commit_data(W.alpha)
+            if k >= 1:
+                evs[k - 1].synchronize()
+        if evs:
+            evs[-1].synchronize()
+
+    e2e_steps(2, False)
+    e2e_steps(2, True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ctx.stage_data(d_host)
-    for k in range(args.steps):
-        ctx.commit_data(W.alpha)
-        if k + 1 < args.steps:
-            ctx.stage_data(d_host)
-        ctx.spdhg_run(1, seed=sd["gates"], x_out=x_host)
+    e2e_steps(args.steps, False)
     e2e_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps(args.steps, True)
+    e2e_sync_s = time.perf_counter() - t0
     e2e = {"value": args.steps * N * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(d_host.numel() * 4), "d2h_bytes_per_step": int(x_host.numel() * 4),
-           "upload": "next step's data staged during the current epoch (mc_stage_data / mc_commit_data)"}
+           "h2d_bytes_per_step": int(d_host.numel() * 4), "d2h_bytes_per_step": int(x_dev.numel() * 4),
+           "pipeline": "step k+1's data uploaded (mc_stage_data) while step k runs and committed right after "
+                       "step k is enqueued; x_k copied to pinned host memory asynchronously and waited for "
+                       "during step k+1",
+           "value_one_step_at_a_time": round(args.steps * N * world / e2e_sync_s, 2)}
 
     # ---- roofline of the dominant kernel (on-chip gather bytes per unit of work)
     S_cnt = algorithmic_units(W)
@@ -319,6 +352,10 @@ def run_ours(args, W):
     if args.batch_slices > 0:
         out["batch_mixed_slices"] = batch_legs(args.batch_slices, args.batch_epochs, args.batch_seq_epochs,
                                                not args.batch_no_autotune)
+        # the same recipe with every slice at the smallest side, where one
+        # slice's launches leave most of the GPU idle
+        out["batch_small_slices"] = batch_legs(args.batch_slices, args.batch_epochs, args.batch_seq_epochs,
+                                               not args.batch_no_autotune, sides=(256,))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(W, samples=args.cpu_pairs)
         out["cpu_baseline_more"] = cpu_baseline_more(W)
@@ -327,6 +364,41 @@ def run_ours(args, W):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_ncu_batch_case(args):
+    """Kernel-profiling driver of the merged batched path: --ncu-batch slices
+    of the mixed recipe (one of each side first), data A_i x, a fixed squared
+    norm, then warm-up + timed batched epochs (mc_batch_run)."""
+    import torch
+
+    import paper_2410_10503_gb300 as mc
+    from paper_2410_10503_gb300 import build
+    build.build()
+    ctxs, seeds = [], []
+    for W in S.slice_batch(args.ncu_batch):
+        sd = S.seeds(W.cid)
+        if W.motion == "rigid":
+            kw = dict(rigid=S.rigid_motion(W.n_gates, W.max_rot_deg, W.max_shift, sd["motion"]))
+        else:
+            kw = dict(fields=S.rbf_fields(W.n, W.n_gates, sd["motion"], W.rbf_count, W.rbf_width,
+                                          W.rbf_max_disp))
+        ctx = mc.Context(W.n, W.n_angles, W.n_bins, W.n_gates, **kw)
+        xt = torch.as_tensor(S.phantom(W.n, W.n_ellipses, sd["phantom"], W.axis_lo, W.axis_hi),
+                             dtype=torch.float32, device="cuda")
+        d = torch.stack([ctx.forward(i, xt) for i in range(W.n_gates)])
+        ctx.set_data(d, W.alpha)
+        ctx.set_norms(np.full(W.n_gates + 1, 1.4 * W.n_angles * W.n))
+        ctxs.append(ctx)
+        seeds.append(sd["gates"])
+    b = mc.Batch(ctxs)
+    for _ in range(args.warmup + args.steps):
+        b.run(1, seeds)
+    torch.cuda.synchronize()
+    b.close()
+    for c in ctxs:
+        c.close()
+    print(json.dumps({"ncu_batch_case": args.ncu_batch, "epochs": args.warmup + args.steps}))
 
 
 def run_ncu_case(args, W):
@@ -560,7 +632,7 @@ def storage_legs(max_epochs, steps=20):
     return out
 
 
-def batch_legs(count, epochs, seq_epochs, autotune=True):
+def batch_legs(count, epochs, seq_epochs, autotune=True, sides=None):
     """The batched-slices workload: `count` independent slices of mixed size
     (mc_synth.slice_batch: sides 256-1024, angles round(1.4 side), bins
     side + 17, gates U{4..32}, rigid and dense-field motion alternating;
@@ -575,7 +647,7 @@ def batch_legs(count, epochs, seq_epochs, autotune=True):
 
     import paper_2410_10503_gb300 as mc
     t_setup = time.perf_counter()
-    ws = S.slice_batch(count)
+    ws = S.slice_batch(count) if sides is None else S.slice_batch(count, sides=sides)
     ctxs, seeds, tunes = [], [], []
     for W in ws:
         sd = S.seeds(W.cid)
@@ -829,12 +901,16 @@ def main():
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling driver: set up the workload, then only warm-up + timed "
                          "epochs as plain launches (no norms, e2e, profile or CPU legs)")
+    ap.add_argument("--ncu-batch", type=int, default=0,
+                    help="with --ncu-case: profile the merged batched path on this many mixed slices")
     ap.add_argument("--subsets", type=int, default=1,
                     help="--ncu-case only: sample gates x this many angle subsets")
     args = ap.parse_args()
     W = S.WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, W)
+    elif args.ncu_case and args.ncu_batch > 0:
+        run_ncu_batch_case(args)
     elif args.ncu_case:
         run_ncu_case(args, W)
     else:
