@@ -287,6 +287,11 @@ mc_status mc_reset(mc_ctx* ctx);
  * trace (nullable, epochs x 3 doubles): per epoch
  * {||x - x*||/||x*||, ||x - x*||^2 + sum_i ||y_i - y_i*||^2, O(x)}; NaN where the
  * reference is unset or MC_OPT_TRACE_OBJECTIVE is off.
+ * With a host x_out or trace the call returns after they have reached host
+ * memory and reports a device-side failure of the run (MC_ETIMEOUT).  With
+ * device (or no) outputs it returns without waiting: the run's error word is
+ * then checked by a later mc_spdhg_run / mc_pdhg_run (as soon as the run has
+ * finished) or by mc_sync.
  * MC_ESTATE if data or step sizes are missing. */
 mc_status mc_spdhg_run(mc_ctx* ctx, int32_t epochs, const mc_sampling* sampling,
                        float* x_out, double* trace);
@@ -325,7 +330,14 @@ mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
  *
  * mc_batch_create groups `count` contexts (same device, angle subsets = 1),
  * orders work on cuda_stream (NULL: a stream of the batch's own) and keeps
- * pointers to the contexts: destroy the batch before any of them.
+ * pointers to the contexts: destroy the batch before any of them.  It also
+ * cuts each slice's forward work into its own coarser items where the
+ * slice's share of a merged launch is small (a block then streams the
+ * slice's image once for more ray groups); these serve while the slices in
+ * flight give every SM at least four such blocks, the slices' own items
+ * otherwise (results do not depend on the cut).  Launch shapes changed after
+ * creation (mc_autotune, mc_set_subsets) make mc_batch_run return MC_ESTATE:
+ * create the batch again.
  * mc_batch_run runs `epochs` SPDHG epochs of every slice (slice i: epochs x
  * N_i iterations, sampling[i] as in mc_spdhg_run, p included); slices with
  * fewer gates finish first and leave the launches.  Per slice the result is
@@ -369,6 +381,10 @@ mc_status mc_profile_reset(mc_ctx* ctx);
 
 /* Iteration counter k of the next SPDHG iteration (host out). */
 mc_status mc_iteration(mc_ctx* ctx, uint64_t* out);
+
+/* Wait for all work of the context and report a device-side failure of a
+ * run that returned without waiting (MC_ETIMEOUT, MC_EDEVICE), or MC_OK. */
+mc_status mc_sync(mc_ctx* ctx);
 
 /* Checkpoint and resume of the solver state (x^K, x^{K+1}, z, every y_i in
  * the current storage type, and the iteration counter k that keys the

@@ -348,6 +348,11 @@ class Context:
     def pdhg_run(self, epochs: int, x_out=None, trace=False, like=None):
         return self._run(1, epochs, 0, 0, x_out, trace, like)
 
+    def sync(self):
+        """Wait for the context's work; raises for a device-side failure of a
+        run that returned without waiting (device or no outputs)."""
+        self._check(self._L.mc_sync(self._h))
+
     def draw_gates(self, seed: int, stream: int, k0: int, count: int, out=None, p=None):
         if out is None:
             out = np.empty(count, np.int32)

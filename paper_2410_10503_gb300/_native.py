@@ -66,6 +66,7 @@ SIGNATURES = {
     "mc_profile_read": (_I32, [_VP, _I32, _VP, _VP, _VP, _VP]),
     "mc_profile_reset": (_I32, [_VP]),
     "mc_iteration": (_I32, [_VP, _VP]),
+    "mc_sync": (_I32, [_VP]),
     "mc_state_size": (_I32, [_VP, _VP]),
     "mc_save_state": (_I32, [_VP, _VP, _U64]),
     "mc_load_state": (_I32, [_VP, _VP, _U64]),

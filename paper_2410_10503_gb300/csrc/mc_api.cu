@@ -148,6 +148,9 @@ struct mc_ctx {
     int* d_gates = nullptr;
     int gates_cap = 0;
     int* d_err = nullptr;
+    int* h_err = nullptr;             // pinned copy of the error word for deferred checks
+    cudaEvent_t err_ev = nullptr;     // that copy has landed
+    bool err_pending = false;         // a deferred check is outstanding
     int* d_draw_out = nullptr;
     int draw_cap = 0;
     uint64_t k_host = 0;
@@ -352,6 +355,50 @@ mc_status check_err_word(mc_ctx* c)
         CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
         if (h == kErrTimeout) return fail(c, MC_ETIMEOUT, "a device-side wait ran out of polls");
         return fail(c, MC_EDEVICE, "device error word %d (out-of-bounds sample)", h);
+    }
+    return MC_OK;
+}
+
+// Deferred check of the error word after a run that returns without waiting
+// (device or no outputs): the word is copied to pinned host memory behind the
+// run; poll_err reads it once that copy has landed (wait = false: only if it
+// has, so a streaming caller is never held up) and reports a failure once.
+mc_status defer_err(mc_ctx* c)
+{
+    if (!c->h_err) {
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return check_err_word(c);     // no pinned word: check now
+        }
+        c->h_err = static_cast<int*>(p);
+        *c->h_err = 0;
+    }
+    if (!c->err_ev) CK(cudaEventCreateWithFlags(&c->err_ev, cudaEventDisableTiming));
+    CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaEventRecord(c->err_ev, c->stream));
+    c->err_pending = true;
+    return MC_OK;
+}
+
+mc_status poll_err(mc_ctx* c, bool wait)
+{
+    if (!c->err_pending) return MC_OK;
+    if (wait) {
+        CK(cudaEventSynchronize(c->err_ev));
+    } else {
+        const cudaError_t q = cudaEventQuery(c->err_ev);
+        if (q == cudaErrorNotReady) return MC_OK;
+        if (q != cudaSuccess) return fail(c, MC_ECUDA, "cudaEventQuery failed: %s", cudaGetErrorString(q));
+    }
+    c->err_pending = false;
+    const int h = *c->h_err;
+    if (h != kErrNone) {
+        *c->h_err = kErrNone;
+        CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+        if (h == kErrTimeout)
+            return fail(c, MC_ETIMEOUT, "a device-side wait of an earlier run ran out of polls");
+        return fail(c, MC_EDEVICE, "device error word %d of an earlier run (out-of-bounds sample)", h);
     }
     return MC_OK;
 }
@@ -1318,6 +1365,8 @@ void mc_destroy(mc_ctx* c)
     }
     if (c->stage_ev) cudaEventDestroy(c->stage_ev);
     if (c->commit_ev) cudaEventDestroy(c->commit_ev);
+    if (c->err_ev) cudaEventDestroy(c->err_ev);
+    if (c->h_err) cudaFreeHost(c->h_err);
     for (void* p : c->allocs) cudaFree(p);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1996,6 +2045,7 @@ static mc_status run_common(mc_ctx* c, int which, int32_t epochs, const mc_sampl
                             float* x_out, double* trace)
 {
     if (!c) return MC_EINVAL;
+    TRY(poll_err(c, false));              // a failure of an earlier run that did not wait
     if (epochs < 0) return fail(c, MC_EINVAL, "epochs must be >= 0");
     if (which == 0 && !smp) return fail(c, MC_EINVAL, "sampling is NULL");
     if (!c->have_data || !c->steps_ok)
@@ -2022,11 +2072,15 @@ static mc_status run_common(mc_ctx* c, int which, int32_t epochs, const mc_sampl
         if (!dev) CK(cudaStreamSynchronize(c->stream));
     }
     if (c->prof_on) TRY(prof_collect(c));
-    if (!x_out && !trace) {
+    const bool host_out = (x_out && ptr_kind(c, x_out) == 0) || (trace && ptr_kind(c, trace) == 0);
+    if (!host_out) {
+        // device or no outputs: return without waiting; the error word is
+        // checked by a later run or by mc_sync
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return fail(c, MC_ECUDA, "CUDA error: %s", cudaGetErrorString(e));
-        return MC_OK;
+        return defer_err(c);
     }
+    TRY(poll_err(c, true));
     TRY(check_err_word(c));
     return finish(c);
 }
@@ -2285,6 +2339,15 @@ mc_status mc_iteration(mc_ctx* c, uint64_t* out)
     return MC_OK;
 }
 
+mc_status mc_sync(mc_ctx* c)
+{
+    if (!c) return MC_EINVAL;
+    CK(cudaStreamSynchronize(c->stream));
+    TRY(poll_err(c, true));
+    TRY(check_err_word(c));
+    return finish(c);
+}
+
 }  // extern "C"
 
 // ============================================================================
@@ -2298,6 +2361,7 @@ namespace {
 // the captured graph of each parity of the iteration index.
 struct BatchPhase {
     BatchBlock* d_map = nullptr;             // every map of the phase, one allocation
+    int plan = 0;                            // forward work items: 0 each slice's own, 1 the batch's
     int n_warp = 0, n_wadj = 0;
     size_t off_warp = 0, off_wadj = 0;
     struct Fwd { int lc, rpt, smem_pairs, n; size_t off; };
@@ -2318,7 +2382,16 @@ struct mc_batch {
     std::vector<int> order;                  // slices by iterations per epoch, descending
     // per-slice argument tables in the order above ([2]: parity of the iteration)
     WarpArgs* d_warp[2] = {nullptr, nullptr};
-    FwdArgs* d_fwd = nullptr;
+    FwdArgs* d_fwd[2] = {nullptr, nullptr};  // [plan]: the slice's own items, the batch's
+    // the batch's forward work items per slice (order above): coarser than a
+    // slice's own when its share of a merged launch is small, so that its
+    // blocks stream its image once for many ray groups; used while enough
+    // slices are in flight to fill the GPU (results do not depend on the cut)
+    std::vector<int2*> d_bgroups;
+    std::vector<RayItem*> d_bitems;
+    std::vector<int> b_nitems, b_rpt;
+    std::vector<char> b_owned;              // 0: the slice's own tables serve (no coarser cut)
+    std::vector<std::array<long long, 5>> shape;   // each context's tables at creation
     BpArgs* d_bp = nullptr;
     WarpAdjArgs* d_wadj[2] = {nullptr, nullptr};
     BatchDraw* d_draw = nullptr;
@@ -2355,9 +2428,18 @@ void batch_free(mc_batch* b)
         if (ph.d_map) cudaFree(ph.d_map);
     }
     b->phase.clear();
-    for (void* p : {(void*)b->d_warp[0], (void*)b->d_warp[1], (void*)b->d_fwd, (void*)b->d_bp,
-                    (void*)b->d_wadj[0], (void*)b->d_wadj[1], (void*)b->d_draw, (void*)b->d_pos})
+    for (void* p : {(void*)b->d_warp[0], (void*)b->d_warp[1], (void*)b->d_fwd[0], (void*)b->d_fwd[1],
+                    (void*)b->d_bp, (void*)b->d_wadj[0], (void*)b->d_wadj[1], (void*)b->d_draw,
+                    (void*)b->d_pos})
         if (p) cudaFree(p);
+    for (size_t q = 0; q < b->d_bgroups.size(); ++q)
+        if (q < b->b_owned.size() && b->b_owned[q]) {
+            if (b->d_bgroups[q]) cudaFree(b->d_bgroups[q]);
+            if (b->d_bitems[q]) cudaFree(b->d_bitems[q]);
+        }
+    b->b_owned.clear();
+    b->d_bgroups.clear();
+    b->d_bitems.clear();
     for (auto e : b->ev) cudaEventDestroy(e);
     b->ev.clear();
 }
@@ -2384,7 +2466,7 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
     const int B = (int)b->order.size();
     std::vector<WarpArgs> w[2];
     std::vector<WarpAdjArgs> wa[2];
-    std::vector<FwdArgs> f(B);
+    std::vector<FwdArgs> f[2] = {std::vector<FwdArgs>(B), std::vector<FwdArgs>(B)};
     std::vector<BpArgs> bp(B);
     std::vector<BatchDraw> dr(B);
     for (int t = 0; t < 2; ++t) { w[t].resize(B); wa[t].resize(B); }
@@ -2407,7 +2489,7 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
             u.tau = (float)c->sS.tau;
             u.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sS.tau * c->alpha));
         }
-        FwdArgs& a = f[q];
+        FwdArgs& a = f[0][q];
         a = FwdArgs{};
         a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
         a.ang = c->d_fang; a.groups = c->d_groups; a.items = c->d_items; a.n_items = c->n_items;
@@ -2419,6 +2501,10 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
         a.inv_den = (float)(1.0 / (1.0 + c->sS.sigma * c->N / 2.0));
         a.pf_rowptr = c->d_rowptr; a.pf_ent = c->d_ent; a.pf_ent_off = c->d_ent_off;
         a.store = c->store; a.dh = c->d_dh; a.yh = c->d_yh;
+        FwdArgs& a1 = f[1][q];
+        a1 = a;
+        a1.groups = b->d_bgroups[q]; a1.items = b->d_bitems[q]; a1.n_items = b->b_nitems[q];
+        a1.ipb = 1; a1.rpt = b->b_rpt[q];
         BpArgs& g = bp[q];
         g = BpArgs{};
         g.sel = sel;
@@ -2434,7 +2520,8 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
         BCK(cudaMemcpy(b->d_warp[t], w[t].data(), B * sizeof(WarpArgs), cudaMemcpyHostToDevice));
         BCK(cudaMemcpy(b->d_wadj[t], wa[t].data(), B * sizeof(WarpAdjArgs), cudaMemcpyHostToDevice));
     }
-    BCK(cudaMemcpy(b->d_fwd, f.data(), B * sizeof(FwdArgs), cudaMemcpyHostToDevice));
+    for (int k = 0; k < 2; ++k)
+        BCK(cudaMemcpy(b->d_fwd[k], f[k].data(), B * sizeof(FwdArgs), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->d_bp, bp.data(), B * sizeof(BpArgs), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->d_draw, dr.data(), B * sizeof(BatchDraw), cudaMemcpyHostToDevice));
     return MC_OK;
@@ -2468,7 +2555,18 @@ mc_status batch_phase(mc_batch* b, int A)
         auto r = add(q, [&](int i) { return warp_layout_tiles(C(i)->n); }, [&](int) { return 0.0; });
         ph.off_warp = r.first; ph.n_warp = r.second;
     }
-    // forward: per lines-per-chunk class; a block's work ~ samples / blocks
+    // forward: the batch's coarser work items while they still give every SM
+    // a few blocks, else each slice's own; per lines-per-chunk class; a
+    // block's work ~ samples / blocks
+    {
+        long long coarse = 0;
+        for (int i : q) coarse += b->b_nitems[i];
+        ph.plan = coarse >= 4LL * b->ctx[0]->sms ? 1 : 0;
+    }
+    auto f_blocks = [&](int i) {
+        return ph.plan ? b->b_nitems[i] : (C(i)->n_items + C(i)->ipb - 1) / C(i)->ipb;
+    };
+    auto f_rpt = [&](int i) { return ph.plan ? b->b_rpt[i] : C(i)->rpt; };
     std::vector<int> lcs;
     for (int i : q) if (std::find(lcs.begin(), lcs.end(), C(i)->lc) == lcs.end()) lcs.push_back(C(i)->lc);
     for (int lc : lcs) {
@@ -2477,13 +2575,12 @@ mc_status batch_phase(mc_batch* b, int A)
         for (int i : q)
             if (C(i)->lc == lc) {
                 qs.push_back(i);
-                rpt = std::max(rpt, C(i)->rpt);
+                rpt = std::max(rpt, f_rpt(i));
                 pairs = std::max(pairs, lc * C(i)->P);
             }
-        auto blocks = [&](int i) { return (C(i)->n_items + C(i)->ipb - 1) / C(i)->ipb; };
-        auto r = add(qs, blocks, [&](int i) {
+        auto r = add(qs, f_blocks, [&](int i) {
             const mc_ctx* c = C(i);
-            return (double)c->na * c->n * c->n / blocks(i);
+            return (double)c->na * c->n * c->n / f_blocks(i);
         });
         ph.fwd.push_back(BatchPhase::Fwd{lc, rpt, pairs, r.second, r.first});
     }
@@ -2516,7 +2613,7 @@ mc_status batch_enqueue(mc_batch* b, int A, int t)
     BCK(launch_draw_batch(b->d_draw, A, s));
     BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
     for (const auto& f : ph.fwd)
-        BCK(launch_forward_batch(b->d_fwd, ph.d_map + f.off, f.n, f.rpt, f.lc, f.smem_pairs, s));
+        BCK(launch_forward_batch(b->d_fwd[ph.plan], ph.d_map + f.off, f.n, f.rpt, f.lc, f.smem_pairs, s));
     for (const auto& g : ph.bp) BCK(launch_backproject_batch(b->d_bp, ph.d_map + g.off, g.n, g.pj, s));
     BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, s));
     return MC_OK;
@@ -2562,8 +2659,60 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream,
     for (int t = 0; t < 2 && st == MC_OK; ++t) {
         st = balloc(b, &b->d_warp[t], count);
         if (st == MC_OK) st = balloc(b, &b->d_wadj[t], count);
+        if (st == MC_OK) st = balloc(b, &b->d_fwd[t], count);
     }
-    if (st == MC_OK) st = balloc(b, &b->d_fwd, count);
+    // the batch's forward work items: about 4 blocks per SM over the whole
+    // batch, each slice's share by its samples per projection, at least as
+    // many items as its groups need (at most 24 warps x 8 slots each) and at
+    // most as many as its own plan has
+    if (st == MC_OK) {
+        const int sms = b->ctx[0]->sms;
+        double W = 0;
+        for (auto* c : b->ctx) W += (double)c->na * c->n * c->n;
+        b->d_bgroups.assign(count, nullptr);
+        b->d_bitems.assign(count, nullptr);
+        b->b_nitems.assign(count, 0);
+        b->b_rpt.assign(count, 2);
+        b->b_owned.assign(count, 0);
+        for (int q = 0; q < count; ++q) {
+            const mc_ctx* c = b->ctx[b->order[q]];
+            b->shape.push_back({(long long)(uintptr_t)c->d_items, c->n_items, c->lc, c->pj, c->rpt});
+        }
+        for (int q = 0; q < count && st == MC_OK; ++q) {
+            mc_ctx* c = b->ctx[b->order[q]];
+            const double share = (double)c->na * c->n * c->n / W;
+            const int own = (c->n_items + c->ipb - 1) / c->ipb;
+            const int target = std::max(1, std::min(own, (int)std::lround(4.0 * sms * share)));
+            if (c->ipb == 1 && 2 * target > own) {
+                // no worthwhile coarsening: the slice's own items serve
+                b->d_bgroups[q] = c->d_groups;
+                b->d_bitems[q] = c->d_items;
+                b->b_nitems[q] = c->n_items;
+                b->b_rpt[q] = c->rpt;
+                continue;
+            }
+            b->b_owned[q] = 1;
+            GroupTable gt;
+            build_groups(c, c->order, c->inv_k, c->t_k, 1, c->lc, gt);
+            std::vector<RayItem> items;
+            std::vector<int> off;
+            int ipb = 1, rpt = 2;
+            plan_forward(c, c->lc, target, 1, kPlanRounds, gt, items, off, ipb, rpt);
+            // one item per block: ipb items of the cut are ipb blocks
+            st = balloc(b, &b->d_bgroups[q], gt.groups.size());
+            if (st == MC_OK) st = balloc(b, &b->d_bitems[q], items.size());
+            if (st == MC_OK &&
+                (cudaMemcpy(b->d_bgroups[q], gt.groups.data(), gt.groups.size() * sizeof(int2),
+                            cudaMemcpyHostToDevice) != cudaSuccess ||
+                 cudaMemcpy(b->d_bitems[q], items.data(), items.size() * sizeof(RayItem),
+                            cudaMemcpyHostToDevice) != cudaSuccess)) {
+                cudaGetLastError();
+                st = MC_ECUDA;
+            }
+            b->b_nitems[q] = (int)items.size();
+            b->b_rpt[q] = rpt;
+        }
+    }
     if (st == MC_OK) st = balloc(b, &b->d_bp, count);
     if (st == MC_OK) st = balloc(b, &b->d_draw, count);
     if (st == MC_OK) st = balloc(b, &b->d_pos, count);
@@ -2616,6 +2765,15 @@ mc_status mc_batch_run(mc_batch* b, int32_t epochs, const mc_sampling* sampling,
         if (st != MC_OK) {
             if (failed) *failed = i;
             return bfail(b, st, "slice %d: %s", i, c->err.c_str());
+        }
+    }
+    for (int q = 0; q < B; ++q) {
+        const mc_ctx* c = b->ctx[b->order[q]];
+        const std::array<long long, 5> now{(long long)(uintptr_t)c->d_items, c->n_items, c->lc, c->pj, c->rpt};
+        if (now != b->shape[q]) {
+            if (failed) *failed = b->order[q];
+            return bfail(b, MC_ESTATE, "slice %d: its launch shapes changed after mc_batch_create "
+                                      "(mc_autotune or mc_set_subsets); create the batch again", b->order[q]);
         }
     }
     if (epochs == 0) return MC_OK;

@@ -169,3 +169,19 @@ def test_merged_batch_reports_the_failing_slice(mc, merged_slices):
     sub = make_ctx(mc, P, O.block_norms2(P, 2, iters=10, tol=1e-8), subsets=2)
     with pytest.raises(mc.MCError):
         mc.Batch([good, sub])
+
+
+def test_merged_batch_refuses_changed_launch_shapes(mc, merged_slices):
+    W, P, sd, nrm = merged_slices[1]
+    a = make_ctx(mc, P, nrm)
+    W2, P2, sd2, nrm2 = merged_slices[2]
+    c = make_ctx(mc, P2, nrm2)
+    with mc.Batch([a, c]) as b:
+        b.run(1, seeds=[1, 2])
+        a.autotune(reps=1)                  # new forward tables after the batch was made
+        with pytest.raises(mc.MCError, match="launch shapes"):
+            b.run(1, seeds=[1, 2])
+    with mc.Batch([a, c]) as b:             # a new batch takes them
+        b.run(1, seeds=[1, 2])
+    a.close()
+    c.close()

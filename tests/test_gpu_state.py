@@ -136,3 +136,25 @@ def test_bounded_wait_running_out_is_reported_and_the_context_recovers(mc, prob,
     ctx.reset()
     x, _ = ctx.spdhg_run(3, seed=sd["gates"])
     np.testing.assert_array_equal(x, ref)
+
+
+def test_wait_running_out_in_a_run_that_did_not_wait_is_reported_later(mc, prob):
+    """A run with device (or no) outputs returns without waiting; a bounded
+    wait that ran out in it is reported by mc_sync (and only once), and the
+    reset context reproduces an undisturbed run."""
+    from paper_2410_10503_gb300 import _native as N
+    W, P, sd, norms = prob
+    ref_ctx = make(mc, W, P, norms)
+    ref, _ = ref_ctx.spdhg_run(2, seed=sd["gates"])
+    ctx = make(mc, W, P, norms)
+    ctx.set_option(N.MC_OPT_TEST_STALL, 1)
+    x_dev = torch.empty((W.n, W.n), dtype=torch.float32, device="cuda")
+    ctx.spdhg_run(1, seed=sd["gates"], x_out=x_dev)          # returns without waiting
+    with pytest.raises(mc.MCError) as e:
+        ctx.sync()
+    assert "MC_ETIMEOUT" in str(e.value)
+    ctx.sync()                                               # reported once
+    ctx.reset()
+    ctx.spdhg_run(2, seed=sd["gates"], x_out=x_dev)
+    ctx.sync()
+    np.testing.assert_array_equal(x_dev.cpu().numpy(), ref)
