@@ -321,10 +321,10 @@ mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
  * of all those slices: the gate draw (each slice's Philox counter and epoch
  * position on the device), the warp D_i, the Joseph forward with the fused
  * dual update, the backprojection and the transpose warp with the fused
- * z / zbar / prox update.  The forward and the backprojection are compiled
- * per launch shape, so slices with different lines per chunk or rows per
- * thread (mc_autotune) add one launch of that stage per distinct shape.
- * Block lists put the slices with the most work per block first.  Each
+ * z / zbar / prox update: five launches per batched iteration whatever the
+ * slices' launch shapes (each block runs with its slice's lines per chunk and
+ * rows per thread).  Block lists put the slices with the most work per block
+ * first.  Each
  * batched iteration is captured once as a CUDA graph per set of slices in
  * flight and parity of the iteration index, and replayed.
  *

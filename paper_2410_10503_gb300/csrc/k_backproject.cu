@@ -156,8 +156,11 @@ __device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long
 
 #endif
 
+// pj: the rows of this launch's tiles (even, <= PJ); the register arrays are
+// sized for PJ and rows j >= pj are skipped, so one PJ = 16 instance serves
+// slices of every tile height with the arithmetic of the PJ = pj instance.
 template <int PJ, bool SUB>
-__device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int slot)
+__device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int slot, int pj)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);                             // [kGroups][kRing]
@@ -167,13 +170,13 @@ __device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int sl
     const int n = a.n;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int c0 = bx * 32, c = c0 + lane;
-    const int r0 = by * PJ;
+    const int r0 = by * pj;
     const float h = 0.5f * (float)(n - 1);
     const float le = (float)min(lane, n - 1 - c0);       // column offset in the tile (clamped at the edge)
     const float2* dys = a.dy + slot * a.dy_stride;
     // tile extent in centred coordinates (columns past the image are clamped)
     const float X0 = (float)c0 - h, xmax = (float)min(c0 + 31, n - 1) - h;   // exact
-    const float Y0 = (float)r0 - h, ymax = Y0 + (float)(PJ - 1);
+    const float Y0 = (float)r0 - h, ymax = Y0 + (float)(pj - 1);
     // angles of this launch: one angle subset of the drawn block, or all;
     // this warp takes the subset's angles g, g + kGroups, ...
     const int S = SUB ? a.sel.subsets : 1;
@@ -241,6 +244,7 @@ __device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int sl
 #endif
 #pragma unroll
             for (int j = 0; j < PJ; j += 2) {
+                if (j >= pj) break;
                 float dx, dy;
 #ifdef MC_CHECKED
                 float2 y0, y1;
@@ -278,7 +282,7 @@ __device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int sl
 #pragma unroll
     for (int j = 0; j < PJ; ++j) s_red[(g * PJ + j) * 32 + lane] = acc[j];
     __syncthreads();
-    for (int j = g; j < PJ; j += kGroups) {
+    for (int j = g; j < pj; j += kGroups) {
         float v = 0.0f;
 #pragma unroll
         for (int q = 0; q < kGroups; ++q) v += s_red[(q * PJ + j) * 32 + lane];
@@ -292,11 +296,11 @@ __global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
 {
     pdl_wait();
     pdl_trigger();
-    bp_block<PJ, SUB>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+    bp_block<PJ, SUB>(a, blockIdx.x, blockIdx.y, blockIdx.z, PJ);
 }
 
-// Batched: the tiles of every slice of the launch (all angles, one slot).
-template <int PJ>
+// Batched: the tiles of every slice of the launch (all angles, one slot),
+// each slice with its own tile height a.pj <= 16.
 __global__ void __launch_bounds__(256, 4) k_backproject_batch(const BpArgs* __restrict__ args,
                                                               const BatchBlock* __restrict__ map)
 {
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(256, 4) k_backproject_batch(const BpArgs* __re
     const BatchBlock m = map[blockIdx.x];
     const BpArgs& a = args[m.slice];
     const int tx = (a.n + 31) / 32;
-    bp_block<PJ, false>(a, m.block % tx, m.block / tx, 0);
+    bp_block<16, false>(a, m.block % tx, m.block / tx, 0, a.pj);
 }
 
 }  // namespace
@@ -328,27 +332,21 @@ cudaError_t backproject_prepare()
 #define MC_BP_ATTR(P, B)                                                                   \
     if (e == cudaSuccess)                                                                 \
         e = cudaFuncSetAttribute(k_backproject<P, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)backproject_smem_bytes(P));                         \
-    if (e == cudaSuccess && !B)                                                           \
-        e = cudaFuncSetAttribute(k_backproject_batch<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  (int)backproject_smem_bytes(P));
     MC_BP_INSTANCES(MC_BP_ATTR)
 #undef MC_BP_ATTR
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_backproject_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)backproject_smem_bytes(16));
     return e;
 }
 
 int backproject_tiles(int n, int pj) { return ((n + 31) / 32) * ((n + pj - 1) / pj); }
 
-cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
-                                     cudaStream_t s)
+cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    const size_t smem = backproject_smem_bytes(pj);
-#define MC_BPB_LAUNCH(P, B)                                                              \
-    if (!B && pj == P) return pdl_launch(k_backproject_batch<P>, dim3(nblocks), dim3(256), smem, s, args, map);
-    MC_BP_INSTANCES(MC_BPB_LAUNCH)
-#undef MC_BPB_LAUNCH
-    return cudaErrorInvalidValue;
+    return pdl_launch(k_backproject_batch, dim3(nblocks), dim3(256), backproject_smem_bytes(16), s, args, map);
 }
 
 cudaError_t launch_backproject(const BpArgs& a_in, cudaStream_t s)

@@ -255,14 +255,13 @@ struct SlotRec {
 // slot `slot`; nbx = blocks sharing the table (the CSR prefetch is split
 // among them).
 template <int RPT, int LC, bool BANDED>
-__device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot, int nbx)
+__device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot, int nbx, SlotState* s_slot,
+                                              SlotRec* s_rec)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
     uint64_t* empty = full + kStages;
     int* s_flag = reinterpret_cast<int*>(smem + 96);
-    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
-    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
     float2* stage0 = reinterpret_cast<float2*>(smem + 128);
     const size_t stage_pairs = (size_t)LC * a.P;   // one chunk: LC whole lines
 
@@ -526,23 +525,32 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
 }
 
 template <int RPT, int LC, bool BANDED>
-__global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
+__global__ void __maxnreg__(80) k_forward(FwdArgs a)
 {
     pdl_wait();
     pdl_trigger();
-    forward_block<RPT, LC, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x);
+    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
+    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
+    forward_block<RPT, LC, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
 }
 
 // Batched: the blocks of every slice of the launch, each on its slice's item
-// table with its slice's arguments (all angles, one slot, no bands).
-template <int RPT, int LC>
-__global__ void __launch_bounds__(kBlock, 1) k_forward_batch(const FwdArgs* __restrict__ args,
+// table with its slice's arguments (all angles, one slot, no bands) and its
+// own lines per chunk (8, 4 or 2: one instance of the block's body each).
+template <int RPT>
+__global__ void __maxnreg__(80) k_forward_batch(const FwdArgs* __restrict__ args,
                                                              const BatchBlock* __restrict__ map)
 {
     pdl_wait();
     pdl_trigger();
+    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
+    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
     const BatchBlock m = map[blockIdx.x];
-    forward_block<RPT, LC, false>(args[m.slice], m.block, 0, m.nblocks);
+    const FwdArgs& a = args[m.slice];
+    const int lc = a.lc;
+    if (lc == 8) forward_block<RPT, 8, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
+    else if (lc == 4) forward_block<RPT, 4, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
+    else forward_block<RPT, 2, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
 }
 
 // Sum of the bands' partial ray sums in band order, then the epilogue of
@@ -615,11 +623,11 @@ cudaError_t forward_prepare(int max_smem)
     if (e == cudaSuccess)                                                                         \
         e = cudaFuncSetAttribute(k_forward<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                  max_smem);                                                       \
-    if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward_batch<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 max_smem);
+
     MC_FWD_INSTANCES(MC_SET_ATTR)
 #undef MC_SET_ATTR
+    for (auto k : {k_forward_batch<2>, k_forward_batch<4>, k_forward_batch<8>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     return e;
 }
 
@@ -645,16 +653,14 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt, int lc,
+cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
                                  int smem_pairs, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = 128 + kStages * (size_t)smem_pairs * sizeof(float2);
-#define MC_LAUNCH_B(R, L)                                                                   \
-    if (rpt == R && lc == L)                                                                 \
-        return pdl_launch(k_forward_batch<R, L>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
-    MC_FWD_INSTANCES(MC_LAUNCH_B)
-#undef MC_LAUNCH_B
+    if (rpt == 2) return pdl_launch(k_forward_batch<2>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+    if (rpt == 4) return pdl_launch(k_forward_batch<4>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+    if (rpt == 8) return pdl_launch(k_forward_batch<8>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
     return cudaErrorInvalidValue;
 }
 

@@ -2364,10 +2364,8 @@ struct BatchPhase {
     int plan = 0;                            // forward work items: 0 each slice's own, 1 the batch's
     int n_warp = 0, n_wadj = 0;
     size_t off_warp = 0, off_wadj = 0;
-    struct Fwd { int lc, rpt, smem_pairs, n; size_t off; };
-    struct Bp { int pj, n; size_t off; };
-    std::vector<Fwd> fwd;
-    std::vector<Bp> bp;
+    int n_fwd = 0, fwd_rpt = 2, fwd_pairs = 0, n_bp = 0;
+    size_t off_fwd = 0, off_bp = 0;
     cudaGraphExec_t g[2] = {nullptr, nullptr};
 };
 
@@ -2528,11 +2526,11 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
 }
 
 // Block maps of the iteration with slices order[0 .. A-1] in flight.  Each
-// stage lists every such slice's blocks (the same blocks as its one-slice
-// launch), slices with more work per block first so that the block scheduler
-// ends the launch with the small ones; the forward and the backprojection
-// get one launch per class of their template shape (lines per chunk, rows
-// per thread).
+// stage is one launch listing every such slice's blocks (for the forward the
+// batch's coarser items while they fill the GPU, else the slice's own), slices
+// with more work per block first so that the block scheduler ends the launch
+// with the small ones; each block runs with its slice's launch shape (lines
+// per chunk, rows per thread).
 mc_status batch_phase(mc_batch* b, int A)
 {
     BatchPhase& ph = b->phase[A - 1];
@@ -2567,32 +2565,22 @@ mc_status batch_phase(mc_batch* b, int A)
         return ph.plan ? b->b_nitems[i] : (C(i)->n_items + C(i)->ipb - 1) / C(i)->ipb;
     };
     auto f_rpt = [&](int i) { return ph.plan ? b->b_rpt[i] : C(i)->rpt; };
-    std::vector<int> lcs;
-    for (int i : q) if (std::find(lcs.begin(), lcs.end(), C(i)->lc) == lcs.end()) lcs.push_back(C(i)->lc);
-    for (int lc : lcs) {
-        std::vector<int> qs;
-        int rpt = 2, pairs = 0;
-        for (int i : q)
-            if (C(i)->lc == lc) {
-                qs.push_back(i);
-                rpt = std::max(rpt, f_rpt(i));
-                pairs = std::max(pairs, lc * C(i)->P);
-            }
-        auto r = add(qs, f_blocks, [&](int i) {
+    {
+        for (int i : q) {
+            ph.fwd_rpt = std::max(ph.fwd_rpt, f_rpt(i));
+            ph.fwd_pairs = std::max(ph.fwd_pairs, C(i)->lc * C(i)->P);
+        }
+        auto r = add(q, f_blocks, [&](int i) {
             const mc_ctx* c = C(i);
             return (double)c->na * c->n * c->n / f_blocks(i);
         });
-        ph.fwd.push_back(BatchPhase::Fwd{lc, rpt, pairs, r.second, r.first});
+        ph.off_fwd = r.first; ph.n_fwd = r.second;
     }
-    // backprojection: per rows-per-thread class; a tile's work ~ angles
-    std::vector<int> pjs;
-    for (int i : q) if (std::find(pjs.begin(), pjs.end(), C(i)->pj) == pjs.end()) pjs.push_back(C(i)->pj);
-    for (int pj : pjs) {
-        std::vector<int> qs;
-        for (int i : q) if (C(i)->pj == pj) qs.push_back(i);
-        auto r = add(qs, [&](int i) { return backproject_tiles(C(i)->n, pj); },
-                     [&](int i) { return (double)C(i)->na; });
-        ph.bp.push_back(BatchPhase::Bp{pj, r.second, r.first});
+    // backprojection: each slice's own tile height; a tile's work ~ angles x rows
+    {
+        auto r = add(q, [&](int i) { return backproject_tiles(C(i)->n, C(i)->pj); },
+                     [&](int i) { return (double)C(i)->na * C(i)->pj; });
+        ph.off_bp = r.first; ph.n_bp = r.second;
     }
     // transpose warp and update: 256 pixels per block
     {
@@ -2612,9 +2600,8 @@ mc_status batch_enqueue(mc_batch* b, int A, int t)
     cudaStream_t s = b->stream;
     BCK(launch_draw_batch(b->d_draw, A, s));
     BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
-    for (const auto& f : ph.fwd)
-        BCK(launch_forward_batch(b->d_fwd[ph.plan], ph.d_map + f.off, f.n, f.rpt, f.lc, f.smem_pairs, s));
-    for (const auto& g : ph.bp) BCK(launch_backproject_batch(b->d_bp, ph.d_map + g.off, g.n, g.pj, s));
+    BCK(launch_forward_batch(b->d_fwd[ph.plan], ph.d_map + ph.off_fwd, ph.n_fwd, ph.fwd_rpt, ph.fwd_pairs, s));
+    BCK(launch_backproject_batch(b->d_bp, ph.d_map + ph.off_bp, ph.n_bp, s));
     BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, s));
     return MC_OK;
 }

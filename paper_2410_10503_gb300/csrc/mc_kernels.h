@@ -163,10 +163,10 @@ struct FwdArgs {
 };
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 // batched (all angles, one slot per slice, no bands): block b runs block
-// map[b].block of slice map[b].slice's item table; every slice of the launch
-// has lines per chunk lc and at most rpt group slots per warp; smem_pairs =
-// the largest lc x P of the launch's slices
-cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt, int lc,
+// map[b].block of slice map[b].slice's item table with that slice's lines per
+// chunk (args[slice].lc: 8, 4 or 2); every slice of the launch has at most rpt
+// group slots per warp; smem_pairs = the largest lc x P of the launch's slices
+cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
                                  int smem_pairs, cudaStream_t s);
 int forward_groups_per_block(int rpt);
 int forward_consumer_warps();         // consumer warps per block
@@ -190,10 +190,10 @@ struct BpArgs {
     int wl;                    // staged window length (pairs), set by the launcher
 };
 cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
-// batched (all angles, one slot per slice): every slice of the launch has pj
-// rows per thread; block b works on tile map[b].block of slice map[b].slice
-cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
-                                     cudaStream_t s);
+// batched (all angles, one slot per slice): block b works on tile
+// map[b].block of slice map[b].slice, with that slice's rows per thread
+// (args[slice].pj, any of 4, 8, 14, 16) and window length (args[slice].wl)
+cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, cudaStream_t s);
 int backproject_tiles(int n, int pj);
 int backproject_window(int pj);
 cudaError_t backproject_prepare();
