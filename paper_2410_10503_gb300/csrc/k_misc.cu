@@ -262,6 +262,30 @@ cudaError_t launch_cg_step2(float* p, const float* r, size_t len, const double* 
     return cudaGetLastError();
 }
 
+// Zero up to kZeroSegs buffers in one launch (the solver-state reset):
+// 16-byte stores where a segment allows them, a byte tail otherwise.
+__global__ void __launch_bounds__(256) k_zero_segments(ZeroSegs z)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int k = 0; k < z.count; ++k) {
+        unsigned char* p = static_cast<unsigned char*>(z.ptr[k]);
+        const size_t bytes = z.bytes[k];
+        const size_t n16 = ((uintptr_t)p & 15) ? 0 : bytes / 16;
+        for (size_t i = t0; i < n16; i += stride) reinterpret_cast<uint4*>(p)[i] = make_uint4(0, 0, 0, 0);
+        for (size_t i = n16 * 16 + t0; i < bytes; i += stride) p[i] = 0;
+    }
+}
+
+cudaError_t launch_zero_segments(const ZeroSegs& z, cudaStream_t s)
+{
+    size_t tot = 0;
+    for (int k = 0; k < z.count; ++k) tot += z.bytes[k];
+    const int blocks = (int)std::min<size_t>(4096, std::max<size_t>(1, (tot / 16 + 255) / 256));
+    k_zero_segments<<<blocks, 256, 0, s>>>(z);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;

@@ -139,7 +139,7 @@ __device__ __forceinline__ void prefetch_csr(const FwdArgs& a, int gate, int par
 }
 
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up (unless the launch sets one)
-constexpr int kConsumers = 24;               // consumer warps per block
+constexpr int kConsumers = 23;               // consumer warps per block (24 warps in all: 6 per scheduler)
 constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
 constexpr int kBlock = kThreads + 32;        // plus one producer warp
 constexpr int kStages = 5;
@@ -525,7 +525,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
 }
 
 template <int RPT, int LC, bool BANDED>
-__global__ void __maxnreg__(80) k_forward(FwdArgs a)
+__global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 {
     pdl_wait();
     pdl_trigger();
@@ -538,7 +538,7 @@ __global__ void __maxnreg__(80) k_forward(FwdArgs a)
 // table with its slice's arguments (all angles, one slot, no bands) and its
 // own lines per chunk (8, 4 or 2: one instance of the block's body each).
 template <int RPT>
-__global__ void __maxnreg__(80) k_forward_batch(const FwdArgs* __restrict__ args,
+__global__ void __launch_bounds__(kBlock, 1) k_forward_batch(const FwdArgs* __restrict__ args,
                                                              const BatchBlock* __restrict__ map)
 {
     pdl_wait();
@@ -606,7 +606,9 @@ int forward_consumer_warps() { return kConsumers; }
 
 int forward_ring_stages() { return kStages; }
 
-int forward_static_smem() { return (int)(kConsumers * 8 * (sizeof(SlotState) + sizeof(SlotRec))); }
+// static shared memory of the largest instance: the slot tables plus room for
+// the alignment padding the compiler may place between them
+int forward_static_smem() { return (int)(kConsumers * 8 * (sizeof(SlotState) + sizeof(SlotRec))) + 256; }
 
 size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }
 

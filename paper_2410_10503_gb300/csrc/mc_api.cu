@@ -1450,12 +1450,16 @@ mc_status mc_reset(mc_ctx* c)
 {
     if (!c) return MC_EINVAL;
     const size_t n2 = (size_t)c->n * c->n, ns = (size_t)c->na * c->nb;
-    CK(cudaMemsetAsync(c->d_x[0], 0, n2 * sizeof(float), c->stream));
-    CK(cudaMemsetAsync(c->d_x[1], 0, n2 * sizeof(float), c->stream));
-    CK(cudaMemsetAsync(c->d_z, 0, n2 * sizeof(float), c->stream));
-    CK(cudaMemsetAsync(c->d_y, 0, (size_t)c->N * ns * sizeof(float), c->stream));
-    if (c->d_yh) CK(cudaMemsetAsync(c->d_yh, 0, (size_t)c->N * ns * sizeof(unsigned short), c->stream));
-    CK(cudaMemsetAsync(c->d_k, 0, sizeof(unsigned long long), c->stream));
+    // x^k, x^{k+1}, z, y (and its reduced-precision copy), the iteration counter: one launch
+    ZeroSegs zs{};
+    auto seg = [&](void* p, size_t bytes) { zs.ptr[zs.count] = p; zs.bytes[zs.count++] = bytes; };
+    seg(c->d_x[0], n2 * sizeof(float));
+    seg(c->d_x[1], n2 * sizeof(float));
+    seg(c->d_z, n2 * sizeof(float));
+    seg(c->d_y, (size_t)c->N * ns * sizeof(float));
+    if (c->d_yh) seg(c->d_yh, (size_t)c->N * ns * sizeof(unsigned short));
+    seg(c->d_k, sizeof(unsigned long long));
+    TRY(launch(c, C_MISC, "reset", [&] { return launch_zero_segments(zs, c->stream); }));
     c->cur = 0;
     c->k_host = 0;
     return finish(c);

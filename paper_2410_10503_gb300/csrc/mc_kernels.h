@@ -226,6 +226,14 @@ cudaError_t launch_trace_combine(const double* dx2, const double* xs2, const dou
 cudaError_t launch_objective_combine(const double* xx, const double* res, int n_res,
                                      double alpha, int N, double* out, cudaStream_t s);
 cudaError_t launch_fill_nan(double* p, int count, cudaStream_t s);
+// zero several buffers in one launch
+constexpr int kZeroSegs = 8;
+struct ZeroSegs {
+    void* ptr[kZeroSegs];
+    size_t bytes[kZeroSegs];
+    int count;
+};
+cudaError_t launch_zero_segments(const ZeroSegs& z, cudaStream_t s);
 // storage conversions (store 1 binary16, 2 bfloat16; round to nearest even)
 cudaError_t launch_to_store(const float* src, unsigned short* dst, size_t len, int store, cudaStream_t s);
 cudaError_t launch_from_store(const unsigned short* src, float* dst, size_t len, int store, cudaStream_t s);
