@@ -295,7 +295,7 @@ def run_ours(args, W):
     e2e_steps(args.steps, True)
     e2e_sync_s = time.perf_counter() - t0
     e2e = {"value": args.steps * N * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": int(d_host.numel() * 4), "d2h_bytes_per_step": int(x_dev.numel() * 4),
+           "h2d_bytes_per_step": int(d_host.numel() * 4), "d2h_bytes_per_step": int(x_dev[0].numel() * 4),
            "pipeline": "step k+1's data uploaded (mc_stage_data) while step k runs and committed right after "
                        "step k is enqueued; x_k copied to pinned host memory on a side stream while step k+1 "
                        "runs and waited for during step k+1",

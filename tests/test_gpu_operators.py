@@ -224,3 +224,15 @@ def test_autotune_keeps_parity(mc):
     fresh = mc.Context(n, na, nb, N, rigid=rig)
     if t["lines_per_chunk"] == 8:
         np.testing.assert_array_equal(host(ctx.forward(1, cuda(x))), host(fresh.forward(1, cuda(x))))
+
+
+def test_shared_load_peak_is_plausible(mc):
+    """mc_measure_shared_load_peak: conflict-free 64-bit shared loads deliver
+    at most the data path's 128 B per clock per SM, and a healthy GPU gets
+    close to it; the clock it reports matches bytes/s over bytes/clk."""
+    r = mc.shared_load_peak(reps=4)
+    assert r is not None
+    assert 96.0 <= r["bytes_per_clk_per_sm"] <= 130.0, r
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ghz = r["bytes_per_s"] / (r["bytes_per_clk_per_sm"] * sms) / 1e9
+    assert abs(ghz - r["sm_ghz"]) <= 0.05 * r["sm_ghz"], r
