@@ -9,8 +9,9 @@
 // wavefronts, no conflict), and packs the loaded pairs into one add.f32x2 per
 // load so that the loads cannot be dropped and issue stays far below the
 // load pipe's rate.  Two blocks of 1024 threads per SM keep all of them
-// resident at once; each block records its clock64 span, so the result is
-// given both per second (CUDA events) and per SM clock.
+// resident at once; each block records its clock64 start and end and its SM,
+// so the result is given both per second (CUDA events) and per SM clock (an
+// SM's blocks' loads over the span of that SM's clock they covered).
 #include <algorithm>
 #include <vector>
 
@@ -53,7 +54,13 @@ __global__ void __launch_bounds__(kPeakThreads, 2) k_smem_peak(int reps, float* 
     float lo, hi;
     asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc));
     if (lo + hi == -1.0f) sink[blockIdx.x] = lo;   // never true; keeps the loads
-    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        cycles[3 * blockIdx.x] = t0;                // the SM's own clock: compared only
+        cycles[3 * blockIdx.x + 1] = t1;            // with blocks on the same SM
+        cycles[3 * blockIdx.x + 2] = smid;
+    }
 }
 
 }  // namespace
@@ -76,7 +83,7 @@ extern "C" mc_status mc_measure_shared_load_peak(int32_t reps, double* out)
         return e == cudaSuccess;
     };
     if (ck(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) && ck(cudaMalloc(&sink, blocks * sizeof(float))) &&
-        ck(cudaMalloc(&cyc, blocks * sizeof(long long))) && ck(cudaEventCreate(&e0)) && ck(cudaEventCreate(&e1))) {
+        ck(cudaMalloc(&cyc, 3 * blocks * sizeof(long long))) && ck(cudaEventCreate(&e0)) && ck(cudaEventCreate(&e1))) {
         const int inner = 128;                             // 16 KB per thread per rep: ~5 GB per rep
         // warm-up, then the timed launch
         k_smem_peak<<<blocks, kPeakThreads, 0, s>>>(inner, sink, cyc);
@@ -86,15 +93,33 @@ extern "C" mc_status mc_measure_shared_load_peak(int32_t reps, double* out)
         ck(cudaGetLastError());
         ck(cudaEventRecord(e1, s));
         float ms = 0.0f;
-        std::vector<long long> h(blocks);
+        std::vector<long long> h(3 * (size_t)blocks);
         if (ck(cudaEventSynchronize(e1)) && ck(cudaEventElapsedTime(&ms, e0, e1)) &&
-            ck(cudaMemcpy(h.data(), cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost))) {
-            const double bytes = (double)blocks * kPeakThreads * (double)inner * reps * kPeakUnroll * 8.0;
-            std::sort(h.begin(), h.end());
-            const double cyc_max = (double)h.back();
-            out[0] = bytes / (ms * 1e-3);                  // bytes per second, whole GPU
-            out[1] = bytes / sms / cyc_max;                // bytes per SM clock
-            out[2] = cyc_max / (ms * 1e-3) * 1e-9;         // SM clock seen by the kernel (GHz)
+            ck(cudaMemcpy(h.data(), cyc, 3 * blocks * sizeof(long long), cudaMemcpyDeviceToHost))) {
+            const double per_block = (double)kPeakThreads * (double)inner * reps * kPeakUnroll * 8.0;
+            const double bytes = (double)blocks * per_block;
+            // per SM: its blocks' loads over the span from the first start to
+            // the last end on that SM's clock
+            std::vector<long long> lo(sms, -1), hi(sms, -1);
+            std::vector<int> nblk(sms, 0);
+            for (int b = 0; b < blocks; ++b) {
+                const long long smid = h[3 * (size_t)b + 2];
+                if (smid < 0 || smid >= sms) continue;
+                const long long t0 = h[3 * (size_t)b], t1 = h[3 * (size_t)b + 1];
+                lo[smid] = lo[smid] < 0 ? t0 : std::min(lo[smid], t0);
+                hi[smid] = std::max(hi[smid], t1);
+                ++nblk[smid];
+            }
+            double b_sum = 0.0, c_sum = 0.0;
+            for (int m = 0; m < sms; ++m)
+                if (nblk[m] > 0 && hi[m] > lo[m]) {
+                    b_sum += nblk[m] * per_block;
+                    c_sum += (double)(hi[m] - lo[m]);
+                }
+            const int used = (int)std::count_if(nblk.begin(), nblk.end(), [](int v) { return v > 0; });
+            out[0] = bytes / (ms * 1e-3);                               // bytes per second, whole GPU
+            out[1] = c_sum > 0 ? b_sum / c_sum : 0.0;                   // bytes per SM clock
+            out[2] = used > 0 ? c_sum / used / (ms * 1e-3) * 1e-9 : 0.0; // mean SM span over event time (GHz)
         }
     }
     if (e0) cudaEventDestroy(e0);
