@@ -697,8 +697,8 @@ def batch_legs(count, epochs, seq_epochs, autotune=True, sides=None):
                        f"alpha 1e-3, 1% noise",
            "epochs_per_slice": epochs, "pairs": pairs,
            "batched_merged": {"seconds": round(bat_s, 3), "pairs_per_s": round(pairs / bat_s, 1),
-                              "launches_per_batched_iteration": "5: gate draw, warp, forward, backprojection, "
-                                                                "transpose warp, each over all slices in flight"},
+                              "launches_per_batched_iteration": "4: warp, forward, backprojection, transpose warp "
+                                                                "(+ gate draw), each over all slices in flight"},
            "one_after_another": {"epochs_per_slice": seq_epochs, "seconds": round(seq_s, 3),
                                  "pairs_per_s": round(seq_pairs / seq_s, 1)},
            "setup_s": round(setup_s, 1), "autotuned": bool(autotune)}

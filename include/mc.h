@@ -317,14 +317,17 @@ mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
  * iteration is a few small launches; slices of uneven sizes and gate counts
  * (each its own context: geometry, gates, motion kind) are therefore advanced
  * together.  One batched iteration runs one SPDHG iteration (Algorithm 1) of
- * every slice still in flight as five stages, each ONE launch over the blocks
- * of all those slices: the gate draw (each slice's Philox counter and epoch
- * position on the device), the warp D_i, the Joseph forward with the fused
- * dual update, the backprojection and the transpose warp with the fused
- * z / zbar / prox update: five launches per batched iteration whatever the
- * slices' launch shapes (each block runs with its slice's lines per chunk and
- * rows per thread).  Block lists put the slices with the most work per block
- * first.  Each
+ * every slice still in flight as four stages, each ONE launch over the blocks
+ * of all those slices: the warp D_i, the Joseph forward with the fused dual
+ * update, the backprojection and the transpose warp with the fused
+ * z / zbar / prox update, whose first block per slice also advances that
+ * slice's position in its epoch and, at an epoch's end, draws the next
+ * epoch's gates (Philox counter on the device, the one-slice draw's
+ * sequence): four launches per batched iteration whatever the slices' launch
+ * shapes (each block runs with its slice's lines per chunk and rows per
+ * thread; when all slices in flight share them, an instance compiled for
+ * them).  Block lists put the slices with the most work per block first.
+ * Each
  * batched iteration is captured once as a CUDA graph per set of slices in
  * flight and parity of the iteration index, and replayed.
  *

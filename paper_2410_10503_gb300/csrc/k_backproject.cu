@@ -312,6 +312,19 @@ __global__ void __launch_bounds__(256, 4) k_backproject_batch(const BpArgs* __re
     bp_block<16, false>(a, m.block % tx, m.block / tx, 0, a.pj);
 }
 
+// Batched, every slice of the launch with tile height PJ.
+template <int PJ>
+__global__ void __launch_bounds__(256, 4) k_backproject_batch_pj(const BpArgs* __restrict__ args,
+                                                                 const BatchBlock* __restrict__ map)
+{
+    pdl_wait();
+    pdl_trigger();
+    const BatchBlock m = map[blockIdx.x];
+    const BpArgs& a = args[m.slice];
+    const int tx = (a.n + 31) / 32;
+    bp_block<PJ, false>(a, m.block % tx, m.block / tx, 0, PJ);
+}
+
 }  // namespace
 
 int backproject_window(int pj) { return ((int)std::ceil(std::sqrt(31.0 * 31.0 + (pj - 1.0) * (pj - 1.0))) + 7) & ~1; }
@@ -338,14 +351,30 @@ cudaError_t backproject_prepare()
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_backproject_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)backproject_smem_bytes(16));
+#define MC_BPB_ATTR(P, B)                                                                 \
+    if (e == cudaSuccess && !B)                                                           \
+        e = cudaFuncSetAttribute(k_backproject_batch_pj<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)backproject_smem_bytes(P));
+    MC_BP_INSTANCES(MC_BPB_ATTR)
+#undef MC_BPB_ATTR
     return e;
 }
 
 int backproject_tiles(int n, int pj) { return ((n + 31) / 32) * ((n + pj - 1) / pj); }
 
-cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, cudaStream_t s)
+cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
+                                     cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
+    if (pj > 0) {
+#define MC_BPB_LAUNCH(P, B)                                                               \
+        if (!B && pj == P)                                                                \
+            return pdl_launch(k_backproject_batch_pj<P>, dim3(nblocks), dim3(256), backproject_smem_bytes(P), s, \
+                              args, map);
+        MC_BP_INSTANCES(MC_BPB_LAUNCH)
+#undef MC_BPB_LAUNCH
+        return cudaErrorInvalidValue;
+    }
     return pdl_launch(k_backproject_batch, dim3(nblocks), dim3(256), backproject_smem_bytes(16), s, args, map);
 }
 

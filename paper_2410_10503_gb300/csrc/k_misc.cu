@@ -37,41 +37,6 @@ __global__ void k_draw_gates(uint64_t seed, uint32_t stream, unsigned long long*
     if (kctr && threadIdx.x == 0) *kctr = (unsigned long long)(k0 + (uint64_t)count);
 }
 
-// Batched iteration: block s serves slice s.  Its epoch position advances by
-// one (mod n_blocks); at position 0 the epoch's gates are drawn exactly as
-// k_draw_gates draws them from the slice's counter, which then advances.
-__global__ void k_draw_batch(const BatchDraw* __restrict__ d)
-{
-    pdl_wait();
-    pdl_trigger();
-    const BatchDraw b = d[blockIdx.x];
-    __shared__ int s_pos;
-    if (threadIdx.x == 0) {
-        const int p = *b.pos + 1;
-        s_pos = p >= b.n_blocks ? 0 : p;
-    }
-    __syncthreads();
-    if (s_pos == 0) {
-        const uint64_t k0 = (uint64_t)*b.kctr;
-        for (int j = threadIdx.x; j < b.n_blocks; j += blockDim.x) {
-            const uint32_t w = philox_word0(b.seed, b.stream, k0 + (uint64_t)j);
-            int g;
-            if (!b.thr) {
-                g = (int)(((uint64_t)w * (uint64_t)b.n_blocks) >> 32);
-            } else {
-                g = 0;
-                while (g < b.n_blocks - 1 && (unsigned long long)w >= b.thr[g]) ++g;
-            }
-            b.gates[j] = g;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *b.pos = s_pos;
-        if (s_pos == 0) *b.kctr = *b.kctr + (unsigned long long)b.n_blocks;
-    }
-}
-
 // dy pairs (m_k y[b], m_k y[b+1]) of one sinogram; y[nb] = 0
 __global__ void k_pad_sino(const float* __restrict__ y, float2* dy, const BpAngle* ang, int na,
                            int nb, int Pb, int Gb)
@@ -195,12 +160,6 @@ cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long
 {
     return pdl_launch(k_draw_gates, dim3(1), dim3(256), 0, s, seed, stream, kctr, k0, count, n_gates, thr,
                       out);
-}
-
-cudaError_t launch_draw_batch(const BatchDraw* d, int count, cudaStream_t s)
-{
-    if (count <= 0) return cudaSuccess;
-    return pdl_launch(k_draw_batch, dim3(count), dim3(128), 0, s, d);
 }
 
 cudaError_t launch_pad_sino(const float* y, float2* dy, const BpAngle* ang, int na, int nb,

@@ -553,6 +553,20 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward_batch(const FwdArgs* __re
     else forward_block<RPT, 2, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
 }
 
+// Batched, every slice of the launch with lines per chunk LC: one compiled
+// body (the dispatching kernel above carries all three and its registers).
+template <int RPT, int LC>
+__global__ void __launch_bounds__(kBlock, 1) k_forward_batch_lc(const FwdArgs* __restrict__ args,
+                                                                const BatchBlock* __restrict__ map)
+{
+    pdl_wait();
+    pdl_trigger();
+    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
+    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
+    const BatchBlock m = map[blockIdx.x];
+    forward_block<RPT, LC, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
+}
+
 // Sum of the bands' partial ray sums in band order, then the epilogue of
 // k_forward (store, or the dual update of Algorithm 1 (ii)); one thread per
 // ray of the launch's angle subset.
@@ -630,6 +644,11 @@ cudaError_t forward_prepare(int max_smem)
 #undef MC_SET_ATTR
     for (auto k : {k_forward_batch<2>, k_forward_batch<4>, k_forward_batch<8>})
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+#define MC_SET_ATTR_B(R, L)                                                                        \
+    if (e == cudaSuccess)                                                                         \
+        e = cudaFuncSetAttribute(k_forward_batch_lc<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+    MC_FWD_INSTANCES(MC_SET_ATTR_B)
+#undef MC_SET_ATTR_B
     return e;
 }
 
@@ -656,10 +675,18 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
 }
 
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
-                                 int smem_pairs, cudaStream_t s)
+                                 int smem_pairs, int lc, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = 128 + kStages * (size_t)smem_pairs * sizeof(float2);
+    if (lc > 0) {
+#define MC_LAUNCH_B(R, L)                                                                   \
+        if (rpt == R && lc == L)                                                            \
+            return pdl_launch(k_forward_batch_lc<R, L>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+        MC_FWD_INSTANCES(MC_LAUNCH_B)
+#undef MC_LAUNCH_B
+        return cudaErrorInvalidValue;
+    }
     if (rpt == 2) return pdl_launch(k_forward_batch<2>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
     if (rpt == 4) return pdl_launch(k_forward_batch<4>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
     if (rpt == 8) return pdl_launch(k_forward_batch<8>, dim3(nblocks), dim3(kBlock), smem, s, args, map);

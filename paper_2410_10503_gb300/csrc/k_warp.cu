@@ -390,13 +390,42 @@ __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
     warp_adjoint_block<UPDATE>(a, blockIdx.x);
 }
 
-// Batched: 256 pixels of one slice per block, every slice of the launch.
+// Batched: 256 pixels of one slice per block, every slice of the launch; the
+// first warp of each slice's first block advances the slice's gate sequence
+// to the next iteration (see BatchDraw).
 __global__ void __launch_bounds__(256) k_warp_adjoint_update_batch(const WarpAdjArgs* __restrict__ args,
-                                                                   const BatchBlock* __restrict__ map)
+                                                                   const BatchBlock* __restrict__ map,
+                                                                   const BatchDraw* __restrict__ draw, int t)
 {
     pdl_wait();
     pdl_trigger();
     const BatchBlock m = map[blockIdx.x];
+    if (m.block == 0 && threadIdx.x < 32) {
+        const BatchDraw d = draw[m.slice];
+        int pos = d.state[2 * t] + 1, epar = d.state[2 * t + 1];
+        if (pos >= d.n_blocks) {
+            pos = 0;
+            epar ^= 1;
+            const uint64_t k0 = (uint64_t)*d.kctr;
+            for (int j = threadIdx.x; j < d.n_blocks; j += 32) {
+                const uint32_t w = philox_word0(d.seed, d.stream, k0 + (uint64_t)j);
+                int g;
+                if (!d.thr) {
+                    g = (int)(((uint64_t)w * (uint64_t)d.n_blocks) >> 32);
+                } else {
+                    g = 0;
+                    while (g < d.n_blocks - 1 && (unsigned long long)w >= d.thr[g]) ++g;
+                }
+                d.gates[epar * d.stride + j] = g;
+            }
+            __syncwarp();
+            if (threadIdx.x == 0) *d.kctr = (unsigned long long)(k0 + (uint64_t)d.n_blocks);
+        }
+        if (threadIdx.x == 0) {
+            d.state[2 * (t ^ 1)] = pos;
+            d.state[2 * (t ^ 1) + 1] = epar;
+        }
+    }
     warp_adjoint_block<true>(args[m.slice], m.block);
 }
 
@@ -415,10 +444,10 @@ cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s)
 int warp_adjoint_blocks(int n) { return (n * n + 255) / 256; }
 
 cudaError_t launch_warp_adjoint_update_batch(const WarpAdjArgs* args, const BatchBlock* map, int nblocks,
-                                             cudaStream_t s)
+                                             const BatchDraw* draw, int t, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    return pdl_launch(k_warp_adjoint_update_batch, dim3(nblocks), dim3(256), 0, s, args, map);
+    return pdl_launch(k_warp_adjoint_update_batch, dim3(nblocks), dim3(256), 0, s, args, map, draw, t);
 }
 
 }  // namespace mcg

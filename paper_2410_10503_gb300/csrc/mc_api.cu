@@ -2369,9 +2369,12 @@ struct BatchPhase {
     int n_warp = 0, n_wadj = 0;
     size_t off_warp = 0, off_wadj = 0;
     int n_fwd = 0, fwd_rpt = 2, fwd_pairs = 0, n_bp = 0;
+    int fwd_lc = 0, bp_pj = 0;               // > 0: every slice in flight has these (compiled shape)
     size_t off_fwd = 0, off_bp = 0;
-    cudaGraphExec_t g[2] = {nullptr, nullptr};
+    cudaGraphExec_t g[2][2] = {};            // [1 or kBatchGraphIters iterations][start parity]
 };
+
+constexpr int kBatchGraphIters = 16;         // batched iterations per replayed graph
 
 }  // namespace
 
@@ -2382,9 +2385,9 @@ struct mc_batch {
     std::string err;
     std::vector<mc_ctx*> ctx;                // caller's order
     std::vector<int> order;                  // slices by iterations per epoch, descending
-    // per-slice argument tables in the order above ([2]: parity of the iteration)
+    // per-slice argument tables in the order above ([t]: parity of the iteration index)
     WarpArgs* d_warp[2] = {nullptr, nullptr};
-    FwdArgs* d_fwd[2] = {nullptr, nullptr};  // [plan]: the slice's own items, the batch's
+    FwdArgs* d_fwd[2][2] = {};               // [plan][t]; plan: the slice's own items, the batch's
     // the batch's forward work items per slice (order above): coarser than a
     // slice's own when its share of a merged launch is small, so that its
     // blocks stream its image once for many ray groups; used while enough
@@ -2394,10 +2397,13 @@ struct mc_batch {
     std::vector<int> b_nitems, b_rpt;
     std::vector<char> b_owned;              // 0: the slice's own tables serve (no coarser cut)
     std::vector<std::array<long long, 5>> shape;   // each context's tables at creation
-    BpArgs* d_bp = nullptr;
+    BpArgs* d_bp[2] = {nullptr, nullptr};
     WarpAdjArgs* d_wadj[2] = {nullptr, nullptr};
     BatchDraw* d_draw = nullptr;
-    int* d_pos = nullptr;
+    int* d_state = nullptr;                  // per slice [2][2]: {iteration in epoch, epoch parity}
+    int* d_bgates = nullptr;                 // per slice two epochs of gates, stride gmax
+    int gmax = 1;
+    std::vector<unsigned long long> k_end;   // each slice's counter after a run (host copy source)
     std::vector<BatchPhase> phase;           // [A - 1] for A slices in flight, built on demand
     std::vector<cudaEvent_t> ev;             // one per slice (hand-off between streams) + 1
 };
@@ -2425,14 +2431,16 @@ mc_status bfail(mc_batch* b, mc_status st, const char* fmt, ...)
 void batch_free(mc_batch* b)
 {
     for (auto& ph : b->phase) {
-        for (auto& g : ph.g)
-            if (g) cudaGraphExecDestroy(g);
+        for (auto& row : ph.g)
+            for (auto& g : row)
+                if (g) cudaGraphExecDestroy(g);
         if (ph.d_map) cudaFree(ph.d_map);
     }
     b->phase.clear();
-    for (void* p : {(void*)b->d_warp[0], (void*)b->d_warp[1], (void*)b->d_fwd[0], (void*)b->d_fwd[1],
-                    (void*)b->d_bp, (void*)b->d_wadj[0], (void*)b->d_wadj[1], (void*)b->d_draw,
-                    (void*)b->d_pos})
+    for (void* p : {(void*)b->d_warp[0], (void*)b->d_warp[1], (void*)b->d_fwd[0][0], (void*)b->d_fwd[0][1],
+                    (void*)b->d_fwd[1][0], (void*)b->d_fwd[1][1], (void*)b->d_bp[0], (void*)b->d_bp[1],
+                    (void*)b->d_wadj[0], (void*)b->d_wadj[1], (void*)b->d_draw, (void*)b->d_state,
+                    (void*)b->d_bgates})
         if (p) cudaFree(p);
     for (size_t q = 0; q < b->d_bgroups.size(); ++q)
         if (q < b->b_owned.size() && b->b_owned[q]) {
@@ -2468,15 +2476,21 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
     const int B = (int)b->order.size();
     std::vector<WarpArgs> w[2];
     std::vector<WarpAdjArgs> wa[2];
-    std::vector<FwdArgs> f[2] = {std::vector<FwdArgs>(B), std::vector<FwdArgs>(B)};
-    std::vector<BpArgs> bp(B);
+    std::vector<FwdArgs> f[2][2];
+    std::vector<BpArgs> bp[2];
     std::vector<BatchDraw> dr(B);
-    for (int t = 0; t < 2; ++t) { w[t].resize(B); wa[t].resize(B); }
+    for (int t = 0; t < 2; ++t) {
+        w[t].resize(B); wa[t].resize(B); bp[t].resize(B);
+        f[0][t].resize(B); f[1][t].resize(B);
+    }
     for (int q = 0; q < B; ++q) {
         mc_ctx* c = b->ctx[b->order[q]];
-        const GateSel sel{c->d_gates, -1, 1, b->d_pos + q};
         const bool nonuni = !c->p_steps.empty();
+        int* gates = b->d_bgates + (size_t)q * 2 * b->gmax;
+        int* state = b->d_state + 4 * (size_t)q;
         for (int t = 0; t < 2; ++t) {
+            // the drawn gate of an iteration of parity t: gates[epar * gmax + pos], state[t] = {pos, epar}
+            const GateSel sel{gates, -1, 1, state + 2 * t, b->gmax};
             WarpArgs& a = w[t][q];
             a = WarpArgs{};
             a.x = c->d_x[c->cur ^ t]; a.n = c->n;
@@ -2490,41 +2504,41 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
             u.coef_tab = nonuni ? c->d_coef : nullptr;
             u.tau = (float)c->sS.tau;
             u.prox_scale = (float)(1.0 / (1.0 + 2.0 * c->sS.tau * c->alpha));
+            FwdArgs& fa = f[0][t][q];
+            fa = FwdArgs{};
+            fa.lrow = c->d_lrow; fa.lcol = c->d_lcol; fa.layout_stride = c->layout_stride; fa.P = c->P;
+            fa.ang = c->d_fang; fa.groups = c->d_groups; fa.items = c->d_items; fa.n_items = c->n_items;
+            fa.ipb = c->ipb; fa.rpt = c->rpt; fa.lc = c->lc; fa.n = c->n; fa.na = c->na; fa.nb = c->nb;
+            fa.sel = sel; fa.n_slots = 1; fa.wait_limit = 1u << 24;
+            fa.dy = c->d_dy; fa.dy_stride = c->dy_stride; fa.Pb = c->Pb; fa.Gb = c->Gb; fa.err = c->d_err;
+            fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y;
+            fa.sigma = (float)c->sS.sigma;
+            fa.inv_den = (float)(1.0 / (1.0 + c->sS.sigma * c->N / 2.0));
+            fa.pf_rowptr = c->d_rowptr; fa.pf_ent = c->d_ent; fa.pf_ent_off = c->d_ent_off;
+            fa.store = c->store; fa.dh = c->d_dh; fa.yh = c->d_yh;
+            FwdArgs& f1 = f[1][t][q];
+            f1 = fa;
+            f1.groups = b->d_bgroups[q]; f1.items = b->d_bitems[q]; f1.n_items = b->b_nitems[q];
+            f1.ipb = 1; f1.rpt = b->b_rpt[q];
+            BpArgs& g = bp[t][q];
+            g = BpArgs{};
+            g.sel = sel;
+            g.dy = c->d_dy; g.dy_stride = c->dy_stride; g.Pb = c->Pb; g.Gb = c->Gb;
+            g.ang = c->d_bang; g.n = c->n; g.na = c->na; g.nb = c->nb; g.n_slots = 1;
+            g.pj = c->pj; g.out = c->d_b; g.err = c->d_err; g.wl = backproject_window(c->pj);
+            if (g.wl > g.Pb)
+                return bfail(b, MC_EINVAL, "slice %d: backprojection window wider than its dual layout", b->order[q]);
         }
-        FwdArgs& a = f[0][q];
-        a = FwdArgs{};
-        a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
-        a.ang = c->d_fang; a.groups = c->d_groups; a.items = c->d_items; a.n_items = c->n_items;
-        a.ipb = c->ipb; a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
-        a.sel = sel; a.n_slots = 1; a.wait_limit = 1u << 24;
-        a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb; a.err = c->d_err;
-        a.mode = 1; a.d = c->d_d; a.y = c->d_y;
-        a.sigma = (float)c->sS.sigma;
-        a.inv_den = (float)(1.0 / (1.0 + c->sS.sigma * c->N / 2.0));
-        a.pf_rowptr = c->d_rowptr; a.pf_ent = c->d_ent; a.pf_ent_off = c->d_ent_off;
-        a.store = c->store; a.dh = c->d_dh; a.yh = c->d_yh;
-        FwdArgs& a1 = f[1][q];
-        a1 = a;
-        a1.groups = b->d_bgroups[q]; a1.items = b->d_bitems[q]; a1.n_items = b->b_nitems[q];
-        a1.ipb = 1; a1.rpt = b->b_rpt[q];
-        BpArgs& g = bp[q];
-        g = BpArgs{};
-        g.sel = sel;
-        g.dy = c->d_dy; g.dy_stride = c->dy_stride; g.Pb = c->Pb; g.Gb = c->Gb;
-        g.ang = c->d_bang; g.n = c->n; g.na = c->na; g.nb = c->nb; g.n_slots = 1;
-        g.pj = c->pj; g.out = c->d_b; g.err = c->d_err; g.wl = backproject_window(c->pj);
-        if (g.wl > g.Pb) return bfail(b, MC_EINVAL, "slice %d: backprojection window wider than its dual layout",
-                                      b->order[q]);
         const mc_sampling& sm = sampling[b->order[q]];
-        dr[q] = BatchDraw{sm.seed, sm.stream, c->N, c->d_k, nonuni ? c->d_thr : nullptr, c->d_gates, b->d_pos + q};
+        dr[q] = BatchDraw{sm.seed, sm.stream, c->N, c->d_k, nonuni ? c->d_thr : nullptr, gates, state, b->gmax};
     }
     for (int t = 0; t < 2; ++t) {
         BCK(cudaMemcpy(b->d_warp[t], w[t].data(), B * sizeof(WarpArgs), cudaMemcpyHostToDevice));
         BCK(cudaMemcpy(b->d_wadj[t], wa[t].data(), B * sizeof(WarpAdjArgs), cudaMemcpyHostToDevice));
+        BCK(cudaMemcpy(b->d_bp[t], bp[t].data(), B * sizeof(BpArgs), cudaMemcpyHostToDevice));
+        for (int k = 0; k < 2; ++k)
+            BCK(cudaMemcpy(b->d_fwd[k][t], f[k][t].data(), B * sizeof(FwdArgs), cudaMemcpyHostToDevice));
     }
-    for (int k = 0; k < 2; ++k)
-        BCK(cudaMemcpy(b->d_fwd[k], f[k].data(), B * sizeof(FwdArgs), cudaMemcpyHostToDevice));
-    BCK(cudaMemcpy(b->d_bp, bp.data(), B * sizeof(BpArgs), cudaMemcpyHostToDevice));
     BCK(cudaMemcpy(b->d_draw, dr.data(), B * sizeof(BatchDraw), cudaMemcpyHostToDevice));
     return MC_OK;
 }
@@ -2570,9 +2584,13 @@ mc_status batch_phase(mc_batch* b, int A)
     };
     auto f_rpt = [&](int i) { return ph.plan ? b->b_rpt[i] : C(i)->rpt; };
     {
+        ph.fwd_lc = C(q[0])->lc;
+        ph.bp_pj = C(q[0])->pj;
         for (int i : q) {
             ph.fwd_rpt = std::max(ph.fwd_rpt, f_rpt(i));
             ph.fwd_pairs = std::max(ph.fwd_pairs, C(i)->lc * C(i)->P);
+            if (C(i)->lc != ph.fwd_lc) ph.fwd_lc = 0;
+            if (C(i)->pj != ph.bp_pj) ph.bp_pj = 0;
         }
         auto r = add(q, f_blocks, [&](int i) {
             const mc_ctx* c = C(i);
@@ -2596,17 +2614,20 @@ mc_status batch_phase(mc_batch* b, int A)
     return MC_OK;
 }
 
-// Enqueue one batched iteration (parity t of the iteration index) for the
-// slices of phase A on the batch's stream.
-mc_status batch_enqueue(mc_batch* b, int A, int t)
+// Enqueue `iters` batched iterations, the first of parity t, for the slices
+// of phase A on the batch's stream: four launches each (the gate sequence
+// advances inside the last one).
+mc_status batch_enqueue(mc_batch* b, int A, int t, int iters)
 {
     BatchPhase& ph = b->phase[A - 1];
     cudaStream_t s = b->stream;
-    BCK(launch_draw_batch(b->d_draw, A, s));
-    BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
-    BCK(launch_forward_batch(b->d_fwd[ph.plan], ph.d_map + ph.off_fwd, ph.n_fwd, ph.fwd_rpt, ph.fwd_pairs, s));
-    BCK(launch_backproject_batch(b->d_bp, ph.d_map + ph.off_bp, ph.n_bp, s));
-    BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, s));
+    for (int i = 0; i < iters; ++i, t ^= 1) {
+        BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
+        BCK(launch_forward_batch(b->d_fwd[ph.plan][t], ph.d_map + ph.off_fwd, ph.n_fwd, ph.fwd_rpt, ph.fwd_pairs,
+                                 ph.fwd_lc, s));
+        BCK(launch_backproject_batch(b->d_bp[t], ph.d_map + ph.off_bp, ph.n_bp, ph.bp_pj, s));
+        BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, b->d_draw, t, s));
+    }
     return MC_OK;
 }
 
@@ -2650,8 +2671,13 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream,
     for (int t = 0; t < 2 && st == MC_OK; ++t) {
         st = balloc(b, &b->d_warp[t], count);
         if (st == MC_OK) st = balloc(b, &b->d_wadj[t], count);
-        if (st == MC_OK) st = balloc(b, &b->d_fwd[t], count);
+        if (st == MC_OK) st = balloc(b, &b->d_bp[t], count);
+        if (st == MC_OK) st = balloc(b, &b->d_fwd[0][t], count);
+        if (st == MC_OK) st = balloc(b, &b->d_fwd[1][t], count);
     }
+    for (auto* c : b->ctx) b->gmax = std::max(b->gmax, c->N);
+    if (st == MC_OK) st = balloc(b, &b->d_state, 4 * (size_t)count);
+    if (st == MC_OK) st = balloc(b, &b->d_bgates, 2 * (size_t)count * b->gmax);
     // the batch's forward work items: about 4 blocks per SM over the whole
     // batch, each slice's share by its samples per projection, at least as
     // many items as its groups need (at most 24 warps x 8 slots each) and at
@@ -2704,9 +2730,7 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream,
             b->b_rpt[q] = rpt;
         }
     }
-    if (st == MC_OK) st = balloc(b, &b->d_bp, count);
     if (st == MC_OK) st = balloc(b, &b->d_draw, count);
-    if (st == MC_OK) st = balloc(b, &b->d_pos, count);
     b->phase.resize(count);
     for (int i = 0; i <= count && st == MC_OK; ++i) {
         cudaEvent_t e = nullptr;
@@ -2777,43 +2801,62 @@ mc_status mc_batch_run(mc_batch* b, int32_t epochs, const mc_sampling* sampling,
     // for new step sizes, seeds or sampling
     BCK(cudaStreamSynchronize(b->stream));
     TRY(batch_tables(b, sampling));
-    // epoch positions: the first iteration of every slice starts an epoch
-    std::vector<int> pos(B);
+    // every slice starts an epoch: state[0] = {0, 0} and its first epoch's
+    // gates drawn into the first half from its counter, as the one-slice
+    // epoch does
+    std::vector<int> st0(4 * (size_t)B, 0);
     std::vector<long long> iters(B);
+    BCK(cudaMemcpyAsync(b->d_state, st0.data(), st0.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     for (int q = 0; q < B; ++q) {
         mc_ctx* c = b->ctx[b->order[q]];
-        pos[q] = c->N - 1;
         iters[q] = (long long)epochs * c->N;
+        const mc_sampling& sm = sampling[b->order[q]];
+        BCK(launch_draw_gates(sm.seed, sm.stream, c->d_k, 0, c->N, c->N, c->p_steps.empty() ? nullptr : c->d_thr,
+                              b->d_bgates + (size_t)q * 2 * b->gmax, b->stream));
     }
-    BCK(cudaMemcpyAsync(b->d_pos, pos.data(), B * sizeof(int), cudaMemcpyHostToDevice, b->stream));
-    BCK(cudaStreamSynchronize(b->stream));           // pos copied from the host vector
+    BCK(cudaStreamSynchronize(b->stream));           // the state copied from the host vector
+    auto graph_for = [&](BatchPhase& ph, int A, int size_i, int t) -> mc_status {
+        cudaGraphExec_t& ge = ph.g[size_i][t];
+        if (ge) return MC_OK;
+        cudaGraph_t g = nullptr;
+        BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        const mc_status st = batch_enqueue(b, A, t, size_i ? kBatchGraphIters : 1);
+        const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st != MC_OK) { if (g) cudaGraphDestroy(g); return st; }
+        if (e != cudaSuccess) return bfail(b, MC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+        const cudaError_t e2 = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) return bfail(b, MC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
+        return MC_OK;
+    };
     long long done = 0;
     int A = B;
     while (A > 0) {
-        // the iterations in which exactly the first A slices are in flight
+        // the iterations in which exactly the first A slices are in flight,
+        // kBatchGraphIters per graph launch (an even count: the parity repeats)
         const long long end = iters[A - 1];
         if (end > done) {
             TRY(batch_phase(b, A));
             BatchPhase& ph = b->phase[A - 1];
-            for (long long it = done; it < end; ++it) {
+            long long it = done;
+            while (it < end) {
                 const int t = (int)(it & 1);
-                if (!ph.g[t]) {
-                    cudaGraph_t g = nullptr;
-                    BCK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-                    const mc_status st = batch_enqueue(b, A, t);
-                    const cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-                    if (st != MC_OK) { if (g) cudaGraphDestroy(g); return st; }
-                    if (e != cudaSuccess) return bfail(b, MC_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-                    const cudaError_t e2 = cudaGraphInstantiate(&ph.g[t], g, 0);
-                    cudaGraphDestroy(g);
-                    if (e2 != cudaSuccess)
-                        return bfail(b, MC_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
-                }
-                BCK(cudaGraphLaunch(ph.g[t], b->stream));
+                const int size_i = (end - it >= kBatchGraphIters) ? 1 : 0;
+                TRY(graph_for(ph, A, size_i, t));
+                BCK(cudaGraphLaunch(ph.g[size_i][t], b->stream));
+                it += size_i ? kBatchGraphIters : 1;
             }
             done = end;
         }
         --A;
+    }
+    // each slice's counter as its own runs leave it (the last iteration of a
+    // slice drew an epoch it does not run)
+    b->k_end.resize(B);
+    for (int q = 0; q < B; ++q) {
+        mc_ctx* c = b->ctx[b->order[q]];
+        b->k_end[q] = (unsigned long long)(c->k_host + (uint64_t)iters[q]);
+        BCK(cudaMemcpyAsync(c->d_k, &b->k_end[q], sizeof(unsigned long long), cudaMemcpyHostToDevice, b->stream));
     }
     // every slice's own stream continues after the batch
     BCK(cudaEventRecord(b->ev[B], b->stream));

@@ -16,13 +16,14 @@ struct GateSel {
     const int* list;
     int fixed;
     int subsets;
-    const int* pos;            // non-null (batched runs): the slot's entry of list is
-                               // list[*pos], the slice's iteration within its epoch
+    const int* pos;            // non-null (batched runs): {iteration within the epoch,
+                               // epoch parity}; the entry is list[pos[1] * stride + pos[0]]
+    int stride;
 };
 
 __device__ __forceinline__ int sel_block(const GateSel& s, int slot)
 {
-    return s.list ? s.list[s.pos ? *s.pos : slot] : (s.fixed >= 0 ? s.fixed : slot);
+    return s.list ? s.list[s.pos ? s.pos[1] * s.stride + s.pos[0] : slot] : (s.fixed >= 0 ? s.fixed : slot);
 }
 
 // Batched launches over many independent slices (one context each): block b
@@ -32,10 +33,14 @@ struct BatchBlock {
     int slice, block, nblocks, pad;
 };
 
-// The gate draw of one slice in a batched iteration (k_draw_batch): the
-// slice's position in its epoch advances by one (mod n_blocks); at position 0
-// the epoch's n_blocks gates are drawn from the slice's counter as the
-// one-slice draw does.
+// The gate sequence of one slice in batched iterations.  state holds, for each
+// parity t of the iteration index, {iteration within the epoch, epoch parity};
+// gates holds two epochs' gates (stride apart, by epoch parity).  The last
+// kernel of an iteration of parity t writes state[t ^ 1] (the next iteration)
+// and, when that starts an epoch, draws its n_blocks gates into the other half
+// exactly as the one-slice draw does (Philox counter kctr, advanced by
+// n_blocks); the kernels of the iteration read only state[t] and the current
+// half, so nothing they read changes under them.
 struct BatchDraw {
     uint64_t seed;
     uint32_t stream;
@@ -43,7 +48,8 @@ struct BatchDraw {
     unsigned long long* kctr;
     const unsigned long long* thr;
     int* gates;
-    int* pos;
+    int* state;                // [2][2]
+    int stride;
 };
 
 __device__ __forceinline__ int sel_gate(const GateSel& s, int slot)
@@ -114,8 +120,10 @@ struct WarpAdjArgs {
 };
 cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s);
 cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s);
+// the transpose warp and update of every slice in flight; the first block of
+// each slice also advances that slice's gate sequence (draw[slice], parity t)
 cudaError_t launch_warp_adjoint_update_batch(const WarpAdjArgs* args, const BatchBlock* map, int nblocks,
-                                             cudaStream_t s);
+                                             const BatchDraw* draw, int t, cudaStream_t s);
 int warp_adjoint_blocks(int n);
 
 // ---- K3 (+K6): Joseph forward projection ------------------------------------
@@ -165,9 +173,10 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 // batched (all angles, one slot per slice, no bands): block b runs block
 // map[b].block of slice map[b].slice's item table with that slice's lines per
 // chunk (args[slice].lc: 8, 4 or 2); every slice of the launch has at most rpt
-// group slots per warp; smem_pairs = the largest lc x P of the launch's slices
+// group slots per warp; smem_pairs = the largest lc x P of the launch's slices;
+// lc > 0: every slice has those lines per chunk (a kernel compiled for them)
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
-                                 int smem_pairs, cudaStream_t s);
+                                 int smem_pairs, int lc, cudaStream_t s);
 int forward_groups_per_block(int rpt);
 int forward_consumer_warps();         // consumer warps per block
 int forward_ring_stages();            // chunks in flight (the drift between warps)
@@ -193,14 +202,14 @@ cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
 // batched (all angles, one slot per slice): block b works on tile
 // map[b].block of slice map[b].slice, with that slice's rows per thread
 // (args[slice].pj, any of 4, 8, 14, 16) and window length (args[slice].wl)
-cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, cudaStream_t s);
+// pj > 0: every slice has that tile height (a kernel compiled for it)
+cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
+                                     cudaStream_t s);
 int backproject_tiles(int n, int pj);
 int backproject_window(int pj);
 cudaError_t backproject_prepare();
 
 // ---- misc -------------------------------------------------------------------
-// one block per slice of a batched iteration (see BatchDraw)
-cudaError_t launch_draw_batch(const BatchDraw* d, int count, cudaStream_t s);
 // thr: null for uniform sampling, else N cumulative thresholds (see k_draw_gates)
 cudaError_t launch_draw_gates(uint64_t seed, uint32_t stream, unsigned long long* kctr,
                               uint64_t k0, int count, int n_gates, const unsigned long long* thr, int* out,
