@@ -382,17 +382,48 @@ __device__ __forceinline__ void warp_adjoint_block(const WarpAdjArgs& a, int bx)
     }
 }
 
+// One warp moves a slice's gate sequence from the iteration of parity t to
+// the next (see BatchDraw): the position advances, and at an epoch's end the
+// next epoch's gates are drawn into the other half as the one-slice draw does.
+__device__ __forceinline__ void advance_gate_sequence(const BatchDraw& d, int t)
+{
+    int pos = d.state[2 * t] + 1, epar = d.state[2 * t + 1];
+    if (pos >= d.n_blocks) {
+        pos = 0;
+        epar ^= 1;
+        const uint64_t k0 = (uint64_t)*d.kctr;
+        for (int j = threadIdx.x; j < d.n_blocks; j += 32) {
+            const uint32_t w = philox_word0(d.seed, d.stream, k0 + (uint64_t)j);
+            int g;
+            if (!d.thr) {
+                g = (int)(((uint64_t)w * (uint64_t)d.n_blocks) >> 32);
+            } else {
+                g = 0;
+                while (g < d.n_blocks - 1 && (unsigned long long)w >= d.thr[g]) ++g;
+            }
+            d.gates[epar * d.stride + j] = g;
+        }
+        __syncwarp();
+        if (threadIdx.x == 0) *d.kctr = (unsigned long long)(k0 + (uint64_t)d.n_blocks);
+    }
+    if (threadIdx.x == 0) {
+        d.state[2 * (t ^ 1)] = pos;
+        d.state[2 * (t ^ 1) + 1] = epar;
+    }
+}
+
 template <bool UPDATE>
 __global__ void __launch_bounds__(256) k_warp_adjoint(WarpAdjArgs a)
 {
     pdl_wait();
     pdl_trigger();
+    if (UPDATE && a.draw && blockIdx.x == 0 && threadIdx.x < 32) advance_gate_sequence(*a.draw, a.draw_t);
     warp_adjoint_block<UPDATE>(a, blockIdx.x);
 }
 
 // Batched: 256 pixels of one slice per block, every slice of the launch; the
 // first warp of each slice's first block advances the slice's gate sequence
-// to the next iteration (see BatchDraw).
+// to the next iteration.
 __global__ void __launch_bounds__(256) k_warp_adjoint_update_batch(const WarpAdjArgs* __restrict__ args,
                                                                    const BatchBlock* __restrict__ map,
                                                                    const BatchDraw* __restrict__ draw, int t)
@@ -400,32 +431,7 @@ __global__ void __launch_bounds__(256) k_warp_adjoint_update_batch(const WarpAdj
     pdl_wait();
     pdl_trigger();
     const BatchBlock m = map[blockIdx.x];
-    if (m.block == 0 && threadIdx.x < 32) {
-        const BatchDraw d = draw[m.slice];
-        int pos = d.state[2 * t] + 1, epar = d.state[2 * t + 1];
-        if (pos >= d.n_blocks) {
-            pos = 0;
-            epar ^= 1;
-            const uint64_t k0 = (uint64_t)*d.kctr;
-            for (int j = threadIdx.x; j < d.n_blocks; j += 32) {
-                const uint32_t w = philox_word0(d.seed, d.stream, k0 + (uint64_t)j);
-                int g;
-                if (!d.thr) {
-                    g = (int)(((uint64_t)w * (uint64_t)d.n_blocks) >> 32);
-                } else {
-                    g = 0;
-                    while (g < d.n_blocks - 1 && (unsigned long long)w >= d.thr[g]) ++g;
-                }
-                d.gates[epar * d.stride + j] = g;
-            }
-            __syncwarp();
-            if (threadIdx.x == 0) *d.kctr = (unsigned long long)(k0 + (uint64_t)d.n_blocks);
-        }
-        if (threadIdx.x == 0) {
-            d.state[2 * (t ^ 1)] = pos;
-            d.state[2 * (t ^ 1) + 1] = epar;
-        }
-    }
+    if (m.block == 0 && threadIdx.x < 32) advance_gate_sequence(draw[m.slice], t);
     warp_adjoint_block<true>(args[m.slice], m.block);
 }
 

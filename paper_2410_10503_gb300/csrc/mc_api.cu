@@ -2404,6 +2404,12 @@ struct mc_batch {
     int* d_bgates = nullptr;                 // per slice two epochs of gates, stride gmax
     int gmax = 1;
     std::vector<unsigned long long> k_end;   // each slice's counter after a run (host copy source)
+    // with one slice in flight (order[0]) the one-slice kernels run on copies
+    // of its table rows, passed by value (baked into that phase's graphs)
+    WarpArgs h_warp[2] = {};
+    FwdArgs h_fwd[2][2] = {};
+    BpArgs h_bp[2] = {};
+    WarpAdjArgs h_wadj[2] = {};
     std::vector<BatchPhase> phase;           // [A - 1] for A slices in flight, built on demand
     std::vector<cudaEvent_t> ev;             // one per slice (hand-off between streams) + 1
 };
@@ -2540,6 +2546,25 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
             BCK(cudaMemcpy(b->d_fwd[k][t], f[k][t].data(), B * sizeof(FwdArgs), cudaMemcpyHostToDevice));
     }
     BCK(cudaMemcpy(b->d_draw, dr.data(), B * sizeof(BatchDraw), cudaMemcpyHostToDevice));
+    // the one-slice phase's arguments by value: its graphs go when they change
+    for (int t = 0; t < 2; ++t) {
+        wa[t][0].draw = b->d_draw;
+        wa[t][0].draw_t = t;
+    }
+    const WarpArgs nw[2] = {w[0][0], w[1][0]};
+    const BpArgs nb[2] = {bp[0][0], bp[1][0]};
+    const WarpAdjArgs nwa[2] = {wa[0][0], wa[1][0]};
+    const FwdArgs nf[2][2] = {{f[0][0][0], f[0][1][0]}, {f[1][0][0], f[1][1][0]}};
+    const bool same = !memcmp(b->h_warp, nw, sizeof nw) && !memcmp(b->h_bp, nb, sizeof nb) &&
+                      !memcmp(b->h_wadj, nwa, sizeof nwa) && !memcmp(b->h_fwd, nf, sizeof nf);
+    if (!same && !b->phase.empty())
+        for (auto& row : b->phase[0].g)
+            for (auto& g : row)
+                if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    memcpy(b->h_warp, nw, sizeof nw);
+    memcpy(b->h_bp, nb, sizeof nb);
+    memcpy(b->h_wadj, nwa, sizeof nwa);
+    memcpy(b->h_fwd, nf, sizeof nf);
     return MC_OK;
 }
 
@@ -2622,6 +2647,14 @@ mc_status batch_enqueue(mc_batch* b, int A, int t, int iters)
     BatchPhase& ph = b->phase[A - 1];
     cudaStream_t s = b->stream;
     for (int i = 0; i < iters; ++i, t ^= 1) {
+        if (A == 1) {
+            // one slice in flight: the one-slice kernels, arguments by value
+            BCK(launch_warp_layouts(b->h_warp[t], s));
+            BCK(launch_forward(b->h_fwd[ph.plan][t], s));
+            BCK(launch_backproject(b->h_bp[t], s));
+            BCK(launch_warp_adjoint_update(b->h_wadj[t], s));
+            continue;
+        }
         BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
         BCK(launch_forward_batch(b->d_fwd[ph.plan][t], ph.d_map + ph.off_fwd, ph.n_fwd, ph.fwd_rpt, ph.fwd_pairs,
                                  ph.fwd_lc, s));

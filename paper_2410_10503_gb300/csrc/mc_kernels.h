@@ -117,6 +117,11 @@ struct WarpAdjArgs {
     const float* coef_tab;     // non-null: theta / p_i per gate, read for the slot's block
     float tau;
     float prox_scale;          // 1 / (1 + 2 tau alpha)
+    // non-null (a batched run with one slice in flight, the one-slice kernel):
+    // the first warp of block 0 advances that slice's gate sequence from
+    // iteration parity draw_t, as the batched kernel's first block does
+    const BatchDraw* draw;
+    int draw_t;
 };
 cudaError_t launch_warp_adjoint_store(const WarpAdjArgs& a, cudaStream_t s);
 cudaError_t launch_warp_adjoint_update(const WarpAdjArgs& a, cudaStream_t s);

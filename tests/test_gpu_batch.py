@@ -185,3 +185,25 @@ def test_merged_batch_refuses_changed_launch_shapes(mc, merged_slices):
         b.run(1, seeds=[1, 2])
     a.close()
     c.close()
+
+
+def test_one_slice_batch_follows_new_step_sizes(mc, merged_slices):
+    """A batch of one slice runs the one-slice kernels on its arguments by
+    value (16-iteration graphs): a run after new step sizes must use them, and
+    every run equals the slice's own runs."""
+    W, P, sd, nrm = merged_slices[0]
+    ctx = make_ctx(mc, P, nrm)
+    own = make_ctx(mc, P, nrm)
+    E = 40 // P.N + 1                                   # more than 16 iterations: the graphs replay
+    with mc.Batch([ctx]) as b:
+        b.run(E, [sd["gates"]])
+        own.spdhg_run(E, seed=sd["gates"])
+        for c in (ctx, own):
+            c.set_norms(np.asarray(nrm) * 1.7)          # new sigma, tau (theta stays 1)
+        b.run(E, [sd["gates"]])
+        x_own, _ = own.spdhg_run(E, seed=sd["gates"])
+    x_b, _ = ctx.spdhg_run(0, seed=sd["gates"])
+    assert ctx.iteration() == 2 * E * P.N
+    np.testing.assert_array_equal(x_b, x_own)
+    ctx.close()
+    own.close()
