@@ -348,7 +348,8 @@ def run_ours(args, W):
     }
     if args.convergence_epochs > 0:
         out["time_to_1e-3"] = convergence_legs(ctx, stream, d, W, norms, sd, args.convergence_epochs,
-                                               args.alpha_epochs)
+                                               args.alpha_epochs,
+                                               tuple(int(v) for v in args.alpha_subsets.split(",") if v))
     if args.storage_epochs > 0:
         out["storage_rbf512"] = storage_legs(args.storage_epochs)
     if args.batch_slices > 0:
@@ -473,13 +474,13 @@ def time_to_tol(ctx, stream, which, tol, max_epochs, seed, graph=True, chunk=1):
             "rel_err": rel}
 
 
-def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs, alpha_epochs):
+def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs, alpha_epochs, alpha_subsets=(8,)):
     """Time to 1e-3 relative distance to x* for graph-replayed SPDHG, SPDHG
     with plain launches and PDHG, in the paper's regime (alpha such that
     ||A||^2 / alpha = 70, Sec. III; at most max_epochs, timed epoch by epoch)
     and at the workload's own alpha (at most alpha_epochs, timed in chunks of
-    100 epochs); in the paper's regime also SPDHG over gates x S angle
-    subsets, S = 2, 4, 8.  x* by float32 CG to a relative residual of 1e-6
+    100 epochs); also SPDHG over gates x S angle subsets, S = 2, 4, 8 in the
+    paper's regime and S in alpha_subsets at the workload's alpha.  x* by float32 CG to a relative residual of 1e-6
     (paper regime) or 1e-9 (the workload's alpha, where the normal operator's
     condition number is ~3.5e7)."""
     import torch
@@ -510,18 +511,20 @@ def convergence_legs(ctx, stream, d, W, norms, sd, max_epochs, alpha_epochs):
             how: projected_time(ctx, stream, how, leg["spdhg_graph"], sd["gates"], 1000)
             for how in ("graph", "plain", "batched")}
         leg["pdhg_graph"] = time_to_tol(ctx, stream, "pdhg", 1e-3, cap, sd["gates"], True, chunk)
-        if label == "paper_regime_kappa70":
-            # sampling over gates x angle subsets (Sec. IV): same objective and x*,
-            # blocks of 1/S of the angles, N S iterations per epoch
-            subs = {}
-            for n_sub in (2, 4, 8):
-                ctx.set_subsets(n_sub)
-                ctx.norms(max_iter=100, tol=1e-7)
-                r = time_to_tol(ctx, stream, "spdhg", 1e-3, max_epochs, sd["gates"], True)
-                r["kappa_spdhg"] = ctx.steps()["kappa"]
-                subs[f"S={n_sub}"] = r
-            ctx.set_subsets(1)
-            ctx.set_norms(norms)
+        # sampling over gates x angle subsets (Sec. IV): same objective and x*,
+        # blocks of 1/S of the angles, N S iterations per epoch; per epoch the
+        # bound improves from l(kappa, N) to l(kappa / S, N S) (block norms^2 ~1/S)
+        subs = {}
+        for n_sub in ((2, 4, 8) if label == "paper_regime_kappa70" else alpha_subsets):
+            ctx.set_subsets(n_sub)
+            ctx.norms(max_iter=100, tol=1e-7)
+            r = time_to_tol(ctx, stream, "spdhg", 1e-3, cap, sd["gates"], True, chunk)
+            r["kappa_spdhg"] = ctx.steps()["kappa"]
+            r["rate_bound_per_epoch"] = _rate(ctx.steps()["kappa"], W.n_gates * n_sub)
+            subs[f"S={n_sub}"] = r
+        ctx.set_subsets(1)
+        ctx.set_norms(norms)
+        if subs:
             leg["spdhg_angle_subsets_graph"] = subs
         out[label] = leg
     ctx.set_data(d, W.alpha)
@@ -890,6 +893,9 @@ def main():
                     help="epoch cap of the time-to-1e-3 legs (0 skips them)")
     ap.add_argument("--alpha-epochs", type=int, default=60000,
                     help="epoch cap of the time-to-1e-3 legs at the workload's own alpha (0: skip)")
+    ap.add_argument("--alpha-subsets", default="8",
+                    help="comma-separated angle-subset counts S of the gates x subsets SPDHG legs at "
+                         "the workload's own alpha ('' skips them)")
     ap.add_argument("--storage-epochs", type=int, default=100,
                     help="epoch cap of the rbf512 float32/binary16/bfloat16 storage legs (0 skips)")
     ap.add_argument("--batch-slices", type=int, default=64,

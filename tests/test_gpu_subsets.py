@@ -56,6 +56,10 @@ CASES = {
     "rbf64_S7": ("rbf256", "rbf", 7, dict(n=64, n_angles=90, n_bins=93, n_gates=3, rbf_width=10.0,
                                           rbf_max_disp=3.0, n_ellipses=8, axis_lo=3.0,
                                           axis_hi=12.0, alpha=1e-2)),
+    # 96^2, 160 x 137, N = 3 rigid, S = 16: eight line bands per subset launch
+    # (the banded forward's group counters at their largest band count)
+    "rigid96_S16": ("rigid128", "rigid", 16, dict(n=96, n_angles=160, n_bins=137, n_gates=3, n_ellipses=8,
+                                                   axis_lo=4.0, axis_hi=24.0)),
 }
 
 
