@@ -104,7 +104,7 @@ enum {
                                     within ||d_h - d|| / (2 sqrt(alpha N)).  The float32 d
                                     is kept for mc_objective, mc_set_reference and
                                     mc_solve_normal.  Switching converts the current y. */
-    MC_OPT_TEST_STALL = 5        /* 1: for testing the failure path of the bounded
+    MC_OPT_TEST_STALL = 5,       /* 1: for testing the failure path of the bounded
                                     device-side waits.  The next forward projection
                                     this context launches (runs then launch epochs
                                     directly instead of replaying a graph) gets a
@@ -115,6 +115,19 @@ enum {
                                     MC_ETIMEOUT) and nothing is left in flight, so
                                     the context stays usable.  Cleared by that
                                     launch; 0 clears it before. */
+    MC_OPT_SUBSET_BANDS = 6,     /* line bands of the angle-subset forward (0, default:
+                                    min(8, max(1, S / 2)); 1..8): each subset launch's
+                                    work items stream one band of the image's lines
+                                    and a combine adds the bands' partial ray sums in
+                                    band order.  With S > 1 the subset tables are
+                                    rebuilt at once (norms and step sizes kept);
+                                    results change within float32 rounding (the
+                                    order of the ray sums).  mc_autotune picks it
+                                    when S > 1. */
+    MC_OPT_SUBSET_ROWS = 7       /* rows per thread of the angle-subset backprojection
+                                    tiles (0, default: those of the all-angle launches;
+                                    4, 8, 14 or 16); results change within float32
+                                    rounding. */
 };
 
 enum { MC_STORE_F32 = 0, MC_STORE_F16 = 1, MC_STORE_BF16 = 2 };
@@ -190,7 +203,11 @@ mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out)
  * rows per thread.  out (nullable, host, 4 int32): {lines per chunk, items per
  * block, group slots per warp, rows per thread}.  Captured epoch graphs are
  * dropped.  The creation-time choice is a heuristic (largest chunk that
- * fits, fewest items, rows per thread giving ~24 warps per SM). */
+ * fits, fewest items, rows per thread giving ~24 warps per SM).  With angle
+ * subsets (mc_set_subsets, S > 1) it also picks the subset forward's line
+ * bands (MC_OPT_SUBSET_BANDS: 1, 2, 3, 4, 6 or 8, timed on the S blocks of
+ * gate 0) and leaves the option at that value; norms, step sizes and
+ * iterates are kept. */
 mc_status mc_autotune(mc_ctx* ctx, int32_t reps, int32_t* out);
 
 /* Sample gates and angle subsets together (the extension named in Sec. IV):

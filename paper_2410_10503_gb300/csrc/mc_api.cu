@@ -104,6 +104,9 @@ struct mc_ctx {
     int s_nitems = 0, s_ipb = 1, s_rpt = 2;
     int s_bands = 1;                  // line bands per subset item (partial sums in d_bandpart)
     float* d_bandpart = nullptr;
+    int bands_opt = 0;                // MC_OPT_SUBSET_BANDS (0: min(8, max(1, S / 2)))
+    int s_pj = 0;                     // MC_OPT_SUBSET_ROWS: backprojection rows per thread of the
+                                      // subset launches (0: pj, the all-angle launches' height)
 
     // motion and D_i^T
     int kind = 0;
@@ -463,7 +466,8 @@ mc_status backproject(mc_ctx* c, GateSel sel, int n_slots, float* out)
     a.sel = sel;
     a.dy = c->d_dy; a.dy_stride = c->dy_stride; a.Pb = c->Pb; a.Gb = c->Gb;
     a.ang = c->d_bang; a.n = c->n; a.na = c->na; a.nb = c->nb; a.n_slots = n_slots;
-    a.pj = c->pj; a.out = out; a.err = c->d_err;
+    a.pj = (sel.subsets > 1 && c->s_pj) ? c->s_pj : c->pj;
+    a.out = out; a.err = c->d_err;
     return launch(c, C_BP, "backproject", [&] { return launch_backproject(a, c->stream); });
 }
 
@@ -1740,6 +1744,36 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
         if (st == MC_OK && ms < best_bp) { best_bp = ms; best_pj = pj; }
     }
     c->pj = best_pj;
+    // with angle subsets: the subset forward's line bands, its tables rebuilt
+    // for each candidate and timed on the S blocks of gate 0 (forward, then
+    // backprojection, block after block as in an epoch); norms and step sizes
+    // are kept
+    if (st == MC_OK && c->S > 1) {
+        const bool had = c->have_norms;
+        const std::vector<double> n2 = c->norms2;
+        const int keep = c->bands_opt;
+        int best_bands = keep;
+        float best_sub = 1e30f;
+        for (int bands : {1, 2, 3, 4, 6, 8}) {
+            c->bands_opt = bands;
+            st = mc_set_subsets(c, c->S);
+            if (st != MC_OK) break;
+            float ms = 0;
+            st = timed([&]() -> mc_status {
+                for (int j = 0; j < c->S; ++j) {
+                    TRY(project_store(c, GateSel{nullptr, j, c->S}, 1, c->d_sinoN));
+                    TRY(backproject(c, GateSel{nullptr, j, c->S}, 1, c->d_b));
+                }
+                return MC_OK;
+            }, ms);
+            if (st != MC_OK) break;
+            if (ms < best_sub) { best_sub = ms; best_bands = bands; }
+        }
+        c->bands_opt = best_bands;
+        const mc_status s2 = mc_set_subsets(c, c->S);
+        if (st == MC_OK) st = s2;
+        if (st == MC_OK && had) st = mc_set_norms(c, n2.data());
+    }
     c->prof_on = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1771,7 +1805,7 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
         // forward work items per angle subset, one table, subset s at soff[s];
         // with B = S / 2 line bands (at most 8) each subset's groups are cut
         // into ~SMs / B ranges, each repeated for every band
-        const int bands = std::min(8, std::max(1, subsets / 2));
+        const int bands = c->bands_opt > 0 ? c->bands_opt : std::min(8, std::max(1, subsets / 2));
         GroupTable gt;
         build_groups(c, c->order, c->inv_k, c->t_k, subsets, c->lc, gt);
         std::vector<RayItem> cut;
@@ -2203,6 +2237,24 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
     case MC_OPT_PROFILE: c->prof_on = value != 0; return MC_OK;
     case MC_OPT_TRACE_OBJECTIVE: c->trace_obj = value != 0; return MC_OK;
     case MC_OPT_TEST_STALL: c->test_stall = value != 0; return MC_OK;
+    case MC_OPT_SUBSET_BANDS: {
+        if (value < 0 || value > 8) return fail(c, MC_EINVAL, "subset bands must be in [0, 8]");
+        c->bands_opt = (int)value;
+        if (c->S <= 1) return MC_OK;
+        // rebuild the subset tables with the new band count (norms and step sizes kept)
+        const bool norms = c->have_norms;
+        const std::vector<double> n2 = c->norms2;
+        TRY(mc_set_subsets(c, c->S));
+        if (norms) TRY(mc_set_norms(c, n2.data()));
+        return MC_OK;
+    }
+    case MC_OPT_SUBSET_ROWS:
+        if (value != 0 && value != 4 && value != 8 && value != 14 && value != 16)
+            return fail(c, MC_EINVAL, "subset rows per thread must be 0, 4, 8, 14 or 16");
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        c->s_pj = (int)value;
+        return MC_OK;
     case MC_OPT_STORAGE: {
         if (value < 0 || value > 2) return fail(c, MC_EINVAL, "storage must be 0 (f32), 1 (f16) or 2 (bf16)");
         const int v = (int)value;

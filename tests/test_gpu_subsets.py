@@ -135,3 +135,38 @@ def test_subsets_one_restores_gate_sampling_and_errors(mc):
     a.set_subsets(6)
     x = S.random_image(W.n, 2).astype(np.float32)
     np.testing.assert_array_equal(a.forward(1, x), b.forward(1, x))
+
+
+def test_subset_launch_shapes_and_autotune(mc, case):
+    """The subset launches' band count and backprojection tile height
+    (MC_OPT_SUBSET_BANDS / MC_OPT_SUBSET_ROWS) change results only within
+    float32 rounding; mc_autotune with subsets picks the band count and keeps
+    the norms, step sizes and iterates; bad values are refused."""
+    from paper_2410_10503_gb300 import _native as N
+    P, sd, Ssub, nb2 = case
+    E = 10
+    ref = O.spdhg(P, E, O.step_sizes(nb2[:-1].max(), P.alpha, P.N, P.N * Ssub), seed=sd["gates"],
+                  subsets=Ssub)
+    for bands, rows in ((1, 0), (3, 8), (8, 16)):
+        ctx = context(mc, P)
+        ctx.set_subsets(Ssub)
+        ctx.set_norms(nb2)
+        ctx.set_option(N.MC_OPT_SUBSET_BANDS, bands)      # tables rebuilt, norms kept
+        ctx.set_option(N.MC_OPT_SUBSET_ROWS, rows)
+        x, _ = ctx.spdhg_run(E, seed=sd["gates"])
+        assert rel_l2(x, ref.x) <= 1e-4, (bands, rows)
+        ctx.close()
+    ctx = context(mc, P)
+    ctx.set_subsets(Ssub)
+    ctx.set_norms(nb2)
+    x1, _ = ctx.spdhg_run(E // 2, seed=sd["gates"])
+    steps = ctx.steps()
+    ctx.autotune(reps=1)
+    assert ctx.steps() == steps
+    x, _ = ctx.spdhg_run(E - E // 2, seed=sd["gates"])      # continues from the kept iterates
+    assert ctx.iteration() == E * P.N * Ssub
+    assert rel_l2(x, ref.x) <= 1e-4
+    for opt, bad in ((N.MC_OPT_SUBSET_BANDS, 9), (N.MC_OPT_SUBSET_BANDS, -1), (N.MC_OPT_SUBSET_ROWS, 5)):
+        with pytest.raises(mc.MCError):
+            ctx.set_option(opt, bad)
+    ctx.close()
