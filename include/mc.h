@@ -124,10 +124,18 @@ enum {
                                     results change within float32 rounding (the
                                     order of the ray sums).  mc_autotune picks it
                                     when S > 1. */
-    MC_OPT_SUBSET_ROWS = 7       /* rows per thread of the angle-subset backprojection
+    MC_OPT_SUBSET_ROWS = 7,      /* rows per thread of the angle-subset backprojection
                                     tiles (0, default: those of the all-angle launches;
                                     4, 8, 14 or 16); results change within float32
                                     rounding. */
+    MC_OPT_FORWARD_LINES = 8     /* lines per staged chunk of the forward projector
+                                    (2, 4, 8 or 16; the ring holds up to 5 chunks in
+                                    the shared memory a block may use, 16-line chunks
+                                    of large images fewer, and at least 2 must fit;
+                                    16 needs the image side rounded up to 8 to be a
+                                    multiple of 16): the forward's work items are cut
+                                    again for it (mc_autotune also tries every size).
+                                    Results change within float32 rounding. */
 };
 
 enum { MC_STORE_F32 = 0, MC_STORE_F16 = 1, MC_STORE_BF16 = 2 };

@@ -9,10 +9,11 @@
 // p / W; an entry {-1, 0} is an empty slot); one block per
 // SM takes `ipb` consecutive items and streams the whole warped image through
 // shared memory for each, in chunks of LC lines.  One producer warp issues a
-// bulk TMA copy (cp.async.bulk) per chunk into a ring of kStages buffers; the
-// consumer warps wait on the chunk's "full" mbarrier and release it through
-// its "empty" mbarrier, so warps drift by up to kStages - 1 chunks instead of
-// meeting at a block barrier every chunk.
+// bulk TMA copy (cp.async.bulk) per chunk into a ring of NS buffers (5; 3 for
+// 16-line chunks and for 8-line chunks of large images); the consumer warps
+// wait on the chunk's "full" mbarrier and release it through its "empty"
+// mbarrier, so warps drift by up to NS - 1 chunks instead of meeting at a
+// block barrier every chunk.
 //
 // A group visits only the chunks its rays cross.  A sample is an FMA for the
 // position, one round-down add whose bits give both floor and shared address,
@@ -21,13 +22,14 @@
 // float-pair arithmetic at its first line, advanced between chunks by the
 // angle's exact integer/fraction split of LC * t, and stepped by j * t inside
 // a chunk, so interpolation weights stay exact to ~1e-6 px.  Every line has
-// kGuard = 17 zero pairs in front and at least 17 behind, and each chunk's
-// starting pair index ui is clamped to [LC - 1, kGuard + n + LC - 1].  With
-// |t| <= 1 and a fraction in [0, 1] a chunk's samples lie at pair indices
-// ui - (LC - 1) .. ui + LC, so every lane stays inside its line; and a lane
-// is clamped only when all of its samples in the chunk fall on zero pairs
-// (image coordinate <= -2 or >= n), where the clamped samples read zeros
-// too.  So the rays of a group that leave the image inside a chunk, or miss
+// G = a.guard >= 2 LC + 1 zero pairs in front and at least G behind
+// (P >= n + 2 G), and each chunk's starting pair index ui is clamped to
+// [LC - 1, G + n + LC - 1].  With |t| <= 1 and a fraction in [0, 1] a chunk's
+// samples lie at pair indices ui - (LC - 1) .. ui + LC, so every lane stays
+// inside its line (at most index G + n + 2 LC - 1 <= P - 1); and a lane is
+// clamped only when all of its samples in the chunk fall on zero pairs
+// (indices up to 2 LC - 1 <= G - 2 in front, from G + n behind), where the
+// clamped samples read zeros too.  So the rays of a group that leave the image inside a chunk, or miss
 // it, need no predication and no separate edge path.
 #include "mc_kernels.h"
 
@@ -96,7 +98,7 @@ __device__ __forceinline__ bool mbar_wait_or_flag(uint64_t* bar, uint32_t parity
 
 // Before the producer leaves: every copy it issued has landed, so no bulk
 // copy is still writing into the block's shared memory when the block ends.
-// Copies g in [issued - kStages, issued) may still be in flight (older ones
+// Copies g in [issued - stages, issued) may still be in flight (older ones
 // were waited for by the consumers before the producer could reuse their
 // stage); each completes the phase g / stages of its stage's full barrier.
 // Bounded: a copy that never lands leaves after `limit` polls with the error
@@ -142,7 +144,6 @@ constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives u
 constexpr int kConsumers = 23;               // consumer warps per block (24 warps in all: 6 per scheduler)
 constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
 constexpr int kBlock = kThreads + 32;        // plus one producer warp
-constexpr int kStages = 5;
 
 #ifdef MC_CHECKED
 // The samples of one ray over the LC lines of a chunk in C, the form used by
@@ -254,13 +255,13 @@ struct SlotRec {
 // One block's work: items bx * ipb .. of the launch's item table for gate
 // slot `slot`; nbx = blocks sharing the table (the CSR prefetch is split
 // among them).
-template <int RPT, int LC, bool BANDED>
+template <int RPT, int LC, int NS, bool BANDED>
 __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot, int nbx, SlotState* s_slot,
                                               SlotRec* s_rec)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + kStages;
+    uint64_t* empty = full + kMaxStages;
     int* s_flag = reinterpret_cast<int*>(smem + 96);
     float2* stage0 = reinterpret_cast<float2*>(smem + 128);
     const size_t stage_pairs = (size_t)LC * a.P;   // one chunk: LC whole lines
@@ -276,7 +277,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kStages; ++i) {
+        for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kConsumers);
         }
@@ -304,9 +305,9 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
                     const int cb0 = item.band * a.cpb, cb1 = min(nch, cb0 + a.cpb);
                     for (int c = cb0; c < cb1; ++c) {
                         const int q = issued;
-                        const int st = q % kStages;
-                        if (q >= kStages &&
-                            !mbar_wait_or_flag(&empty[st], (uint32_t)((q / kStages - 1) & 1), wlim, s_flag)) {
+                        const int st = q % NS;
+                        if (q >= NS &&
+                            !mbar_wait_or_flag(&empty[st], (uint32_t)((q / NS - 1) & 1), wlim, s_flag)) {
                             atomicExch(s_flag, 1);
                             atomicExch(a.err, kErrTimeout);
                             stop = true;
@@ -322,9 +323,9 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
                 for (int g = 0; g < n_it * nch; ++g) {
                     const int it = g / nch, c = g - it * nch;
                     const float2* src = (items[it0 + it].dir ? a.lcol : a.lrow) + slot * a.layout_stride;
-                    const int st = g % kStages;
-                    if (g >= kStages &&
-                        !mbar_wait_or_flag(&empty[st], (uint32_t)((g / kStages - 1) & 1), wlim, s_flag)) {
+                    const int st = g % NS;
+                    if (g >= NS &&
+                        !mbar_wait_or_flag(&empty[st], (uint32_t)((g / NS - 1) & 1), wlim, s_flag)) {
                         atomicExch(s_flag, 1);
                         atomicExch(a.err, kErrTimeout);
                         break;
@@ -335,7 +336,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
                     ++issued;
                 }
             }
-            drain_copies(full, issued, kStages, wlim);
+            drain_copies(full, issued, NS, wlim);
         }
         // off the ring's critical path: prefetch the CSR the iteration's
         // transpose warp will read (a.pf_rowptr is set for one-slot SPDHG launches)
@@ -347,7 +348,8 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     const int gate = sel_gate(a.sel, slot);
     const float h = 0.5f * (float)(n - 1);
     const float hb = 0.5f * (float)(nb - 1);
-    const float off = h + (float)kGuard;
+    const int guard = a.guard;
+    const float off = h + (float)guard;
     float mj[LC];
 #pragma unroll
     for (int j = 0; j < LC; ++j) mj[j] = kMagic + (float)(j * a.P);
@@ -359,7 +361,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
         mm[q] = pk2(mj[2 * q], mj[2 * q + 1]);
     }
     // clamp of a chunk's first-line pair index (see the file comment)
-    const int ui_lo = LC - 1, ui_hi = kGuard + n + LC - 1;
+    const int ui_lo = LC - 1, ui_hi = guard + n + LC - 1;
 
     int q_run = 0;                        // BANDED: chunks consumed so far
     for (int it = 0; it < n_it; ++it) {
@@ -389,15 +391,15 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
             const FwdAngle T = rec[m].T;
             const float B = (float)b - hb;                      // exact
             const float t = T.t_hi;
-            // lines with a non-zero weight have u in (kGuard - 1, kGuard + n);
+            // lines with a non-zero weight have u in (guard - 1, guard + n);
             // widen by up to two lines (extra samples read zeros)
             const float u0 = fmaf(h, t, fmaf(B, T.inv_hi, off));
             int lo = n, hi = -1;
             if (fabsf(t) < 1e-6f) {
-                if (u0 > (float)kGuard - 2.0f && u0 < (float)(kGuard + n) + 1.0f) { lo = 0; hi = n - 1; }
+                if (u0 > (float)guard - 2.0f && u0 < (float)(guard + n) + 1.0f) { lo = 0; hi = n - 1; }
             } else {
-                const float e1 = (u0 - (float)(kGuard + n)) / t;
-                const float e3 = (u0 - (float)(kGuard - 1)) / t;
+                const float e1 = (u0 - (float)(guard + n)) / t;
+                const float e3 = (u0 - (float)(guard - 1)) / t;
                 const float l_lo = fmaxf(floorf(fminf(e1, e3)) - 1.0f, 0.0f);
                 const float l_hi = fminf(ceilf(fmaxf(e1, e3)) + 1.0f, (float)(n - 1));
                 if (l_lo <= l_hi) { lo = (int)l_lo; hi = (int)l_hi; }
@@ -423,9 +425,9 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
 
         for (int ch = cb0; ch < cb1; ++ch) {
             const int g = BANDED ? q_run++ : it * nch + ch;
-            const int st = g % kStages;
+            const int st = g % NS;
             // one verdict per warp, so that all lanes leave or none does
-            if (!__all_sync(0xffffffffu, mbar_wait_or_flag(&full[st], (uint32_t)((g / kStages) & 1), wlim, s_flag))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_or_flag(&full[st], (uint32_t)((g / NS) & 1), wlim, s_flag))) {
                 // this wait ran out, or another warp's did: the producer sees
                 // the flag, stops issuing and drains the copies it has in
                 // flight before the block ends
@@ -524,38 +526,21 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     }
 }
 
-template <int RPT, int LC, bool BANDED>
+template <int RPT, int LC, int NS, bool BANDED>
 __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 {
     pdl_wait();
     pdl_trigger();
     __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
     __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
-    forward_block<RPT, LC, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
+    forward_block<RPT, LC, NS, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
 }
 
 // Batched: the blocks of every slice of the launch, each on its slice's item
-// table with its slice's arguments (all angles, one slot, no bands) and its
-// own lines per chunk (8, 4 or 2: one instance of the block's body each).
-template <int RPT>
-__global__ void __launch_bounds__(kBlock, 1) k_forward_batch(const FwdArgs* __restrict__ args,
-                                                             const BatchBlock* __restrict__ map)
-{
-    pdl_wait();
-    pdl_trigger();
-    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
-    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
-    const BatchBlock m = map[blockIdx.x];
-    const FwdArgs& a = args[m.slice];
-    const int lc = a.lc;
-    if (lc == 8) forward_block<RPT, 8, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
-    else if (lc == 4) forward_block<RPT, 4, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
-    else forward_block<RPT, 2, false>(a, m.block, 0, m.nblocks, s_slot, s_rec);
-}
-
-// Batched, every slice of the launch with lines per chunk LC: one compiled
-// body (the dispatching kernel above carries all three and its registers).
-template <int RPT, int LC>
+// table with its slice's arguments (all angles, one slot, no bands); every
+// slice of the launch has LC lines per chunk and an NS-stage ring (the batch
+// launches one such class per chunk size and ring).
+template <int RPT, int LC, int NS>
 __global__ void __launch_bounds__(kBlock, 1) k_forward_batch_lc(const FwdArgs* __restrict__ args,
                                                                 const BatchBlock* __restrict__ map)
 {
@@ -564,7 +549,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward_batch_lc(const FwdArgs* _
     __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
     __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
     const BatchBlock m = map[blockIdx.x];
-    forward_block<RPT, LC, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
+    forward_block<RPT, LC, NS, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
 }
 
 // Sum of the bands' partial ray sums in band order, then the epilogue of
@@ -618,55 +603,60 @@ int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
 
 int forward_consumer_warps() { return kConsumers; }
 
-int forward_ring_stages() { return kStages; }
 
 // static shared memory of the largest instance: the slot tables plus room for
 // the alignment padding the compiler may place between them
 int forward_static_smem() { return (int)(kConsumers * 8 * (sizeof(SlotState) + sizeof(SlotRec))) + 256; }
 
-size_t forward_smem_bytes(int lc, int P) { return 128 + kStages * (size_t)lc * P * sizeof(float2); }
+size_t forward_smem_bytes(int lc, int P)
+{
+    return 128 + (size_t)forward_ring(lc, P) * lc * P * sizeof(float2);
+}
 
+// (group slots per warp, lines per chunk, ring stages)
 #define MC_FWD_INSTANCES(X) \
-    X(2, 2) X(4, 2) X(8, 2) X(2, 4) X(4, 4) X(8, 4) X(2, 8) X(4, 8) X(8, 8)
+    X(2, 2, 5) X(4, 2, 5) X(8, 2, 5) X(2, 4, 5) X(4, 4, 5) X(8, 4, 5) X(2, 8, 5) X(4, 8, 5) X(8, 8, 5) \
+    X(2, 8, 3) X(4, 8, 3) X(8, 8, 3) X(2, 16, 3) X(4, 16, 3) X(8, 16, 3)
 
 cudaError_t forward_prepare(int max_smem)
 {
     cudaError_t e = cudaSuccess;
-#define MC_SET_ATTR(R, L)                                                                          \
+#define MC_SET_ATTR(R, L, NS)                                                                      \
     if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward<R, L, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+        e = cudaFuncSetAttribute(k_forward<R, L, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  max_smem);                                                       \
     if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward<R, L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+        e = cudaFuncSetAttribute(k_forward<R, L, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  max_smem);                                                       \
 
     MC_FWD_INSTANCES(MC_SET_ATTR)
 #undef MC_SET_ATTR
-    for (auto k : {k_forward_batch<2>, k_forward_batch<4>, k_forward_batch<8>})
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-#define MC_SET_ATTR_B(R, L)                                                                        \
+#define MC_SET_ATTR_B(R, L, NS)                                                                    \
     if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward_batch_lc<R, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        e = cudaFuncSetAttribute(k_forward_batch_lc<R, L, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
     MC_FWD_INSTANCES(MC_SET_ATTR_B)
 #undef MC_SET_ATTR_B
     return e;
 }
 
-cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
+cudaError_t launch_forward(const FwdArgs& a_in, cudaStream_t s)
 {
+    FwdArgs a = a_in;
+    a.stages = forward_ring(a.lc, a.P);
+    if (!forward_lines_fit(a.n, a.P, a.guard, a.lc) || a.P < a.n + 2 * a.guard) return cudaErrorInvalidValue;
     if (a.nbands > 1 && (a.n_slots != 1 || !a.part)) return cudaErrorInvalidValue;   // one partial buffer
     const dim3 grid((a.n_items + a.ipb - 1) / a.ipb, a.n_slots);
     const size_t smem = forward_smem_bytes(a.lc, a.P);
-#define MC_LAUNCH(R, L)                                                                   \
-    if (a.rpt == R && a.lc == L) {                                                        \
+#define MC_LAUNCH(R, L, NS)                                                               \
+    if (a.rpt == R && a.lc == L && a.stages == NS) {                                      \
         if (a.nbands > 1) {                                                               \
-            cudaError_t e = pdl_launch(k_forward<R, L, true>, grid, dim3(kBlock), smem, s, a);  \
+            cudaError_t e = pdl_launch(k_forward<R, L, NS, true>, grid, dim3(kBlock), smem, s, a);  \
             if (e != cudaSuccess) return e;                                               \
             const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;                          \
             const int rays = ((a.na + S - 1) / S) * a.nb;                                 \
             return pdl_launch(k_forward_combine, dim3((rays + 255) / 256, a.n_slots), dim3(256), 0, s, a); \
         } else {                                                                          \
-            return pdl_launch(k_forward<R, L, false>, grid, dim3(kBlock), smem, s, a);    \
+            return pdl_launch(k_forward<R, L, NS, false>, grid, dim3(kBlock), smem, s, a); \
         }                                                                                 \
     }
     MC_FWD_INSTANCES(MC_LAUNCH)
@@ -675,21 +665,15 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s)
 }
 
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
-                                 int smem_pairs, int lc, cudaStream_t s)
+                                 size_t smem_bytes, int lc, int stages, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    const size_t smem = 128 + kStages * (size_t)smem_pairs * sizeof(float2);
-    if (lc > 0) {
-#define MC_LAUNCH_B(R, L)                                                                   \
-        if (rpt == R && lc == L)                                                            \
-            return pdl_launch(k_forward_batch_lc<R, L>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
-        MC_FWD_INSTANCES(MC_LAUNCH_B)
+    const size_t smem = smem_bytes;
+#define MC_LAUNCH_B(R, L, NS)                                                               \
+    if (rpt == R && lc == L && stages == NS)                                                \
+        return pdl_launch(k_forward_batch_lc<R, L, NS>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+    MC_FWD_INSTANCES(MC_LAUNCH_B)
 #undef MC_LAUNCH_B
-        return cudaErrorInvalidValue;
-    }
-    if (rpt == 2) return pdl_launch(k_forward_batch<2>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
-    if (rpt == 4) return pdl_launch(k_forward_batch<4>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
-    if (rpt == 8) return pdl_launch(k_forward_batch<8>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
     return cudaErrorInvalidValue;
 }
 

@@ -70,8 +70,8 @@ __device__ __forceinline__ void warp_layouts_block(const WarpArgs& a, int bx, in
             const int r = r_t + rr, c = c_t + cc;
             if (r < n && c < n) {
                 const float v = w_s[rr][cc];
-                lrow[(size_t)r * a.P + kGuard + c] = make_float2(v, w_s[rr][cc + 1] - v);
-                if (c == 0) lrow[(size_t)r * a.P + kGuard - 1] = make_float2(0.0f, v);
+                lrow[(size_t)r * a.P + a.guard + c] = make_float2(v, w_s[rr][cc + 1] - v);
+                if (c == 0) lrow[(size_t)r * a.P + a.guard - 1] = make_float2(0.0f, v);
             }
         }
         {   // column lines: consecutive threads along the rows of one column
@@ -79,8 +79,8 @@ __device__ __forceinline__ void warp_layouts_block(const WarpArgs& a, int bx, in
             const int r = r_t + rr, c = c_t + cc;
             if (r < n && c < n) {
                 const float v = w_s[rr][cc];
-                lcol[(size_t)c * a.P + kGuard + r] = make_float2(v, w_s[rr + 1][cc] - v);
-                if (r == 0) lcol[(size_t)c * a.P + kGuard - 1] = make_float2(0.0f, v);
+                lcol[(size_t)c * a.P + a.guard + r] = make_float2(v, w_s[rr + 1][cc] - v);
+                if (r == 0) lcol[(size_t)c * a.P + a.guard - 1] = make_float2(0.0f, v);
             }
         }
     }
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256) k_warp_plain(WarpArgs a)
 
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s)
 {
+    if (a.guard < 1 || a.P < a.n + 2 * a.guard) return cudaErrorInvalidValue;   // the lines' zero pairs
     dim3 grid((a.n + 31) / 32, (a.n + kWarpTileRows - 1) / kWarpTileRows, a.n_slots), block(1024);
     return pdl_launch(k_warp_layouts, grid, block, 0, s, a);
 }

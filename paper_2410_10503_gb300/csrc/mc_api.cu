@@ -92,6 +92,7 @@ struct mc_ctx {
     int2* d_groups = nullptr;
     RayItem* d_items = nullptr;
     int n_items = 0, ipb = 1, rpt = 1, lc = 1, P = 0, Gb = 0, Pb = 0, pj = 4;
+    int guard = kGuardNarrow;         // zero pairs around each layout line (layout_guard)
     size_t layout_stride = 0, dy_stride = 0;
     std::vector<int> order;           // angles, rows-driven first
     std::vector<double> inv_k, t_k;   // per angle: 1/|sin| or 1/|cos|, and the slope
@@ -422,6 +423,7 @@ mc_status warp_into_layouts(mc_ctx* c, const float* x, GateSel sel, int n_slots,
     a.rigid = c->d_rigid; a.field = c->d_field; a.identity = identity ? 1 : 0;
     a.sel = sel; a.n_slots = n_slots;
     a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+    a.guard = c->guard;
     return launch(c, C_WARP, "warp", [&] { return launch_warp_layouts(a, c->stream); });
 }
 
@@ -429,6 +431,7 @@ FwdArgs fwd_args(mc_ctx* c, GateSel sel, int n_slots)
 {
     FwdArgs a{};
     a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+    a.guard = c->guard;
     a.ang = c->d_fang; a.groups = c->d_groups; a.items = c->d_items; a.n_items = c->n_items;
     a.ipb = c->ipb; a.rpt = c->rpt; a.lc = c->lc; a.n = c->n; a.na = c->na; a.nb = c->nb;
     if (sel.subsets > 1) {            // the drawn block's angle subset
@@ -906,12 +909,13 @@ void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float
     int lo_min = n, hi_max = -1;
     for (int l = 0; l < 32; ++l) {
         const int b = std::min(b0 + l, nb - 1);
-        const double u0 = h * t + (b - hb) * inv + h + kGuard;
+        const double G = c->guard;
+        const double u0 = h * t + (b - hb) * inv + h + G;
         int lo = n, hi = -1;
         if (std::fabs(t) < 1e-6) {
-            if (u0 > kGuard - 2.0 && u0 < kGuard + n + 1.0) { lo = 0; hi = n - 1; }
+            if (u0 > G - 2.0 && u0 < G + n + 1.0) { lo = 0; hi = n - 1; }
         } else {
-            const double e1 = (u0 - (kGuard + n)) / t, e3 = (u0 - (kGuard - 1)) / t;
+            const double e1 = (u0 - (G + n)) / t, e3 = (u0 - (G - 1)) / t;
             const double llo = std::max(std::floor(std::min(e1, e3)) - 1.0, 0.0);
             const double lhi = std::min(std::ceil(std::max(e1, e3)) + 1.0, (double)(n - 1));
             if (llo <= lhi) { lo = (int)llo; hi = (int)lhi; }
@@ -970,7 +974,7 @@ void parallel_for(size_t count, F&& body)
 void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vector<RayItem>& items, int& rpt,
                    std::vector<double>* item_time = nullptr)
 {
-    const int W = forward_consumer_warps(), half = forward_ring_stages() - 1;
+    const int W = forward_consumer_warps(), half = forward_ring(lc, c->P) - 1;
     const int nch = layout_lines(c->n) / lc;
     struct Deal {
         std::vector<std::vector<int>> lists;
@@ -1032,7 +1036,7 @@ void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vect
         }
         if (item_time) {
             // the block's time in a model of the ring: a warp may start chunk ch
-            // once every warp has released chunk ch - kStages; a group's chunk
+            // once every warp has released chunk ch - stages; a group's chunk
             // costs 2.8 + its angle's load wavefronts (the fit of measured block
             // times), plus a fixed share per chunk
             const int S = half + 1;
@@ -1132,13 +1136,14 @@ void plan_forward(const mc_ctx* c, int lc, int sms, int ipb_start, int refine, G
 mc_status build_tables(mc_ctx* c)
 {
     const int n = c->n, na = c->na, nb = c->nb;
-    // line layouts: kGuard zero pairs in front, >= kGuard behind, 16-byte
-    // pitch, lines padded to whole chunks; chunks of lc in {8, 4, 2} lines per
-    // ring stage (five stages of at most 36 KB in the one block per SM)
-    c->P = layout_pitch(n);
+    // line layouts: `guard` zero pairs in front, >= guard behind, 16-byte
+    // pitch, lines padded to whole chunks; chunks of lc in {16, 8, 4, 2} lines
+    // per ring stage, the longest whose ring in the one block per SM keeps at
+    // least 3 stages (16 only with the wide guard of small images)
+    c->guard = layout_guard(n);
+    c->P = layout_pitch(n, c->guard);
     c->layout_stride = (size_t)layout_lines(n) * c->P;
-    c->lc = 8;
-    while (c->lc > 2 && (size_t)c->lc * c->P * sizeof(float2) > kMaxStageBytes) c->lc >>= 1;
+    c->lc = forward_default_lines(n, c->P, c->guard);
     std::vector<FwdAngle> fa(na);
     std::vector<BpAngle> ba(na);
     // forward group order: rows-driven angles first, then columns-driven; in
@@ -1704,9 +1709,9 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
     // forward: chunk lines x items per block x group slots per warp
     int best_lc = c->lc, best_ipb = c->ipb, best_rpt = c->rpt;
     float best = 1e30f;
-    for (int lc : {2, 4, 8}) {
+    for (int lc : {2, 4, 8, 16}) {
         if (st != MC_OK) break;
-        if ((size_t)lc * c->P * sizeof(float2) > kMaxStageBytes) continue;
+        if (!forward_lines_fit(c->n, c->P, c->guard, lc)) continue;   // guard, whole chunks, ring
         int ipb0 = 0;
         for (int step = 0; step < 3 && st == MC_OK; ++step) {
             const int ipb_try = ipb0 ? ipb0 + step : 1;
@@ -2248,6 +2253,25 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
         if (norms) TRY(mc_set_norms(c, n2.data()));
         return MC_OK;
     }
+    case MC_OPT_FORWARD_LINES: {
+        const int lc = (int)value;
+        if (lc != 2 && lc != 4 && lc != 8 && lc != 16)
+            return fail(c, MC_EINVAL, "forward lines per chunk must be 2, 4, 8 or 16");
+        if (!forward_lines_fit(c->n, c->P, c->guard, lc))
+            return fail(c, MC_EINVAL, "chunks of %d lines do not fit this context's layouts (n = %d: %d guard "
+                                      "pairs, room for %d ring stages, %d lines)", lc, c->n, c->guard,
+                        forward_stages(lc, c->P), layout_lines(c->n));
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        TRY(install_forward_tables(c, lc, 1, 0, kPlanRounds));
+        if (c->S > 1) {               // the subset tables follow the chunk size
+            const bool norms = c->have_norms;
+            const std::vector<double> n2 = c->norms2;
+            TRY(mc_set_subsets(c, c->S));
+            if (norms) TRY(mc_set_norms(c, n2.data()));
+        }
+        return finish(c);
+    }
     case MC_OPT_SUBSET_ROWS:
         if (value != 0 && value != 4 && value != 8 && value != 14 && value != 16)
             return fail(c, MC_EINVAL, "subset rows per thread must be 0, 4, 8, 14 or 16");
@@ -2415,14 +2439,24 @@ namespace {
 // The launches of one batched iteration for the slices 0 .. A-1 of the
 // batch's order (those still running): block maps per stage and class, and
 // the captured graph of each parity of the iteration index.
+// The forward blocks of the slices in flight that share one chunk size and
+// ring (one compiled kernel): their block map range, the most group slots per
+// warp among them and the largest ring.
+struct FwdClass {
+    size_t off = 0;
+    int n = 0, rpt = 2, lc = 8, ns = 5;
+    size_t smem = 0;
+};
+
 struct BatchPhase {
     BatchBlock* d_map = nullptr;             // every map of the phase, one allocation
     int plan = 0;                            // forward work items: 0 each slice's own, 1 the batch's
     int n_warp = 0, n_wadj = 0;
     size_t off_warp = 0, off_wadj = 0;
-    int n_fwd = 0, fwd_rpt = 2, fwd_pairs = 0, n_bp = 0;
-    int fwd_lc = 0, bp_pj = 0;               // > 0: every slice in flight has these (compiled shape)
-    size_t off_fwd = 0, off_bp = 0;
+    std::vector<FwdClass> fwd;               // one forward launch per class, classes concurrent
+    int n_bp = 0;
+    int bp_pj = 0;                           // > 0: every slice in flight has this tile height
+    size_t off_bp = 0;
     cudaGraphExec_t g[2][2] = {};            // [1 or kBatchGraphIters iterations][start parity]
 };
 
@@ -2464,6 +2498,11 @@ struct mc_batch {
     WarpAdjArgs h_wadj[2] = {};
     std::vector<BatchPhase> phase;           // [A - 1] for A slices in flight, built on demand
     std::vector<cudaEvent_t> ev;             // one per slice (hand-off between streams) + 1
+    // forward classes after the first run on side streams: a fork before and a
+    // join after (graph branches once captured)
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join_ev;
+    cudaEvent_t fork_ev = nullptr;
 };
 
 namespace {
@@ -2510,6 +2549,12 @@ void batch_free(mc_batch* b)
     b->d_bitems.clear();
     for (auto e : b->ev) cudaEventDestroy(e);
     b->ev.clear();
+    for (auto e : b->join_ev) cudaEventDestroy(e);
+    b->join_ev.clear();
+    for (auto q : b->side) cudaStreamDestroy(q);
+    b->side.clear();
+    if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+    b->fork_ev = nullptr;
 }
 
 template <class T>
@@ -2555,6 +2600,7 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
             a.rigid = c->d_rigid; a.field = c->d_field; a.identity = 0;
             a.sel = sel; a.n_slots = 1;
             a.lrow = c->d_lrow; a.lcol = c->d_lcol; a.layout_stride = c->layout_stride; a.P = c->P;
+            a.guard = c->guard;
             WarpAdjArgs& u = wa[t][q];
             u = wadj_args(c, sel, 1, c->d_b);
             u.z = c->d_z; u.x_in = c->d_x[c->cur ^ t]; u.x_out = c->d_x[c->cur ^ t ^ 1];
@@ -2565,8 +2611,10 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
             FwdArgs& fa = f[0][t][q];
             fa = FwdArgs{};
             fa.lrow = c->d_lrow; fa.lcol = c->d_lcol; fa.layout_stride = c->layout_stride; fa.P = c->P;
+            fa.guard = c->guard;
             fa.ang = c->d_fang; fa.groups = c->d_groups; fa.items = c->d_items; fa.n_items = c->n_items;
             fa.ipb = c->ipb; fa.rpt = c->rpt; fa.lc = c->lc; fa.n = c->n; fa.na = c->na; fa.nb = c->nb;
+            fa.stages = forward_ring(c->lc, c->P);
             fa.sel = sel; fa.n_slots = 1; fa.wait_limit = 1u << 24;
             fa.dy = c->d_dy; fa.dy_stride = c->dy_stride; fa.Pb = c->Pb; fa.Gb = c->Gb; fa.err = c->d_err;
             fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y;
@@ -2649,8 +2697,8 @@ mc_status batch_phase(mc_batch* b, int A)
         ph.off_warp = r.first; ph.n_warp = r.second;
     }
     // forward: the batch's coarser work items while they still give every SM
-    // a few blocks, else each slice's own; per lines-per-chunk class; a
-    // block's work ~ samples / blocks
+    // a few blocks, else each slice's own; one class (and launch) per chunk
+    // size and ring; a block's work ~ samples / blocks
     {
         long long coarse = 0;
         for (int i : q) coarse += b->b_nitems[i];
@@ -2661,19 +2709,47 @@ mc_status batch_phase(mc_batch* b, int A)
     };
     auto f_rpt = [&](int i) { return ph.plan ? b->b_rpt[i] : C(i)->rpt; };
     {
-        ph.fwd_lc = C(q[0])->lc;
-        ph.bp_pj = C(q[0])->pj;
+        std::vector<std::pair<int, int>> keys;          // (lc, ring stages), in order of appearance
+        std::vector<std::vector<int>> members;
         for (int i : q) {
-            ph.fwd_rpt = std::max(ph.fwd_rpt, f_rpt(i));
-            ph.fwd_pairs = std::max(ph.fwd_pairs, C(i)->lc * C(i)->P);
-            if (C(i)->lc != ph.fwd_lc) ph.fwd_lc = 0;
-            if (C(i)->pj != ph.bp_pj) ph.bp_pj = 0;
+            const std::pair<int, int> k{C(i)->lc, forward_ring(C(i)->lc, C(i)->P)};
+            size_t j = 0;
+            while (j < keys.size() && keys[j] != k) ++j;
+            if (j == keys.size()) { keys.push_back(k); members.emplace_back(); }
+            members[j].push_back(i);
         }
-        auto r = add(q, f_blocks, [&](int i) {
-            const mc_ctx* c = C(i);
-            return (double)c->na * c->n * c->n / f_blocks(i);
-        });
-        ph.off_fwd = r.first; ph.n_fwd = r.second;
+        ph.fwd.clear();
+        for (size_t j = 0; j < keys.size(); ++j) {
+            FwdClass fc;
+            fc.lc = keys[j].first;
+            fc.ns = keys[j].second;
+            for (int i : members[j]) {
+                fc.rpt = std::max(fc.rpt, f_rpt(i));
+                fc.smem = std::max(fc.smem, forward_smem_bytes(C(i)->lc, C(i)->P));
+            }
+            auto r = add(members[j], f_blocks, [&](int i) {
+                const mc_ctx* c = C(i);
+                return (double)c->na * c->n * c->n / f_blocks(i);
+            });
+            fc.off = r.first;
+            fc.n = r.second;
+            ph.fwd.push_back(fc);
+        }
+        // side streams and events for the classes after the first
+        while (b->side.size() + 1 < ph.fwd.size()) {
+            cudaStream_t q2 = nullptr;
+            cudaEvent_t e2 = nullptr;
+            BCK(cudaStreamCreateWithFlags(&q2, cudaStreamNonBlocking));
+            b->side.push_back(q2);
+            BCK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+            b->join_ev.push_back(e2);
+        }
+        if (ph.fwd.size() > 1 && !b->fork_ev) BCK(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
+    }
+    {
+        ph.bp_pj = C(q[0])->pj;
+        for (int i : q)
+            if (C(i)->pj != ph.bp_pj) ph.bp_pj = 0;
     }
     // backprojection: each slice's own tile height; a tile's work ~ angles x rows
     {
@@ -2708,8 +2784,20 @@ mc_status batch_enqueue(mc_batch* b, int A, int t, int iters)
             continue;
         }
         BCK(launch_warp_layouts_batch(b->d_warp[t], ph.d_map + ph.off_warp, ph.n_warp, s));
-        BCK(launch_forward_batch(b->d_fwd[ph.plan][t], ph.d_map + ph.off_fwd, ph.n_fwd, ph.fwd_rpt, ph.fwd_pairs,
-                                 ph.fwd_lc, s));
+        // the forward: one launch per class, the classes after the first on
+        // side streams between a fork and a join, so that they run together
+        const FwdArgs* fa = b->d_fwd[ph.plan][t];
+        if (ph.fwd.size() > 1) BCK(cudaEventRecord(b->fork_ev, s));
+        for (size_t k = 1; k < ph.fwd.size(); ++k) {
+            const FwdClass& fc = ph.fwd[k];
+            cudaStream_t q2 = b->side[k - 1];
+            BCK(cudaStreamWaitEvent(q2, b->fork_ev, 0));
+            BCK(launch_forward_batch(fa, ph.d_map + fc.off, fc.n, fc.rpt, fc.smem, fc.lc, fc.ns, q2));
+            BCK(cudaEventRecord(b->join_ev[k - 1], q2));
+        }
+        const FwdClass& f0 = ph.fwd[0];
+        BCK(launch_forward_batch(fa, ph.d_map + f0.off, f0.n, f0.rpt, f0.smem, f0.lc, f0.ns, s));
+        for (size_t k = 1; k < ph.fwd.size(); ++k) BCK(cudaStreamWaitEvent(s, b->join_ev[k - 1], 0));
         BCK(launch_backproject_batch(b->d_bp[t], ph.d_map + ph.off_bp, ph.n_bp, ph.bp_pj, s));
         BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, b->d_draw, t, s));
     }

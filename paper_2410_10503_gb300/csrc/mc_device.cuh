@@ -3,9 +3,9 @@
 // HBM layouts (per gate slot):
 //   line layouts  Two copies of the warped image w = D_i x, each as
 //                 layout_lines(n) lines (n rounded up to a multiple of 8, the
-//                 extra lines zero) of pitch P = layout_pitch(n) float2
-//                 "pairs" (w[p], w[p+1] - w[p]) with kGuard zero cells before
-//                 the data and at least kGuard after it:
+//                 extra lines zero) of pitch P = layout_pitch(n, guard) float2
+//                 "pairs" (w[p], w[p+1] - w[p]) with `guard` zero cells before
+//                 the data and at least `guard` after it:
 //                 ROWS  line l = image row l    (used by rows-driven angles),
 //                 COLS  line l = image column l (used by columns-driven angles).
 //                 One 8-byte load gives both interpolation taps, and the zero
@@ -24,15 +24,55 @@
 
 namespace mcg {
 
-constexpr int kGuard = 17;                // zero cells before each image line
+// Zero pairs before each image line of a layout (and at least as many after
+// it): the forward projector's clamped chunk positions need 2 LC + 1 of them
+// for chunks of LC lines, so 17 serve chunks of up to 8 lines and 33 chunks of
+// 16.  A context takes the wide guard only where a ring of 16-line chunks with
+// at least 3 stages fits (small images); wider lines cost staged bytes.
+constexpr int kGuardNarrow = 17, kGuardWide = 33;
+__host__ __device__ constexpr int guard_max_lines(int guard) { return (guard - 1) / 2; }
 
-// Lines and pitch (pairs) of a line layout: whole chunks of up to 8 lines, and
-// room for the forward projector's clamped chunk positions (kGuard >= 2 x 8 + 1
-// zero pairs in front, P >= n + 2 kGuard).
+// Lines and pitch (pairs) of a line layout: whole chunks of 8 lines (16 where
+// the line count allows), and a pitch P >= n + 2 guard.
 __host__ __device__ constexpr int layout_lines(int n) { return (n + 7) / 8 * 8; }
-__host__ __device__ constexpr int layout_pitch(int n) { return (n + 2 * kGuard + 3) / 4 * 4; }
-// Largest ring stage (bytes) of the forward projector: lc lines x P pairs.
-constexpr size_t kMaxStageBytes = 36864;
+__host__ __device__ constexpr int layout_pitch(int n, int guard) { return (n + 2 * guard + 3) / 4 * 4; }
+// Stages of lc lines x P pairs that kRingBytes of shared memory (what a block
+// has beside its static tables) holds, at most kMaxStages.
+constexpr int kMaxStages = 5;
+constexpr size_t kRingBytes = 221440;
+__host__ __device__ constexpr int forward_stages(int lc, int P)
+{
+    return kRingBytes / ((size_t)lc * P * 8) < (size_t)kMaxStages ? (int)(kRingBytes / ((size_t)lc * P * 8))
+                                                                  : kMaxStages;
+}
+// The ring a chunk size runs with (the kernels are compiled for these): five
+// stages, or three for 16-line chunks and for 8-line chunks whose five stages
+// do not fit (large images); 4- and 2-line chunks always fit five.
+__host__ __device__ constexpr int forward_ring(int lc, int P)
+{
+    return lc >= 16 ? 3 : (lc == 8 && forward_stages(lc, P) < 5 ? 3 : 5);
+}
+// Whether chunks of lc lines can run on layouts of n lines, pitch P and the
+// given guard: whole chunks, the guard's clamp reach, and room for the ring.
+__host__ __device__ constexpr bool forward_lines_fit(int n, int P, int guard, int lc)
+{
+    return (lc == 2 || lc == 4 || lc == 8 || lc == 16) && lc <= guard_max_lines(guard) &&
+           layout_lines(n) % lc == 0 && forward_stages(lc, P) >= forward_ring(lc, P);
+}
+// The default chunk: the longest that fits (measured: 16-line chunks in three
+// stages beat 8-line ones at 128^2-384^2; a two-stage ring of 16-line chunks
+// lost inside the iteration at 512^2, so such sizes keep the narrow guard).
+__host__ __device__ constexpr int forward_default_lines(int n, int P, int guard)
+{
+    return forward_lines_fit(n, P, guard, 16) ? 16
+         : forward_lines_fit(n, P, guard, 8)  ? 8
+         : forward_lines_fit(n, P, guard, 4)  ? 4 : 2;
+}
+// The guard of a context's layouts: wide where 16-line chunks fit their ring.
+__host__ __device__ constexpr int layout_guard(int n)
+{
+    return forward_lines_fit(n, layout_pitch(n, kGuardWide), kGuardWide, 16) ? kGuardWide : kGuardNarrow;
+}
 constexpr float kMagic = 12582912.0f;     // 1.5 * 2^23
 constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 

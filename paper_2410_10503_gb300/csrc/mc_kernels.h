@@ -76,6 +76,7 @@ struct WarpArgs {
     float2* lcol;
     size_t layout_stride;
     int P;                     // line pitch (pairs)
+    int guard;                 // zero pairs before each line's data (layout_guard)
     float* out;                // plain mode: n*n per slot
 };
 cudaError_t launch_warp_layouts(const WarpArgs& a, cudaStream_t s);
@@ -148,7 +149,10 @@ struct FwdArgs {
     float* part;               //      kernel adds them and runs the epilogue
     int ipb;                   // items per block (one block per SM)
     int rpt;                   // group slots per consumer warp (2, 4, 8)
-    int lc;                    // lines per staged chunk (2, 4, 8)
+    int guard;                 // zero pairs before each line's data (>= 2 lc + 1)
+    int lc;                    // lines per staged chunk (2, 4, 8, 16)
+    int stages;                // ring stages: forward_ring(lc, P) (launch_forward sets it;
+                               // batched argument tables carry it)
     int n, na, nb;
     GateSel sel;
     int n_slots;
@@ -177,14 +181,14 @@ struct FwdArgs {
 cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 // batched (all angles, one slot per slice, no bands): block b runs block
 // map[b].block of slice map[b].slice's item table with that slice's lines per
-// chunk (args[slice].lc: 8, 4 or 2); every slice of the launch has at most rpt
-// group slots per warp; smem_pairs = the largest lc x P of the launch's slices;
-// lc > 0: every slice has those lines per chunk (a kernel compiled for them)
+// chunk (args[slice].lc: 16, 8, 4 or 2) and ring stages (args[slice].stages,
+// forward_ring); every slice of the launch has lc lines per chunk, a ring of
+// `stages` stages (the kernel is compiled for both) and at most rpt group
+// slots per warp; smem_bytes = the largest forward_smem_bytes of its slices
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
-                                 int smem_pairs, int lc, cudaStream_t s);
+                                 size_t smem_bytes, int lc, int stages, cudaStream_t s);
 int forward_groups_per_block(int rpt);
 int forward_consumer_warps();         // consumer warps per block
-int forward_ring_stages();            // chunks in flight (the drift between warps)
 int forward_static_smem();           // static shared memory of the largest instance
 size_t forward_smem_bytes(int lc, int P);
 cudaError_t forward_prepare(int max_smem);

@@ -239,9 +239,8 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
 
     // sizes: same line pitch and chunking as the context path; items of at
     // most gpi groups, gpi sized for one block per SM
-    const int P = layout_pitch(n);
-    int lc = 8;
-    while (lc > 2 && (size_t)lc * P * sizeof(float2) > kMaxStageBytes) lc >>= 1;
+    const int P = layout_pitch(n, kGuardNarrow);
+    const int lc = forward_default_lines(n, P, kGuardNarrow);
     const int gpa = (nb + 31) / 32;
     const int kx0 = (na + 3) / 4, kx1 = (3 * na) / 4;
     const int ny = kx0 + (na - 1 - kx1);
@@ -289,9 +288,11 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     w.x = x; w.n = n; w.rigid = d_rg; w.field = nullptr; w.identity = rigid ? 0 : 1;
     w.sel = GateSel{nullptr, 0}; w.n_slots = 1;
     w.lrow = d_lrow; w.lcol = d_lcol; w.layout_stride = (size_t)layout_lines(n) * P; w.P = P;
+    w.guard = kGuardNarrow;
     if (e == cudaSuccess) e = launch_warp_layouts(w, s);
     FwdArgs f{};
     f.lrow = d_lrow; f.lcol = d_lcol; f.layout_stride = (size_t)layout_lines(n) * P; f.P = P;
+    f.guard = kGuardNarrow;
     f.ang = d_ang; f.groups = d_groups; f.items = d_items; f.n_items = n_items;
     f.ipb = ipb; f.rpt = rpt; f.lc = lc; f.n = n; f.na = na; f.nb = nb;
     f.sel = GateSel{nullptr, 0}; f.n_slots = 1; f.mode = 0; f.out = out; f.err = d_err;

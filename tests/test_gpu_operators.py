@@ -216,13 +216,13 @@ def test_autotune_keeps_parity(mc):
     x = S.phantom(n, 10, 22, 5, 40)
     y = S.random_sinogram(na, nb, 23)
     t = ctx.autotune(reps=2)
-    assert t["lines_per_chunk"] in (2, 4, 8) and t["rows_per_thread"] in (4, 8, 14, 16)
+    assert t["lines_per_chunk"] in (2, 4, 8, 16) and t["rows_per_thread"] in (4, 8, 14, 16)
     assert t["group_slots"] in (2, 4, 8) and t["items_per_block"] >= 1
     for i in range(N):
         assert rel_l2(host(ctx.forward(i, cuda(x))), O.Ai(x, P, i)) <= TOL
         assert rel_l2(host(ctx.adjoint(i, cuda(y))), O.Ait(y, P, i)) <= TOL
     fresh = mc.Context(n, na, nb, N, rigid=rig)
-    if t["lines_per_chunk"] == 8:
+    if t["lines_per_chunk"] == 16:     # the creation-time chunk at 128^2 (wide guard, 5-stage ring)
         np.testing.assert_array_equal(host(ctx.forward(1, cuda(x))), host(fresh.forward(1, cuda(x))))
 
 
@@ -236,3 +236,39 @@ def test_shared_load_peak_is_plausible(mc):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     ghz = r["bytes_per_s"] / (r["bytes_per_clk_per_sm"] * sms) / 1e9
     assert abs(ghz - r["sm_ghz"]) <= 0.05 * r["sm_ghz"], r
+
+
+# forward chunk sizes (MC_OPT_FORWARD_LINES), each against the oracle: small
+# images get layouts with the wide guard and 16-line chunks (384^2: a 3-stage
+# ring, 96^2 and 256^2: 5 stages); at 512^2 a 16-line ring would keep 2 stages,
+# so its layouts keep the narrow guard and 16-line chunks are refused
+@pytest.mark.parametrize("n,na,nb", [(512, 20, 517), (384, 24, 401), (256, 45, 300), (96, 30, 101)])
+@pytest.mark.parametrize("lc", [2, 4, 8, 16])
+def test_forward_chunk_sizes_match_oracle(mc, n, na, nb, lc):
+    from paper_2410_10503_gb300 import _native as N
+    g = O.Geometry(n, na, nb)
+    rig = _rigid(2, 41, rot=8.0, shift=6.0)
+    ctx = mc.Context(n, na, nb, 2, rigid=rig)
+    if n == 512 and lc == 16:
+        with pytest.raises(mc.MCError, match="guard"):
+            ctx.set_option(N.MC_OPT_FORWARD_LINES, lc)
+        ctx.close()
+        return
+    ctx.set_option(N.MC_OPT_FORWARD_LINES, lc)
+    P = O.Problem(g, O.Motion(rigid=rig), np.zeros((2, na, nb)), 1.0)
+    x = S.phantom(n, 6, 42, n / 16 + 0.5, n / 4 + 1)
+    y = S.random_sinogram(na, nb, 43)
+    assert rel_l2(host(ctx.project(cuda(x))), O.A(x, g)) <= TOL
+    assert rel_l2(host(ctx.forward(1, cuda(x))), O.Ai(x, P, 1)) <= TOL
+    assert rel_l2(host(ctx.adjoint(1, cuda(y))), O.Ait(y, P, 1)) <= TOL
+    ctx.close()
+
+
+def test_forward_chunk_size_refusals(mc):
+    from paper_2410_10503_gb300 import _native as N
+    ctx = mc.Context(520, 8, 40, 1, rigid=np.zeros((1, 3)))   # 520 lines: not whole 16-line chunks
+    for bad in (16, 3, 32):
+        with pytest.raises(mc.MCError):
+            ctx.set_option(N.MC_OPT_FORWARD_LINES, bad)
+    ctx.set_option(N.MC_OPT_FORWARD_LINES, 8)
+    ctx.close()
