@@ -204,14 +204,14 @@ mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out)
 /* Tune the launch shapes of the two projectors for this context's geometry
  * by timing them on the device (each candidate `reps` launches after one
  * warm-up, CUDA events on the context's stream): the forward's lines per
- * staged chunk (2, 4, 8, as shared memory allows), work items per block and
+ * staged chunk (2, 4, 8, 16, as the layouts and shared memory allow), work items per block and
  * ray-group slots per warp, and the backprojector's rows per thread (4, 8,
  * 14, 16).  The fastest setting is kept; results are unchanged bit for bit by
  * the item split and change within float32 rounding with the chunk size and
  * rows per thread.  out (nullable, host, 4 int32): {lines per chunk, items per
  * block, group slots per warp, rows per thread}.  Captured epoch graphs are
- * dropped.  The creation-time choice is a heuristic (largest chunk that
- * fits, fewest items, rows per thread giving ~24 warps per SM).  With angle
+ * dropped.  The creation-time choice is a heuristic (the longest chunk whose
+ * ring fits, fewest items, rows per thread giving ~24 warps per SM).  With angle
  * subsets (mc_set_subsets, S > 1) it also picks the subset forward's line
  * bands (MC_OPT_SUBSET_BANDS: 1, 2, 3, 4, 6 or 8, timed on the S blocks of
  * gate 0) and leaves the option at that value; norms, step sizes and
