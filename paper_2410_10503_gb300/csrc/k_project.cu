@@ -21,15 +21,16 @@
 // position is carried as an integer plus a float fraction: computed in
 // float-pair arithmetic at its first line, advanced between chunks by the
 // angle's exact integer/fraction split of LC * t, and stepped by j * t inside
-// a chunk, so interpolation weights stay exact to ~1e-6 px.  Every line has
-// G = a.guard >= 2 LC + 1 zero pairs in front and at least G behind
-// (P >= n + 2 G), and each chunk's starting pair index ui is clamped to
-// [LC - 1, G + n + LC - 1].  With |t| <= 1 and a fraction in [0, 1] a chunk's
-// samples lie at pair indices ui - (LC - 1) .. ui + LC, so every lane stays
-// inside its line (at most index G + n + 2 LC - 1 <= P - 1); and a lane is
-// clamped only when all of its samples in the chunk fall on zero pairs
-// (indices up to 2 LC - 1 <= G - 2 in front, from G + n behind), where the
-// clamped samples read zeros too.  So the rays of a group that leave the image inside a chunk, or miss
+// a chunk, so interpolation weights stay exact to ~1e-6 px.  A chunk is
+// sampled in parts of CL lines (CL = LC, or 8 for a 16-line chunk on layouts
+// with the narrow guard); every line has G = a.guard >= 2 CL + 1 zero pairs
+// in front and at least G behind (P >= n + 2 G), and each part's starting
+// pair index ui is clamped to [CL - 1, G + n + CL - 1].  With |t| <= 1 and a
+// fraction in [0, 1] a part's samples lie at pair indices ui - (CL - 1) ..
+// ui + CL, so every lane stays inside its line (at most index
+// G + n + 2 CL - 1 <= P - 1); and a lane is clamped only when all of its
+// samples in the part fall on zero pairs (indices up to 2 CL - 1 <= G - 2 in
+// front, from G + n behind), where the clamped samples read zeros too.  So the rays of a group that leave the image inside a chunk, or miss
 // it, need no predication and no separate edge path.
 #include "mc_kernels.h"
 
@@ -255,7 +256,7 @@ struct SlotRec {
 // One block's work: items bx * ipb .. of the launch's item table for gate
 // slot `slot`; nbx = blocks sharing the table (the CSR prefetch is split
 // among them).
-template <int RPT, int LC, int NS, bool BANDED>
+template <int RPT, int LC, int NS, int CL, bool BANDED>
 __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot, int nbx, SlotState* s_slot,
                                               SlotRec* s_rec)
 {
@@ -350,18 +351,20 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     const float hb = 0.5f * (float)(nb - 1);
     const int guard = a.guard;
     const float off = h + (float)guard;
-    float mj[LC];
+    static_assert(LC % CL == 0, "a chunk is whole sampling parts");
+    float mj[CL];
 #pragma unroll
-    for (int j = 0; j < LC; ++j) mj[j] = kMagic + (float)(j * a.P);
+    for (int j = 0; j < CL; ++j) mj[j] = kMagic + (float)(j * a.P);
     SlotState* my = s_slot + warp * RPT;
-    unsigned long long jj[LC / 2], mm[LC / 2];
+    unsigned long long jj[CL / 2], mm[CL / 2];
 #pragma unroll
-    for (int q = 0; q < LC / 2; ++q) {
+    for (int q = 0; q < CL / 2; ++q) {
         jj[q] = pk2(-(float)(2 * q), -(float)(2 * q + 1));
         mm[q] = pk2(mj[2 * q], mj[2 * q + 1]);
     }
-    // clamp of a chunk's first-line pair index (see the file comment)
-    const int ui_lo = LC - 1, ui_hi = guard + n + LC - 1;
+    // clamp of a part's first-line pair index (see the file comment; a chunk is
+    // sampled in LC / CL parts of CL lines, each clamped on its own)
+    const int ui_lo = CL - 1, ui_hi = guard + n + CL - 1;
 
     int q_run = 0;                        // BANDED: chunks consumed so far
     for (int it = 0; it < n_it; ++it) {
@@ -442,19 +445,23 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
             for (int m = 0; m < RPT; ++m) {
                 if (!((act >> m) & 1u)) continue;
                 const float4 gs = *reinterpret_cast<const float4*>(my + m);   // {t, t, step_frac, step_int}
-                const int ib = min(max(ui[m], ui_lo), ui_hi) - kMagicBits;
+#pragma unroll
+                for (int part = 0; part < LC / CL; ++part) {
+                    const int ib = min(max(ui[m], ui_lo), ui_hi) - kMagicBits;
+                    const float2* pp = sp + (size_t)part * CL * a.P;
 #ifdef MC_CHECKED
-                acc[m] = sample_lines<LC>(sp, ib, frac[m], gs.x, mj, acc[m], a.P, a.err);
+                    acc[m] = sample_lines<CL>(pp, ib, frac[m], gs.x, mj, acc[m], a.P, a.err);
 #else
-                const uint32_t gbase = (uint32_t)__cvta_generic_to_shared(sp) + ((uint32_t)ib << 3);
-                acc[m] = sample_interior<LC>(gbase, pk2(gs.x, gs.y), pk2(frac[m], frac[m]), jj, mm, acc[m]);
+                    const uint32_t gbase = (uint32_t)__cvta_generic_to_shared(pp) + ((uint32_t)ib << 3);
+                    acc[m] = sample_interior<CL>(gbase, pk2(gs.x, gs.y), pk2(frac[m], frac[m]), jj, mm, acc[m]);
 #endif
-                // advance to the first line of the next chunk: u -= LC * t
-                float nf = frac[m] - gs.z;
-                int nu = ui[m] - __float_as_int(gs.w);
-                if (nf < 0.0f) { nf += 1.0f; nu -= 1; }
-                frac[m] = nf;
-                ui[m] = nu;
+                    // advance to the first line of the next part: u -= CL * t
+                    float nf = frac[m] - gs.z;
+                    int nu = ui[m] - __float_as_int(gs.w);
+                    if (nf < 0.0f) { nf += 1.0f; nu -= 1; }
+                    frac[m] = nf;
+                    ui[m] = nu;
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
@@ -526,21 +533,21 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     }
 }
 
-template <int RPT, int LC, int NS, bool BANDED>
+template <int RPT, int LC, int NS, int CL, bool BANDED>
 __global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
 {
     pdl_wait();
     pdl_trigger();
     __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
     __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
-    forward_block<RPT, LC, NS, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
+    forward_block<RPT, LC, NS, CL, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
 }
 
 // Batched: the blocks of every slice of the launch, each on its slice's item
 // table with its slice's arguments (all angles, one slot, no bands); every
 // slice of the launch has LC lines per chunk and an NS-stage ring (the batch
 // launches one such class per chunk size and ring).
-template <int RPT, int LC, int NS>
+template <int RPT, int LC, int NS, int CL>
 __global__ void __launch_bounds__(kBlock, 1) k_forward_batch_lc(const FwdArgs* __restrict__ args,
                                                                 const BatchBlock* __restrict__ map)
 {
@@ -549,7 +556,7 @@ __global__ void __launch_bounds__(kBlock, 1) k_forward_batch_lc(const FwdArgs* _
     __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
     __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
     const BatchBlock m = map[blockIdx.x];
-    forward_block<RPT, LC, NS, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
+    forward_block<RPT, LC, NS, CL, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
 }
 
 // Sum of the bands' partial ray sums in band order, then the epilogue of
@@ -613,27 +620,29 @@ size_t forward_smem_bytes(int lc, int P)
     return 128 + (size_t)forward_ring(lc, P) * lc * P * sizeof(float2);
 }
 
-// (group slots per warp, lines per chunk, ring stages)
+// (group slots per warp, lines per chunk, ring stages, lines per clamped part)
 #define MC_FWD_INSTANCES(X) \
-    X(2, 2, 5) X(4, 2, 5) X(8, 2, 5) X(2, 4, 5) X(4, 4, 5) X(8, 4, 5) X(2, 8, 5) X(4, 8, 5) X(8, 8, 5) \
-    X(2, 8, 3) X(4, 8, 3) X(8, 8, 3) X(2, 16, 3) X(4, 16, 3) X(8, 16, 3)
+    X(2, 2, 5, 2) X(4, 2, 5, 2) X(8, 2, 5, 2) X(2, 4, 5, 4) X(4, 4, 5, 4) X(8, 4, 5, 4) \
+    X(2, 8, 5, 8) X(4, 8, 5, 8) X(8, 8, 5, 8) X(2, 8, 3, 8) X(4, 8, 3, 8) X(8, 8, 3, 8) \
+    X(2, 16, 3, 16) X(4, 16, 3, 16) X(8, 16, 3, 16) X(2, 16, 3, 8) X(4, 16, 3, 8) X(8, 16, 3, 8)
 
 cudaError_t forward_prepare(int max_smem)
 {
     cudaError_t e = cudaSuccess;
-#define MC_SET_ATTR(R, L, NS)                                                                      \
+#define MC_SET_ATTR(R, L, NS, CL)                                                                  \
     if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward<R, L, NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+        e = cudaFuncSetAttribute(k_forward<R, L, NS, CL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  max_smem);                                                       \
     if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward<R, L, NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+        e = cudaFuncSetAttribute(k_forward<R, L, NS, CL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                  max_smem);                                                       \
 
     MC_FWD_INSTANCES(MC_SET_ATTR)
 #undef MC_SET_ATTR
-#define MC_SET_ATTR_B(R, L, NS)                                                                    \
+#define MC_SET_ATTR_B(R, L, NS, CL)                                                                \
     if (e == cudaSuccess)                                                                         \
-        e = cudaFuncSetAttribute(k_forward_batch_lc<R, L, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+        e = cudaFuncSetAttribute(k_forward_batch_lc<R, L, NS, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 max_smem);
     MC_FWD_INSTANCES(MC_SET_ATTR_B)
 #undef MC_SET_ATTR_B
     return e;
@@ -643,20 +652,21 @@ cudaError_t launch_forward(const FwdArgs& a_in, cudaStream_t s)
 {
     FwdArgs a = a_in;
     a.stages = forward_ring(a.lc, a.P);
+    a.cl = forward_part_lines(a.lc, a.guard);
     if (!forward_lines_fit(a.n, a.P, a.guard, a.lc) || a.P < a.n + 2 * a.guard) return cudaErrorInvalidValue;
     if (a.nbands > 1 && (a.n_slots != 1 || !a.part)) return cudaErrorInvalidValue;   // one partial buffer
     const dim3 grid((a.n_items + a.ipb - 1) / a.ipb, a.n_slots);
     const size_t smem = forward_smem_bytes(a.lc, a.P);
-#define MC_LAUNCH(R, L, NS)                                                               \
-    if (a.rpt == R && a.lc == L && a.stages == NS) {                                      \
+#define MC_LAUNCH(R, L, NS, CL)                                                           \
+    if (a.rpt == R && a.lc == L && a.stages == NS && a.cl == CL) {                        \
         if (a.nbands > 1) {                                                               \
-            cudaError_t e = pdl_launch(k_forward<R, L, NS, true>, grid, dim3(kBlock), smem, s, a);  \
+            cudaError_t e = pdl_launch(k_forward<R, L, NS, CL, true>, grid, dim3(kBlock), smem, s, a); \
             if (e != cudaSuccess) return e;                                               \
             const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;                          \
             const int rays = ((a.na + S - 1) / S) * a.nb;                                 \
             return pdl_launch(k_forward_combine, dim3((rays + 255) / 256, a.n_slots), dim3(256), 0, s, a); \
         } else {                                                                          \
-            return pdl_launch(k_forward<R, L, NS, false>, grid, dim3(kBlock), smem, s, a); \
+            return pdl_launch(k_forward<R, L, NS, CL, false>, grid, dim3(kBlock), smem, s, a); \
         }                                                                                 \
     }
     MC_FWD_INSTANCES(MC_LAUNCH)
@@ -665,13 +675,13 @@ cudaError_t launch_forward(const FwdArgs& a_in, cudaStream_t s)
 }
 
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
-                                 size_t smem_bytes, int lc, int stages, cudaStream_t s)
+                                 size_t smem_bytes, int lc, int stages, int cl, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     const size_t smem = smem_bytes;
-#define MC_LAUNCH_B(R, L, NS)                                                               \
-    if (rpt == R && lc == L && stages == NS)                                                \
-        return pdl_launch(k_forward_batch_lc<R, L, NS>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+#define MC_LAUNCH_B(R, L, NS, CL)                                                           \
+    if (rpt == R && lc == L && stages == NS && cl == CL)                                    \
+        return pdl_launch(k_forward_batch_lc<R, L, NS, CL>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
     MC_FWD_INSTANCES(MC_LAUNCH_B)
 #undef MC_LAUNCH_B
     return cudaErrorInvalidValue;

@@ -1187,7 +1187,7 @@ mc_status build_tables(mc_ctx* c)
     c->order = order;
     c->inv_k = inv_k;
     c->t_k = t_k;
-    fa = fwd_angles(c, c->lc);
+    fa = fwd_angles(c, forward_part_lines(c->lc, c->guard));
     GroupTable gt;
     build_groups(c, order, inv_k, t_k, 1, c->lc, gt);
     std::vector<RayItem> items;
@@ -1647,7 +1647,7 @@ mc_status mc_warp_adjoint(mc_ctx* c, int32_t gate, const float* v, float* out)
 // ipb_start items per block (rpt = 0: the smallest that fits, else at least rpt).
 mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min, int refine = 0)
 {
-    std::vector<FwdAngle> fa = fwd_angles(c, lc);
+    std::vector<FwdAngle> fa = fwd_angles(c, forward_part_lines(lc, c->guard));
     GroupTable gt;
     build_groups(c, c->order, c->inv_k, c->t_k, 1, lc, gt);
     std::vector<RayItem> items;
@@ -2258,9 +2258,9 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
         if (lc != 2 && lc != 4 && lc != 8 && lc != 16)
             return fail(c, MC_EINVAL, "forward lines per chunk must be 2, 4, 8 or 16");
         if (!forward_lines_fit(c->n, c->P, c->guard, lc))
-            return fail(c, MC_EINVAL, "chunks of %d lines do not fit this context's layouts (n = %d: %d guard "
-                                      "pairs, room for %d ring stages, %d lines)", lc, c->n, c->guard,
-                        forward_stages(lc, c->P), layout_lines(c->n));
+            return fail(c, MC_EINVAL, "chunks of %d lines do not fit this context's layouts (n = %d: room for "
+                                      "%d ring stages, %d lines)", lc, c->n, forward_stages(lc, c->P),
+                        layout_lines(c->n));
         CK(cudaStreamSynchronize(c->stream));
         drop_graphs(c);
         TRY(install_forward_tables(c, lc, 1, 0, kPlanRounds));
@@ -2444,7 +2444,7 @@ namespace {
 // warp among them and the largest ring.
 struct FwdClass {
     size_t off = 0;
-    int n = 0, rpt = 2, lc = 8, ns = 5;
+    int n = 0, rpt = 2, lc = 8, ns = 5, cl = 8;
     size_t smem = 0;
 };
 
@@ -2615,6 +2615,7 @@ mc_status batch_tables(mc_batch* b, const mc_sampling* sampling)
             fa.ang = c->d_fang; fa.groups = c->d_groups; fa.items = c->d_items; fa.n_items = c->n_items;
             fa.ipb = c->ipb; fa.rpt = c->rpt; fa.lc = c->lc; fa.n = c->n; fa.na = c->na; fa.nb = c->nb;
             fa.stages = forward_ring(c->lc, c->P);
+            fa.cl = forward_part_lines(c->lc, c->guard);
             fa.sel = sel; fa.n_slots = 1; fa.wait_limit = 1u << 24;
             fa.dy = c->d_dy; fa.dy_stride = c->dy_stride; fa.Pb = c->Pb; fa.Gb = c->Gb; fa.err = c->d_err;
             fa.mode = 1; fa.d = c->d_d; fa.y = c->d_y;
@@ -2709,10 +2710,11 @@ mc_status batch_phase(mc_batch* b, int A)
     };
     auto f_rpt = [&](int i) { return ph.plan ? b->b_rpt[i] : C(i)->rpt; };
     {
-        std::vector<std::pair<int, int>> keys;          // (lc, ring stages), in order of appearance
+        std::vector<std::array<int, 3>> keys;           // (lc, ring stages, part lines), in order
         std::vector<std::vector<int>> members;
         for (int i : q) {
-            const std::pair<int, int> k{C(i)->lc, forward_ring(C(i)->lc, C(i)->P)};
+            const std::array<int, 3> k{C(i)->lc, forward_ring(C(i)->lc, C(i)->P),
+                                       forward_part_lines(C(i)->lc, C(i)->guard)};
             size_t j = 0;
             while (j < keys.size() && keys[j] != k) ++j;
             if (j == keys.size()) { keys.push_back(k); members.emplace_back(); }
@@ -2721,8 +2723,9 @@ mc_status batch_phase(mc_batch* b, int A)
         ph.fwd.clear();
         for (size_t j = 0; j < keys.size(); ++j) {
             FwdClass fc;
-            fc.lc = keys[j].first;
-            fc.ns = keys[j].second;
+            fc.lc = keys[j][0];
+            fc.ns = keys[j][1];
+            fc.cl = keys[j][2];
             for (int i : members[j]) {
                 fc.rpt = std::max(fc.rpt, f_rpt(i));
                 fc.smem = std::max(fc.smem, forward_smem_bytes(C(i)->lc, C(i)->P));
@@ -2792,11 +2795,11 @@ mc_status batch_enqueue(mc_batch* b, int A, int t, int iters)
             const FwdClass& fc = ph.fwd[k];
             cudaStream_t q2 = b->side[k - 1];
             BCK(cudaStreamWaitEvent(q2, b->fork_ev, 0));
-            BCK(launch_forward_batch(fa, ph.d_map + fc.off, fc.n, fc.rpt, fc.smem, fc.lc, fc.ns, q2));
+            BCK(launch_forward_batch(fa, ph.d_map + fc.off, fc.n, fc.rpt, fc.smem, fc.lc, fc.ns, fc.cl, q2));
             BCK(cudaEventRecord(b->join_ev[k - 1], q2));
         }
         const FwdClass& f0 = ph.fwd[0];
-        BCK(launch_forward_batch(fa, ph.d_map + f0.off, f0.n, f0.rpt, f0.smem, f0.lc, f0.ns, s));
+        BCK(launch_forward_batch(fa, ph.d_map + f0.off, f0.n, f0.rpt, f0.smem, f0.lc, f0.ns, f0.cl, s));
         for (size_t k = 1; k < ph.fwd.size(); ++k) BCK(cudaStreamWaitEvent(s, b->join_ev[k - 1], 0));
         BCK(launch_backproject_batch(b->d_bp[t], ph.d_map + ph.off_bp, ph.n_bp, ph.bp_pj, s));
         BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, b->d_draw, t, s));

@@ -25,10 +25,11 @@
 namespace mcg {
 
 // Zero pairs before each image line of a layout (and at least as many after
-// it): the forward projector's clamped chunk positions need 2 LC + 1 of them
-// for chunks of LC lines, so 17 serve chunks of up to 8 lines and 33 chunks of
-// 16.  A context takes the wide guard only where a ring of 16-line chunks with
-// at least 3 stages fits (small images); wider lines cost staged bytes.
+// it): the forward projector's clamped positions need 2 CL + 1 of them for
+// parts of CL lines, so 17 serve parts of up to 8 lines and 33 whole 16-line
+// chunks.  A context takes the wide guard where a 3-stage ring of 16-line
+// chunks with such lines fits (small images); elsewhere 16-line chunks are
+// sampled in two 8-line parts.
 constexpr int kGuardNarrow = 17, kGuardWide = 33;
 __host__ __device__ constexpr int guard_max_lines(int guard) { return (guard - 1) / 2; }
 
@@ -52,16 +53,25 @@ __host__ __device__ constexpr int forward_ring(int lc, int P)
 {
     return lc >= 16 ? 3 : (lc == 8 && forward_stages(lc, P) < 5 ? 3 : 5);
 }
-// Whether chunks of lc lines can run on layouts of n lines, pitch P and the
-// given guard: whole chunks, the guard's clamp reach, and room for the ring.
+// A chunk is sampled in parts of at most as many lines as the guard's clamp
+// reaches (each part clamps its own starting position): whole chunks where
+// the guard allows, two 8-line parts of a 16-line chunk with the narrow guard.
+__host__ __device__ constexpr int forward_part_lines(int lc, int guard)
+{
+    return lc < guard_max_lines(guard) ? lc : guard_max_lines(guard);
+}
+// Whether chunks of lc lines can run on layouts of n lines and pitch P: whole
+// chunks and room for their ring.
 __host__ __device__ constexpr bool forward_lines_fit(int n, int P, int guard, int lc)
 {
-    return (lc == 2 || lc == 4 || lc == 8 || lc == 16) && lc <= guard_max_lines(guard) &&
-           layout_lines(n) % lc == 0 && forward_stages(lc, P) >= forward_ring(lc, P);
+    return (lc == 2 || lc == 4 || lc == 8 || lc == 16) && guard >= 2 * 2 + 1 && layout_lines(n) % lc == 0 &&
+           forward_stages(lc, P) >= forward_ring(lc, P);
 }
-// The default chunk: the longest that fits (measured: 16-line chunks in three
-// stages beat 8-line ones at 128^2-384^2; a two-stage ring of 16-line chunks
-// lost inside the iteration at 512^2, so such sizes keep the narrow guard).
+// The default chunk: the longest that fits (measured SPDHG epochs: 16-line
+// chunks in three stages beat 8-line ones at 128^2-384^2 with the wide guard
+// and at 512^2 in two 8-line parts with the narrow one, 1.661 against 1.704
+// ms; 8-line chunks in three stages beat 4-line ones in five at 768^2 and
+// 1024^2).
 __host__ __device__ constexpr int forward_default_lines(int n, int P, int guard)
 {
     return forward_lines_fit(n, P, guard, 16) ? 16

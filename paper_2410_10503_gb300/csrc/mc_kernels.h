@@ -149,8 +149,10 @@ struct FwdArgs {
     float* part;               //      kernel adds them and runs the epilogue
     int ipb;                   // items per block (one block per SM)
     int rpt;                   // group slots per consumer warp (2, 4, 8)
-    int guard;                 // zero pairs before each line's data (>= 2 lc + 1)
+    int guard;                 // zero pairs before each line's data (>= 2 cl + 1)
     int lc;                    // lines per staged chunk (2, 4, 8, 16)
+    int cl;                    // lines per sampled part of a chunk: forward_part_lines(lc, guard)
+                               // (launch_forward sets it; batched argument tables carry it)
     int stages;                // ring stages: forward_ring(lc, P) (launch_forward sets it;
                                // batched argument tables carry it)
     int n, na, nb;
@@ -182,11 +184,12 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 // batched (all angles, one slot per slice, no bands): block b runs block
 // map[b].block of slice map[b].slice's item table with that slice's lines per
 // chunk (args[slice].lc: 16, 8, 4 or 2) and ring stages (args[slice].stages,
-// forward_ring); every slice of the launch has lc lines per chunk, a ring of
-// `stages` stages (the kernel is compiled for both) and at most rpt group
-// slots per warp; smem_bytes = the largest forward_smem_bytes of its slices
+// forward_ring); every slice of the launch has lc lines per chunk sampled in
+// parts of cl lines, a ring of `stages` stages (the kernel is compiled for
+// these) and at most rpt group slots per warp; smem_bytes = the largest
+// forward_smem_bytes of its slices
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
-                                 size_t smem_bytes, int lc, int stages, cudaStream_t s);
+                                 size_t smem_bytes, int lc, int stages, int cl, cudaStream_t s);
 int forward_groups_per_block(int rpt);
 int forward_consumer_warps();         // consumer warps per block
 int forward_static_smem();           // static shared memory of the largest instance

@@ -240,7 +240,7 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     // sizes: same line pitch and chunking as the context path; items of at
     // most gpi groups, gpi sized for one block per SM
     const int P = layout_pitch(n, kGuardNarrow);
-    const int lc = forward_default_lines(n, P, kGuardNarrow);
+    const int lc = std::min(8, forward_default_lines(n, P, kGuardNarrow));   // chunks sampled whole
     const int gpa = (nb + 31) / 32;
     const int kx0 = (na + 3) / 4, kx1 = (3 * na) / 4;
     const int ny = kx0 + (na - 1 - kx1);

@@ -239,9 +239,9 @@ def test_shared_load_peak_is_plausible(mc):
 
 
 # forward chunk sizes (MC_OPT_FORWARD_LINES), each against the oracle: small
-# images get layouts with the wide guard and 16-line chunks (384^2: a 3-stage
-# ring, 96^2 and 256^2: 5 stages); at 512^2 a 16-line ring would keep 2 stages,
-# so its layouts keep the narrow guard and 16-line chunks are refused
+# images get layouts with the wide guard and whole 16-line chunks (384^2: a
+# 3-stage ring, 96^2 and 256^2); 512^2 keeps the narrow guard, where a 16-line
+# chunk is sampled in two clamped 8-line parts
 @pytest.mark.parametrize("n,na,nb", [(512, 20, 517), (384, 24, 401), (256, 45, 300), (96, 30, 101)])
 @pytest.mark.parametrize("lc", [2, 4, 8, 16])
 def test_forward_chunk_sizes_match_oracle(mc, n, na, nb, lc):
@@ -249,11 +249,6 @@ def test_forward_chunk_sizes_match_oracle(mc, n, na, nb, lc):
     g = O.Geometry(n, na, nb)
     rig = _rigid(2, 41, rot=8.0, shift=6.0)
     ctx = mc.Context(n, na, nb, 2, rigid=rig)
-    if n == 512 and lc == 16:
-        with pytest.raises(mc.MCError, match="guard"):
-            ctx.set_option(N.MC_OPT_FORWARD_LINES, lc)
-        ctx.close()
-        return
     ctx.set_option(N.MC_OPT_FORWARD_LINES, lc)
     P = O.Problem(g, O.Motion(rigid=rig), np.zeros((2, na, nb)), 1.0)
     x = S.phantom(n, 6, 42, n / 16 + 0.5, n / 4 + 1)
