@@ -348,13 +348,14 @@ mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
  * z / zbar / prox update, whose first block per slice also advances that
  * slice's position in its epoch and, at an epoch's end, draws the next
  * epoch's gates (Philox counter on the device, the one-slice draw's
- * sequence): four launches per batched iteration whatever the slices' launch
- * shapes (each block runs with its slice's lines per chunk and rows per
- * thread; when all slices in flight share them, an instance compiled for
- * them).  Block lists put the slices with the most work per block first.
- * Each
- * batched iteration is captured once as a CUDA graph per set of slices in
- * flight and parity of the iteration index, and replayed.
+ * sequence): four stages per batched iteration whatever the slices' launch
+ * shapes (the forward is one launch per class of slices that share a chunk
+ * size and ring, the classes run concurrently between a fork and a join; the
+ * backprojection's blocks run with their slice's rows per thread, an instance
+ * compiled for one height when all slices in flight share it).  Block lists
+ * put the slices with the most work per block first.  Each batched iteration
+ * is captured once as a CUDA graph per set of slices in flight and parity of
+ * the iteration index, and replayed.
  *
  * mc_batch_create groups `count` contexts (same device, angle subsets = 1),
  * orders work on cuda_stream (NULL: a stream of the batch's own) and keeps
