@@ -88,9 +88,10 @@ constexpr int kMagicBits = 0x4B400000;    // bit pattern of kMagic
 
 // Joseph sampling table of one angle (host float64 -> float32).
 // Along a line l of the driving axis the ray (k, b) sits at the padded
-// position u = (b - hb) * inv - (l - h) * t + h + kGuard.  Between the first
-// lines of two consecutive staged chunks u moves by -lc * t, split exactly
-// into step_int + step_frac (step_frac in [0, 1)).
+// position u = (b - hb) * inv - (l - h) * t + h + guard.  Between the first
+// lines of two consecutive sampled parts (CL lines: a whole chunk, or half of
+// a 16-line chunk) u moves by -CL * t, split exactly into step_int +
+// step_frac (step_frac in [0, 1)).
 struct FwdAngle {
     float t_hi;             // cos/sin or sin/cos (first 16 bytes: chunk loop)
     float step_frac;
