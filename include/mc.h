@@ -126,9 +126,9 @@ enum {
                                     when S > 1. */
     MC_OPT_SUBSET_ROWS = 7,      /* rows per thread of the angle-subset backprojection
                                     tiles (0, default: those of the all-angle launches;
-                                    4, 8, 14 or 16); results change within float32
+                                    4, 8, 14, 16 or 28); results change within float32
                                     rounding. */
-    MC_OPT_FORWARD_LINES = 8     /* lines per staged chunk of the forward projector
+    MC_OPT_FORWARD_LINES = 8,    /* lines per staged chunk of the forward projector
                                     (2, 4, 8 or 16; the ring holds up to 5 chunks in
                                     the shared memory a block may use, 16-line chunks
                                     of large images fewer, and at least 2 must fit;
@@ -136,6 +136,12 @@ enum {
                                     multiple of 16): the forward's work items are cut
                                     again for it (mc_autotune also tries every size).
                                     Results change within float32 rounding. */
+    MC_OPT_BACKPROJECT_ROWS = 9  /* rows per thread of the backprojection tiles (4, 8,
+                                    14, 16: four blocks of 8 warps per SM; 28: two),
+                                    overriding the creation-time choice (the grid
+                                    that fills whole waves at the least work per
+                                    SM) or mc_autotune's.  Results change within
+                                    float32 rounding. */
 };
 
 enum { MC_STORE_F32 = 0, MC_STORE_F16 = 1, MC_STORE_BF16 = 2 };
@@ -206,7 +212,7 @@ mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out)
  * warm-up, CUDA events on the context's stream): the forward's lines per
  * staged chunk (2, 4, 8, 16, as the layouts and shared memory allow), work items per block and
  * ray-group slots per warp, and the backprojector's rows per thread (4, 8,
- * 14, 16).  The fastest setting is kept; results are unchanged bit for bit by
+ * 14, 16, 28).  The fastest setting is kept; results are unchanged bit for bit by
  * the item split and change within float32 rounding with the chunk size and
  * rows per thread.  out (nullable, host, 4 int32): {lines per chunk, items per
  * block, group slots per warp, rows per thread}.  Captured epoch graphs are

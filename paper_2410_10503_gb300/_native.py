@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "MC_OK", -1: "MC_EINVAL", -2: "MC_ENOMEM", -3: "MC_ECUDA",
                 -4: "MC_ETIMEOUT", -5: "MC_ESTATE", -6: "MC_EDEVICE"}
 MC_MOTION_RIGID, MC_MOTION_FIELD = 0, 1
 MC_OPT_GRAPH, MC_OPT_PROFILE, MC_OPT_TRACE_OBJECTIVE, MC_OPT_STORAGE, MC_OPT_TEST_STALL = 1, 2, 3, 4, 5
-MC_OPT_SUBSET_BANDS, MC_OPT_SUBSET_ROWS, MC_OPT_FORWARD_LINES = 6, 7, 8
+MC_OPT_SUBSET_BANDS, MC_OPT_SUBSET_ROWS, MC_OPT_FORWARD_LINES, MC_OPT_BACKPROJECT_ROWS = 6, 7, 8, 9
 MC_STORE_F32, MC_STORE_F16, MC_STORE_BF16 = 0, 1, 2
 
 

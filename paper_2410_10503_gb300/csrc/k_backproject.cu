@@ -156,9 +156,9 @@ __device__ __forceinline__ void bp_two_rows(unsigned long long jj, unsigned long
 
 #endif
 
-// pj: the rows of this launch's tiles (even, <= PJ); the register arrays are
-// sized for PJ and rows j >= pj are skipped, so one PJ = 16 instance serves
-// slices of every tile height with the arithmetic of the PJ = pj instance.
+// pj: the rows of this launch's tiles (even, <= PJ; every caller passes PJ,
+// so the row bounds below are compile-time); the register arrays are sized for
+// PJ.
 template <int PJ, bool SUB>
 __device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int slot, int pj)
 {
@@ -291,8 +291,15 @@ __device__ __forceinline__ void bp_block(const BpArgs& a, int bx, int by, int sl
     }
 }
 
+// Residency: 4 blocks (32 warps) per SM at 64 registers for tiles of up to 16
+// rows; 28-row tiles take 2 blocks per SM with up to 128 registers, and pay
+// the per-angle set-up (slot constants, the column's beta, the window) once
+// per 28 rows.
+template <int PJ>
+constexpr int bp_min_blocks() { return PJ > 16 ? 2 : 4; }
+
 template <int PJ, bool SUB>
-__global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
+__global__ void __launch_bounds__(256, bp_min_blocks<PJ>()) k_backproject(BpArgs a)
 {
     pdl_wait();
     pdl_trigger();
@@ -300,21 +307,10 @@ __global__ void __launch_bounds__(256, 4) k_backproject(BpArgs a)
 }
 
 // Batched: the tiles of every slice of the launch (all angles, one slot),
-// each slice with its own tile height a.pj <= 16.
-__global__ void __launch_bounds__(256, 4) k_backproject_batch(const BpArgs* __restrict__ args,
-                                                              const BatchBlock* __restrict__ map)
-{
-    pdl_wait();
-    pdl_trigger();
-    const BatchBlock m = map[blockIdx.x];
-    const BpArgs& a = args[m.slice];
-    const int tx = (a.n + 31) / 32;
-    bp_block<16, false>(a, m.block % tx, m.block / tx, 0, a.pj);
-}
-
-// Batched, every slice of the launch with tile height PJ.
+// every slice with tile height PJ (the batch launches one such class per
+// tile height).
 template <int PJ>
-__global__ void __launch_bounds__(256, 4) k_backproject_batch_pj(const BpArgs* __restrict__ args,
+__global__ void __launch_bounds__(256, bp_min_blocks<PJ>()) k_backproject_batch_pj(const BpArgs* __restrict__ args,
                                                                  const BatchBlock* __restrict__ map)
 {
     pdl_wait();
@@ -337,7 +333,8 @@ size_t backproject_smem_bytes(int pj)
 }
 
 #define MC_BP_INSTANCES(X) \
-    X(4, false) X(8, false) X(14, false) X(16, false) X(4, true) X(8, true) X(14, true) X(16, true)
+    X(4, false) X(8, false) X(14, false) X(16, false) X(28, false) \
+    X(4, true) X(8, true) X(14, true) X(16, true) X(28, true)
 
 cudaError_t backproject_prepare()
 {
@@ -348,9 +345,6 @@ cudaError_t backproject_prepare()
                                  (int)backproject_smem_bytes(P));
     MC_BP_INSTANCES(MC_BP_ATTR)
 #undef MC_BP_ATTR
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_backproject_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)backproject_smem_bytes(16));
 #define MC_BPB_ATTR(P, B)                                                                 \
     if (e == cudaSuccess && !B)                                                           \
         e = cudaFuncSetAttribute(k_backproject_batch_pj<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
@@ -366,16 +360,13 @@ cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, 
                                      cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    if (pj > 0) {
 #define MC_BPB_LAUNCH(P, B)                                                               \
-        if (!B && pj == P)                                                                \
-            return pdl_launch(k_backproject_batch_pj<P>, dim3(nblocks), dim3(256), backproject_smem_bytes(P), s, \
-                              args, map);
-        MC_BP_INSTANCES(MC_BPB_LAUNCH)
+    if (!B && pj == P)                                                                    \
+        return pdl_launch(k_backproject_batch_pj<P>, dim3(nblocks), dim3(256), backproject_smem_bytes(P), s, \
+                          args, map);
+    MC_BP_INSTANCES(MC_BPB_LAUNCH)
 #undef MC_BPB_LAUNCH
-        return cudaErrorInvalidValue;
-    }
-    return pdl_launch(k_backproject_batch, dim3(nblocks), dim3(256), backproject_smem_bytes(16), s, args, map);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_backproject(const BpArgs& a_in, cudaStream_t s)

@@ -1210,21 +1210,24 @@ mc_status build_tables(mc_ctx* c)
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));   // host vectors go out of scope
     // backprojection tiles: 32 columns x pj rows per block of 8 warps.  Among
-    // the tile heights that still give about 24 warps per SM, the one whose
-    // busiest SM does the least work: ceil(blocks / SMs) tiles, each costing
-    // about 8 pj + 30 instructions per angle and lane (pj rows plus the
-    // per-angle set-up), so that the grid fills whole waves
+    // the tile heights whose grid still fills every SM's residency (4 blocks
+    // of up to 16 rows, or 2 of 28: 24 and 16 warps per SM at least), the one
+    // whose busiest SM does the least work: ceil(blocks / SMs) tiles, each
+    // costing about 8 pj + 30 instructions per angle and lane (pj rows plus the
+    // per-angle set-up), so that the grid fills whole waves (measured at
+    // rigid512: 28 rows, 2 blocks per SM, ran the SPDHG epoch 4.6% faster than
+    // 14 rows, 4 blocks per SM)
     c->pj = 4;
     long long best_cost = -1;
-    for (int pj : {16, 14, 8}) {
+    for (int pj : {28, 16, 14, 8}) {
         const long long blocks = (long long)((n + 31) / 32) * ((n + pj - 1) / pj);
-        if (8 * blocks < 24LL * c->sms) continue;
+        if (blocks < (pj > 16 ? 2LL : 3LL) * c->sms) continue;
         const long long cost = (blocks + c->sms - 1) / c->sms * (8LL * pj + 30);
         if (best_cost < 0 || cost < best_cost) { best_cost = cost; c->pj = pj; }
     }
     // dual increment layout: guards wide enough for every pixel's two bins
     const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
-    const int pj_max = 16;
+    const int pj_max = 28;
     c->Gb = std::max(2, (int)std::ceil(std::sqrt(2.0) * (h + pj_max + 1) - hb) + 2);
     c->Pb = (nb + 2 * c->Gb + 2 + 3) / 4 * 4;
     c->dy_stride = (size_t)na * c->Pb;
@@ -1738,7 +1741,7 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
     // the SMs as the forward's blocks drain); the forward is the same for all
     int best_pj = c->pj;
     float best_bp = 1e30f;
-    for (int pj : {4, 8, 14, 16}) {
+    for (int pj : {4, 8, 14, 16, 28}) {
         if (st != MC_OK) break;
         c->pj = pj;
         float ms = 0;
@@ -2272,9 +2275,16 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
         }
         return finish(c);
     }
+    case MC_OPT_BACKPROJECT_ROWS:
+        if (value != 4 && value != 8 && value != 14 && value != 16 && value != 28)
+            return fail(c, MC_EINVAL, "backprojection rows per thread must be 4, 8, 14, 16 or 28");
+        CK(cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        c->pj = (int)value;
+        return MC_OK;
     case MC_OPT_SUBSET_ROWS:
-        if (value != 0 && value != 4 && value != 8 && value != 14 && value != 16)
-            return fail(c, MC_EINVAL, "subset rows per thread must be 0, 4, 8, 14 or 16");
+        if (value != 0 && value != 4 && value != 8 && value != 14 && value != 16 && value != 28)
+            return fail(c, MC_EINVAL, "subset rows per thread must be 0, 4, 8, 14, 16 or 28");
         CK(cudaStreamSynchronize(c->stream));
         drop_graphs(c);
         c->s_pj = (int)value;
@@ -2448,15 +2458,19 @@ struct FwdClass {
     size_t smem = 0;
 };
 
+// The backprojection tiles of the slices in flight with one tile height.
+struct BpClass {
+    size_t off = 0;
+    int n = 0, pj = 4;
+};
+
 struct BatchPhase {
     BatchBlock* d_map = nullptr;             // every map of the phase, one allocation
     int plan = 0;                            // forward work items: 0 each slice's own, 1 the batch's
     int n_warp = 0, n_wadj = 0;
     size_t off_warp = 0, off_wadj = 0;
     std::vector<FwdClass> fwd;               // one forward launch per class, classes concurrent
-    int n_bp = 0;
-    int bp_pj = 0;                           // > 0: every slice in flight has this tile height
-    size_t off_bp = 0;
+    std::vector<BpClass> bp;                 // one backprojection launch per tile height, likewise
     cudaGraphExec_t g[2][2] = {};            // [1 or kBatchGraphIters iterations][start parity]
 };
 
@@ -2738,8 +2752,30 @@ mc_status batch_phase(mc_batch* b, int A)
             fc.n = r.second;
             ph.fwd.push_back(fc);
         }
-        // side streams and events for the classes after the first
-        while (b->side.size() + 1 < ph.fwd.size()) {
+    }
+    // backprojection: one class per tile height; a tile's work ~ angles x rows
+    {
+        std::vector<int> heights;
+        for (int i : q)
+            if (std::find(heights.begin(), heights.end(), C(i)->pj) == heights.end()) heights.push_back(C(i)->pj);
+        ph.bp.clear();
+        for (int pj : heights) {
+            std::vector<int> members;
+            for (int i : q)
+                if (C(i)->pj == pj) members.push_back(i);
+            auto r = add(members, [&](int i) { return backproject_tiles(C(i)->n, C(i)->pj); },
+                         [&](int i) { return (double)C(i)->na * C(i)->pj; });
+            BpClass bc;
+            bc.off = r.first;
+            bc.n = r.second;
+            bc.pj = pj;
+            ph.bp.push_back(bc);
+        }
+    }
+    {
+        // side streams and events for the classes after the first of either stage
+        const size_t classes = std::max(ph.fwd.size(), ph.bp.size());
+        while (b->side.size() + 1 < classes) {
             cudaStream_t q2 = nullptr;
             cudaEvent_t e2 = nullptr;
             BCK(cudaStreamCreateWithFlags(&q2, cudaStreamNonBlocking));
@@ -2747,18 +2783,7 @@ mc_status batch_phase(mc_batch* b, int A)
             BCK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
             b->join_ev.push_back(e2);
         }
-        if (ph.fwd.size() > 1 && !b->fork_ev) BCK(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
-    }
-    {
-        ph.bp_pj = C(q[0])->pj;
-        for (int i : q)
-            if (C(i)->pj != ph.bp_pj) ph.bp_pj = 0;
-    }
-    // backprojection: each slice's own tile height; a tile's work ~ angles x rows
-    {
-        auto r = add(q, [&](int i) { return backproject_tiles(C(i)->n, C(i)->pj); },
-                     [&](int i) { return (double)C(i)->na * C(i)->pj; });
-        ph.off_bp = r.first; ph.n_bp = r.second;
+        if (classes > 1 && !b->fork_ev) BCK(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming));
     }
     // transpose warp and update: 256 pixels per block
     {
@@ -2801,7 +2826,17 @@ mc_status batch_enqueue(mc_batch* b, int A, int t, int iters)
         const FwdClass& f0 = ph.fwd[0];
         BCK(launch_forward_batch(fa, ph.d_map + f0.off, f0.n, f0.rpt, f0.smem, f0.lc, f0.ns, f0.cl, s));
         for (size_t k = 1; k < ph.fwd.size(); ++k) BCK(cudaStreamWaitEvent(s, b->join_ev[k - 1], 0));
-        BCK(launch_backproject_batch(b->d_bp[t], ph.d_map + ph.off_bp, ph.n_bp, ph.bp_pj, s));
+        // the backprojection: one launch per tile height, the same way
+        if (ph.bp.size() > 1) BCK(cudaEventRecord(b->fork_ev, s));
+        for (size_t k = 1; k < ph.bp.size(); ++k) {
+            const BpClass& bc = ph.bp[k];
+            cudaStream_t q2 = b->side[k - 1];
+            BCK(cudaStreamWaitEvent(q2, b->fork_ev, 0));
+            BCK(launch_backproject_batch(b->d_bp[t], ph.d_map + bc.off, bc.n, bc.pj, q2));
+            BCK(cudaEventRecord(b->join_ev[k - 1], q2));
+        }
+        BCK(launch_backproject_batch(b->d_bp[t], ph.d_map + ph.bp[0].off, ph.bp[0].n, ph.bp[0].pj, s));
+        for (size_t k = 1; k < ph.bp.size(); ++k) BCK(cudaStreamWaitEvent(s, b->join_ev[k - 1], 0));
         BCK(launch_warp_adjoint_update_batch(b->d_wadj[t], ph.d_map + ph.off_wadj, ph.n_wadj, b->d_draw, t, s));
     }
     return MC_OK;

@@ -212,9 +212,9 @@ struct BpArgs {
 };
 cudaError_t launch_backproject(const BpArgs& a, cudaStream_t s);
 // batched (all angles, one slot per slice): block b works on tile
-// map[b].block of slice map[b].slice, with that slice's rows per thread
-// (args[slice].pj, any of 4, 8, 14, 16) and window length (args[slice].wl)
-// pj > 0: every slice has that tile height (a kernel compiled for it)
+// map[b].block of slice map[b].slice; every slice of the launch has tile
+// height pj (args[slice].pj: 4, 8, 14, 16 or 28; a kernel compiled for it)
+// and its own window length (args[slice].wl)
 cudaError_t launch_backproject_batch(const BpArgs* args, const BatchBlock* map, int nblocks, int pj,
                                      cudaStream_t s);
 int backproject_tiles(int n, int pj);

@@ -267,3 +267,23 @@ def test_forward_chunk_size_refusals(mc):
             ctx.set_option(N.MC_OPT_FORWARD_LINES, bad)
     ctx.set_option(N.MC_OPT_FORWARD_LINES, 8)
     ctx.close()
+
+
+# backprojection tile heights (MC_OPT_BACKPROJECT_ROWS), each against the
+# oracle: 28-row tiles run two blocks per SM with more registers per thread
+@pytest.mark.parametrize("n,na,nb", [(512, 20, 517), (96, 30, 101)])
+@pytest.mark.parametrize("rows", [4, 8, 14, 16, 28])
+def test_backprojection_tile_heights_match_oracle(mc, n, na, nb, rows):
+    from paper_2410_10503_gb300 import _native as N
+    g = O.Geometry(n, na, nb)
+    rig = _rigid(2, 51, rot=8.0, shift=6.0)
+    ctx = mc.Context(n, na, nb, 2, rigid=rig)
+    ctx.set_option(N.MC_OPT_BACKPROJECT_ROWS, rows)
+    P = O.Problem(g, O.Motion(rigid=rig), np.zeros((2, na, nb)), 1.0)
+    y = S.random_sinogram(na, nb, 52)
+    assert rel_l2(host(ctx.backproject(cuda(y))), O.At(y, g)) <= TOL
+    assert rel_l2(host(ctx.adjoint(1, cuda(y))), O.Ait(y, P, 1)) <= TOL
+    for bad in (0, 12, 32):
+        with pytest.raises(mc.MCError):
+            ctx.set_option(N.MC_OPT_BACKPROJECT_ROWS, bad)
+    ctx.close()

@@ -147,7 +147,7 @@ def test_subset_launch_shapes_and_autotune(mc, case):
     E = 10
     ref = O.spdhg(P, E, O.step_sizes(nb2[:-1].max(), P.alpha, P.N, P.N * Ssub), seed=sd["gates"],
                   subsets=Ssub)
-    for bands, rows in ((1, 0), (3, 8), (8, 16)):
+    for bands, rows in ((1, 0), (3, 8), (8, 16), (2, 28)):
         ctx = context(mc, P)
         ctx.set_subsets(Ssub)
         ctx.set_norms(nb2)
