@@ -1133,17 +1133,57 @@ void plan_forward(const mc_ctx* c, int lc, int sms, int ipb_start, int refine, G
     rpt = best_rpt;
 }
 
-mc_status build_tables(mc_ctx* c)
+// The launch shapes and layout pitches a context of this geometry starts with
+// (mc_create; mc_plan_shapes reports them without a device).
+struct Shapes {
+    int guard, P, lines, lc, cl, ring, pj, Gb, Pb;
+};
+
+Shapes choose_shapes(int n, int nb, int sms)
 {
-    const int n = c->n, na = c->na, nb = c->nb;
+    Shapes sh{};
     // line layouts: `guard` zero pairs in front, >= guard behind, 16-byte
     // pitch, lines padded to whole chunks; chunks of lc in {16, 8, 4, 2} lines
     // per ring stage, the longest whose ring in the one block per SM keeps at
-    // least 3 stages (16 only with the wide guard of small images)
-    c->guard = layout_guard(n);
-    c->P = layout_pitch(n, c->guard);
-    c->layout_stride = (size_t)layout_lines(n) * c->P;
-    c->lc = forward_default_lines(n, c->P, c->guard);
+    // least 3 stages
+    sh.guard = layout_guard(n);
+    sh.P = layout_pitch(n, sh.guard);
+    sh.lines = layout_lines(n);
+    sh.lc = forward_default_lines(n, sh.P, sh.guard);
+    sh.cl = forward_part_lines(sh.lc, sh.guard);
+    sh.ring = forward_ring(sh.lc, sh.P);
+    // backprojection tiles: 32 columns x pj rows per block of 8 warps.  Among
+    // the tile heights whose grid still fills every SM's residency (4 blocks
+    // of up to 16 rows, or 2 of 28: 24 and 16 warps per SM at least), the one
+    // whose busiest SM does the least work: ceil(blocks / SMs) tiles, each
+    // costing about 8 pj + 30 instructions per angle and lane (pj rows plus the
+    // per-angle set-up), so that the grid fills whole waves (measured at
+    // rigid512: 28 rows, 2 blocks per SM, ran the SPDHG epoch 4.6% faster than
+    // 14 rows, 4 blocks per SM)
+    sh.pj = 4;
+    long long best_cost = -1;
+    for (int pj : {28, 16, 14, 8}) {
+        const long long blocks = (long long)((n + 31) / 32) * ((n + pj - 1) / pj);
+        if (blocks < (pj > 16 ? 2LL : 3LL) * sms) continue;
+        const long long cost = (blocks + sms - 1) / sms * (8LL * pj + 30);
+        if (best_cost < 0 || cost < best_cost) { best_cost = cost; sh.pj = pj; }
+    }
+    // dual increment layout: guards wide enough for every pixel's two bins
+    const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
+    const int pj_max = 28;
+    sh.Gb = std::max(2, (int)std::ceil(std::sqrt(2.0) * (h + pj_max + 1) - hb) + 2);
+    sh.Pb = (nb + 2 * sh.Gb + 2 + 3) / 4 * 4;
+    return sh;
+}
+
+mc_status build_tables(mc_ctx* c)
+{
+    const int n = c->n, na = c->na, nb = c->nb;
+    const Shapes sh = choose_shapes(n, nb, c->sms);
+    c->guard = sh.guard;
+    c->P = sh.P;
+    c->layout_stride = (size_t)sh.lines * c->P;
+    c->lc = sh.lc;
     std::vector<FwdAngle> fa(na);
     std::vector<BpAngle> ba(na);
     // forward group order: rows-driven angles first, then columns-driven; in
@@ -1209,27 +1249,9 @@ mc_status build_tables(mc_ctx* c)
     CK(cudaMemcpyAsync(c->d_items, items.data(), items.size() * sizeof(RayItem), cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaStreamSynchronize(c->stream));   // host vectors go out of scope
-    // backprojection tiles: 32 columns x pj rows per block of 8 warps.  Among
-    // the tile heights whose grid still fills every SM's residency (4 blocks
-    // of up to 16 rows, or 2 of 28: 24 and 16 warps per SM at least), the one
-    // whose busiest SM does the least work: ceil(blocks / SMs) tiles, each
-    // costing about 8 pj + 30 instructions per angle and lane (pj rows plus the
-    // per-angle set-up), so that the grid fills whole waves (measured at
-    // rigid512: 28 rows, 2 blocks per SM, ran the SPDHG epoch 4.6% faster than
-    // 14 rows, 4 blocks per SM)
-    c->pj = 4;
-    long long best_cost = -1;
-    for (int pj : {28, 16, 14, 8}) {
-        const long long blocks = (long long)((n + 31) / 32) * ((n + pj - 1) / pj);
-        if (blocks < (pj > 16 ? 2LL : 3LL) * c->sms) continue;
-        const long long cost = (blocks + c->sms - 1) / c->sms * (8LL * pj + 30);
-        if (best_cost < 0 || cost < best_cost) { best_cost = cost; c->pj = pj; }
-    }
-    // dual increment layout: guards wide enough for every pixel's two bins
-    const double h = 0.5 * (n - 1), hb = 0.5 * (nb - 1);
-    const int pj_max = 28;
-    c->Gb = std::max(2, (int)std::ceil(std::sqrt(2.0) * (h + pj_max + 1) - hb) + 2);
-    c->Pb = (nb + 2 * c->Gb + 2 + 3) / 4 * 4;
+    c->pj = sh.pj;
+    c->Gb = sh.Gb;
+    c->Pb = sh.Pb;
     c->dy_stride = (size_t)na * c->Pb;
     return MC_OK;
 }
@@ -1354,6 +1376,18 @@ mc_status alloc_state(mc_ctx* c)
 extern "C" {
 
 const char* mc_version(void) { return "libmc 0.1 (sm_103a)"; }
+
+mc_status mc_plan_shapes(const mc_geometry* geom, int32_t sms, int32_t* out)
+{
+    if (!geom || !out || sms < 1) return MC_EINVAL;
+    if (geom->n < 2 || geom->n > 2048 || geom->n_angles < 1 || geom->n_angles > 8192 || geom->n_bins < 1 ||
+        geom->n_bins > 8192)
+        return MC_EINVAL;
+    const Shapes sh = choose_shapes(geom->n, geom->n_bins, sms);
+    const int32_t v[9] = {sh.guard, sh.P, sh.lines, sh.lc, sh.cl, sh.ring, sh.pj, sh.Gb, sh.Pb};
+    std::memcpy(out, v, sizeof v);
+    return MC_OK;
+}
 
 const char* mc_last_error(const mc_ctx* ctx)
 {
