@@ -207,3 +207,32 @@ def test_one_slice_batch_follows_new_step_sizes(mc, merged_slices):
     np.testing.assert_array_equal(x_b, x_own)
     ctx.close()
     own.close()
+
+
+def test_merged_batch_with_tall_tiles_and_two_part_chunks(mc):
+    """A 512^2 slice (16-line chunks in two 8-line parts, 28-row backprojection
+    tiles) merged with a 96^2 slice (whole 16-line chunks, short tiles): each
+    stage runs one launch per shape class between a fork and a join; each
+    slice equals its own runs bit for bit."""
+    def make(n, na, nb, N, seed, norms=None):
+        rig = S.rigid_motion(N, 6.0, 4.0, seed)
+        ctx = mc.Context(n, na, nb, N, rigid=rig)
+        xt = torch.as_tensor(S.phantom(n, 8, seed + 1, n / 16 + 0.5, n / 4 + 1), dtype=torch.float32,
+                             device="cuda")
+        d = torch.stack([ctx.forward(i, xt) for i in range(N)])
+        ctx.set_data(d, 1e-2)
+        norms = ctx.norms(max_iter=10, tol=1e-4) * 1.05 if norms is None else norms
+        ctx.set_norms(norms)
+        return ctx, norms
+    shapes = {512: (24, 529, 3, 7100, 11), 96: (30, 101, 4, 7200, 12)}
+    made = {n: make(n, *v[:4]) for n, v in shapes.items()}
+    with mc.Batch([made[512][0], made[96][0]]) as b:
+        b.run(3, seeds=[shapes[512][4], shapes[96][4]])
+    for n, (ctx, norms) in made.items():
+        na, nb, N, seed, gseed = shapes[n]
+        own, _ = make(n, na, nb, N, seed, norms)
+        x_own, _ = own.spdhg_run(3, seed=gseed)
+        x_b, _ = ctx.spdhg_run(0, seed=gseed)
+        np.testing.assert_array_equal(x_b, x_own)
+        own.close()
+        ctx.close()
