@@ -142,9 +142,7 @@ __device__ __forceinline__ void prefetch_csr(const FwdArgs& a, int gate, int par
 }
 
 constexpr uint32_t kWaitLimit = 1u << 24;   // polls before a stage wait gives up (unless the launch sets one)
-constexpr int kConsumers = 23;               // consumer warps per block (24 warps in all: 6 per scheduler)
-constexpr int kThreads = 32 * kConsumers;    // consumer threads (rays per slot)
-constexpr int kBlock = kThreads + 32;        // plus one producer warp
+constexpr int kMaxConsumers = 23;            // the most consumer warps of any instance (forward_warps)
 
 #ifdef MC_CHECKED
 // The samples of one ray over the LC lines of a chunk in C, the form used by
@@ -256,7 +254,7 @@ struct SlotRec {
 // One block's work: items bx * ipb .. of the launch's item table for gate
 // slot `slot`; nbx = blocks sharing the table (the CSR prefetch is split
 // among them).
-template <int RPT, int LC, int NS, int CL, bool BANDED>
+template <int RPT, int LC, int NS, int CL, int W, bool BANDED>
 __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot, int nbx, SlotState* s_slot,
                                               SlotRec* s_rec)
 {
@@ -280,7 +278,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) {
             mbar_init(&full[i], 1);
-            mbar_init(&empty[i], kConsumers);
+            mbar_init(&empty[i], W);
         }
         *s_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -293,7 +291,7 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     // On a failure (its own wait for a free stage ran out, or a consumer raised
     // the block's flag) the producer issues nothing more and waits for the
     // copies it has in flight before it leaves.
-    if (warp == kConsumers) {
+    if (warp == W) {
         if (a.stall) return;          // test of the waits' failure path: no copies in flight
         if (lane == 0) {
             int issued = 0;           // copies issued so far (ring position of the next one)
@@ -371,15 +369,15 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
         const RayItem item = items[it0 + it];
         const int cb0 = BANDED ? item.band * a.cpb : 0;
         const int cb1 = BANDED ? min(nch, cb0 + a.cpb) : nch;
-        // this warp's groups: item.begin + warp + m * kConsumers
-        const int ns = max(0, min(RPT, (item.end - item.begin - warp + kConsumers - 1) / kConsumers));
+        // this warp's groups: item.begin + warp + m * W
+        const int ns = max(0, min(RPT, (item.end - item.begin - warp + W - 1) / W));
         float frac[RPT], acc[RPT];
         int ui[RPT];
         int my_lo = nch, my_hi = -1;      // lane m < RPT: chunk range of slot m
         SlotRec* rec = s_rec + warp * RPT;
         if (lane < ns) {
             SlotRec r;
-            r.grp = __ldg(a.groups + item.begin + warp + lane * kConsumers);
+            r.grp = __ldg(a.groups + item.begin + warp + lane * W);
             if (r.grp.x >= 0) r.T = a.ang[r.grp.x];
             rec[lane] = r;
         }
@@ -533,30 +531,30 @@ __device__ __forceinline__ void forward_block(const FwdArgs& a, int bx, int slot
     }
 }
 
-template <int RPT, int LC, int NS, int CL, bool BANDED>
-__global__ void __launch_bounds__(kBlock, 1) k_forward(FwdArgs a)
+template <int RPT, int LC, int NS, int CL, bool BANDED, int W = forward_warps(LC, CL)>
+__global__ void __launch_bounds__(32 * (W + 1), 1) k_forward(FwdArgs a)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
-    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
-    forward_block<RPT, LC, NS, CL, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
+    __shared__ __align__(16) SlotState s_slot[W * RPT];
+    __shared__ __align__(16) SlotRec s_rec[W * RPT];
+    forward_block<RPT, LC, NS, CL, W, BANDED>(a, blockIdx.x, blockIdx.y, gridDim.x, s_slot, s_rec);
 }
 
 // Batched: the blocks of every slice of the launch, each on its slice's item
 // table with its slice's arguments (all angles, one slot, no bands); every
 // slice of the launch has LC lines per chunk and an NS-stage ring (the batch
 // launches one such class per chunk size and ring).
-template <int RPT, int LC, int NS, int CL>
-__global__ void __launch_bounds__(kBlock, 1) k_forward_batch_lc(const FwdArgs* __restrict__ args,
+template <int RPT, int LC, int NS, int CL, int W = forward_warps(LC, CL)>
+__global__ void __launch_bounds__(32 * (W + 1), 1) k_forward_batch_lc(const FwdArgs* __restrict__ args,
                                                                 const BatchBlock* __restrict__ map)
 {
     pdl_wait();
     pdl_trigger();
-    __shared__ __align__(16) SlotState s_slot[kConsumers * RPT];
-    __shared__ __align__(16) SlotRec s_rec[kConsumers * RPT];
+    __shared__ __align__(16) SlotState s_slot[W * RPT];
+    __shared__ __align__(16) SlotRec s_rec[W * RPT];
     const BatchBlock m = map[blockIdx.x];
-    forward_block<RPT, LC, NS, CL, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
+    forward_block<RPT, LC, NS, CL, W, false>(args[m.slice], m.block, 0, m.nblocks, s_slot, s_rec);
 }
 
 // Sum of the bands' partial ray sums in band order, then the epilogue of
@@ -606,14 +604,13 @@ __global__ void __launch_bounds__(256) k_forward_combine(FwdArgs a)
 
 }  // namespace
 
-int forward_groups_per_block(int rpt) { return kConsumers * rpt; }
+int forward_groups_per_block(int rpt, int warps) { return warps * rpt; }
 
-int forward_consumer_warps() { return kConsumers; }
 
 
 // static shared memory of the largest instance: the slot tables plus room for
 // the alignment padding the compiler may place between them
-int forward_static_smem() { return (int)(kConsumers * 8 * (sizeof(SlotState) + sizeof(SlotRec))) + 256; }
+int forward_static_smem() { return (int)(kMaxConsumers * 8 * (sizeof(SlotState) + sizeof(SlotRec))) + 256; }
 
 size_t forward_smem_bytes(int lc, int P)
 {
@@ -660,13 +657,15 @@ cudaError_t launch_forward(const FwdArgs& a_in, cudaStream_t s)
 #define MC_LAUNCH(R, L, NS, CL)                                                           \
     if (a.rpt == R && a.lc == L && a.stages == NS && a.cl == CL) {                        \
         if (a.nbands > 1) {                                                               \
-            cudaError_t e = pdl_launch(k_forward<R, L, NS, CL, true>, grid, dim3(kBlock), smem, s, a); \
+            cudaError_t e = pdl_launch(k_forward<R, L, NS, CL, true>, grid, dim3(32 * (forward_warps(L, CL) + 1)), \
+                                       smem, s, a);                                        \
             if (e != cudaSuccess) return e;                                               \
             const int S = a.sel.subsets > 1 ? a.sel.subsets : 1;                          \
             const int rays = ((a.na + S - 1) / S) * a.nb;                                 \
             return pdl_launch(k_forward_combine, dim3((rays + 255) / 256, a.n_slots), dim3(256), 0, s, a); \
         } else {                                                                          \
-            return pdl_launch(k_forward<R, L, NS, CL, false>, grid, dim3(kBlock), smem, s, a); \
+            return pdl_launch(k_forward<R, L, NS, CL, false>, grid, dim3(32 * (forward_warps(L, CL) + 1)), \
+                              smem, s, a);                                                 \
         }                                                                                 \
     }
     MC_FWD_INSTANCES(MC_LAUNCH)
@@ -681,7 +680,8 @@ cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int
     const size_t smem = smem_bytes;
 #define MC_LAUNCH_B(R, L, NS, CL)                                                           \
     if (rpt == R && lc == L && stages == NS && cl == CL)                                    \
-        return pdl_launch(k_forward_batch_lc<R, L, NS, CL>, dim3(nblocks), dim3(kBlock), smem, s, args, map);
+        return pdl_launch(k_forward_batch_lc<R, L, NS, CL>, dim3(nblocks), dim3(32 * (forward_warps(L, CL) + 1)), \
+                          smem, s, args, map);
     MC_FWD_INSTANCES(MC_LAUNCH_B)
 #undef MC_LAUNCH_B
     return cudaErrorInvalidValue;

@@ -858,9 +858,9 @@ void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vec
 
 // Cut every set into about ipb * sms items of equal weight (each driving-axis
 // class separately: an item streams one line layout); the smallest ipb whose
-// items hold at most kConsumers * rpt groups, rpt in {2, 4, 8}.  Items of set
+// items hold at most warps * rpt groups, rpt in {2, 4, 8}.  Items of set
 // s are items[set_off[s] .. set_off[s+1]).
-void partition_items(const GroupTable& gt, int sms, int ipb_start, std::vector<RayItem>& items,
+void partition_items(const GroupTable& gt, int sms, int ipb_start, int warps, std::vector<RayItem>& items,
                      std::vector<int>& set_off, int& ipb, int& rpt)
 {
     const std::vector<long long>& cum = gt.cum;
@@ -890,8 +890,8 @@ void partition_items(const GroupTable& gt, int sms, int ipb_start, std::vector<R
             set_off.push_back((int)items.size());
         }
         rpt = 2;
-        while (rpt < 8 && forward_groups_per_block(rpt) < max_groups) rpt <<= 1;
-        if (forward_groups_per_block(rpt) >= max_groups) return;
+        while (rpt < 8 && forward_groups_per_block(rpt, warps) < max_groups) rpt <<= 1;
+        if (forward_groups_per_block(rpt, warps) >= max_groups) return;
     }
 }
 
@@ -974,7 +974,7 @@ void parallel_for(size_t count, F&& body)
 void balance_items(const mc_ctx* c, int lc, std::vector<int2>& groups, std::vector<RayItem>& items, int& rpt,
                    std::vector<double>* item_time = nullptr)
 {
-    const int W = forward_consumer_warps(), half = forward_ring(lc, c->P) - 1;
+    const int W = forward_warps(lc, forward_part_lines(lc, c->guard)), half = forward_ring(lc, c->P) - 1;
     const int nch = layout_lines(c->n) / lc;
     struct Deal {
         std::vector<std::vector<int>> lists;
@@ -1107,7 +1107,8 @@ void plan_forward(const mc_ctx* c, int lc, int sms, int ipb_start, int refine, G
         std::vector<RayItem> its;
         std::vector<int> off;
         int ipb_r = 1, rpt_r = 2;
-        partition_items(t, sms, ipb_start, its, off, ipb_r, rpt_r);
+        partition_items(t, sms, ipb_start, forward_warps(lc, forward_part_lines(lc, c->guard)), its, off, ipb_r,
+                        rpt_r);
         const std::vector<RayItem> cut = its;        // undealt ranges, for the re-weighting
         std::vector<double> T;
         balance_items(c, lc, t.groups, its, rpt_r, refine > 0 ? &T : nullptr);
@@ -1853,7 +1854,8 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
         std::vector<RayItem> cut;
         std::vector<int> cut_off;
         int ipb = 1, rpt = 2;
-        partition_items(gt, std::max(1, c->sms / bands), 1, cut, cut_off, ipb, rpt);
+        partition_items(gt, std::max(1, c->sms / bands), 1, forward_warps(c->lc, forward_part_lines(c->lc, c->guard)),
+                        cut, cut_off, ipb, rpt);
         balance_items(c, c->lc, gt.groups, cut, rpt);   // one deal serves every band of a cut
         std::vector<RayItem> items;
         std::vector<int> off(1, 0);

@@ -67,6 +67,11 @@ __host__ __device__ constexpr bool forward_lines_fit(int n, int P, int guard, in
     return (lc == 2 || lc == 4 || lc == 8 || lc == 16) && guard >= 2 * 2 + 1 && layout_lines(n) % lc == 0 &&
            forward_stages(lc, P) >= forward_ring(lc, P);
 }
+// Consumer warps of a forward block (plus one producer warp): 23 at 80
+// registers, or 15 with up to 128 registers for 16-line chunks sampled in two
+// 8-line parts (measured at rigid512: the register count, not the warp count,
+// paid there; other shapes kept 23).
+__host__ __device__ constexpr int forward_warps(int lc, int cl) { return (lc == 16 && cl == 8) ? 15 : 23; }
 // The default chunk: the longest that fits (measured SPDHG epochs: 16-line
 // chunks in three stages beat 8-line ones at 128^2-384^2 with the wide guard
 // and at 512^2 in two 8-line parts with the narrow one, 1.661 against 1.704

@@ -190,8 +190,7 @@ cudaError_t launch_forward(const FwdArgs& a, cudaStream_t s);
 // forward_smem_bytes of its slices
 cudaError_t launch_forward_batch(const FwdArgs* args, const BatchBlock* map, int nblocks, int rpt,
                                  size_t smem_bytes, int lc, int stages, int cl, cudaStream_t s);
-int forward_groups_per_block(int rpt);
-int forward_consumer_warps();         // consumer warps per block
+int forward_groups_per_block(int rpt, int warps);   // group slots of an item: warps x rpt
 int forward_static_smem();           // static shared memory of the largest instance
 size_t forward_smem_bytes(int lc, int P);
 cudaError_t forward_prepare(int max_smem);

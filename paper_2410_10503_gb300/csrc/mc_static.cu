@@ -247,8 +247,9 @@ extern "C" mc_status mc_forward_static(const mc_geometry* geom, const double* ri
     const long long n_groups = (long long)na * gpa;
     int rpt = 2;
     long long gpi = (n_groups + sms - 1) / sms;
-    while (rpt < 8 && forward_groups_per_block(rpt) < gpi) rpt <<= 1;
-    gpi = std::min<long long>(gpi, forward_groups_per_block(rpt));
+    const int warps = forward_warps(lc, lc);   // chunks sampled whole
+    while (rpt < 8 && forward_groups_per_block(rpt, warps) < gpi) rpt <<= 1;
+    gpi = std::min<long long>(gpi, forward_groups_per_block(rpt, warps));
     const int items0 = (int)(((long long)ny * gpa + gpi - 1) / gpi);
     const int items1 = (int)(((long long)(na - ny) * gpa + gpi - 1) / gpi);
     const int n_items = items0 + items1;
