@@ -2927,8 +2927,8 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream,
     if (st == MC_OK) st = balloc(b, &b->d_bgates, 2 * (size_t)count * b->gmax);
     // the batch's forward work items: about 4 blocks per SM over the whole
     // batch, each slice's share by its samples per projection, at least as
-    // many items as its groups need (at most 24 warps x 8 slots each) and at
-    // most as many as its own plan has
+    // many items as its groups need (at most forward_warps warps x 8 slots
+    // each) and at most as many as its own plan has
     if (st == MC_OK) {
         const int sms = b->ctx[0]->sms;
         double W = 0;
