@@ -453,14 +453,17 @@ const char* mc_version(void);
 
 /* The launch shapes and layouts mc_create would choose for this geometry on a
  * GPU with `sms` SMs, computed on the host (no device needed; mc_autotune and
- * the MC_OPT_* shape options may change them later).  out (host, 9 int32):
+ * the MC_OPT_* shape options may change them later).  out (host, 10 int32):
  * {guard: zero pairs around each line of the warped-image layouts (17, or 33
  * where 16-line chunks are sampled whole), line pitch P in pairs (>= n + 2
  * guard), layout lines (n rounded up to 8), forward lines per staged chunk,
  * lines per sampled part of a chunk (each part clamps its positions: the
  * guard must hold 2 x part + 1 pairs), ring stages (5, or 3), backprojection
  * rows per thread, zero bins Gb before each line of the dual increment and
- * its pitch Pb}.  The paper has no counterpart: these are this library's own
+ * its pitch Pb, forward consumer warps per block (15 where 16-line chunks are
+ * sampled in two parts, whose state wants up to 128 registers a thread; 23
+ * otherwise), each block one more warp for the copies}.  The paper has no
+ * counterpart: these are this library's own
  * layouts (Sec. II-A defines only the operators).  MC_EINVAL for a geometry
  * mc_create refuses. */
 mc_status mc_plan_shapes(const mc_geometry* geom, int32_t sms, int32_t* out);

@@ -1385,7 +1385,8 @@ mc_status mc_plan_shapes(const mc_geometry* geom, int32_t sms, int32_t* out)
         geom->n_bins > 8192)
         return MC_EINVAL;
     const Shapes sh = choose_shapes(geom->n, geom->n_bins, sms);
-    const int32_t v[9] = {sh.guard, sh.P, sh.lines, sh.lc, sh.cl, sh.ring, sh.pj, sh.Gb, sh.Pb};
+    const int32_t v[10] = {sh.guard, sh.P,  sh.lines, sh.lc, sh.cl, sh.ring,
+                           sh.pj,    sh.Gb, sh.Pb,    forward_warps(sh.lc, sh.cl)};
     std::memcpy(out, v, sizeof v);
     return MC_OK;
 }

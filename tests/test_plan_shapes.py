@@ -18,10 +18,10 @@ FORWARD_SHAPES = {(2, 5, 2), (4, 5, 4), (8, 5, 8), (8, 3, 8), (16, 3, 16), (16, 
 def plan(n, na=180, nb=None, sms=SMS):
     nb = nb if nb is not None else n + 17
     lib = N.load()
-    out = (ctypes.c_int32 * 9)()
+    out = (ctypes.c_int32 * 10)()
     geom = N.mc_geometry(n, na, nb)
     st = lib.mc_plan_shapes(ctypes.byref(geom), sms, out)
-    return st, dict(zip(("guard", "P", "lines", "lc", "cl", "ring", "pj", "Gb", "Pb"), list(out)))
+    return st, dict(zip(("guard", "P", "lines", "lc", "cl", "ring", "pj", "Gb", "Pb", "warps"), list(out)))
 
 
 def bp_window(pj):
@@ -39,6 +39,9 @@ def test_shape_invariants(n):
     assert s["ring"] * s["lc"] * s["P"] * 8 <= RING_BYTES
     assert s["pj"] in (4, 8, 14, 16, 28)
     assert s["Pb"] >= n + 17 + 2 * s["Gb"] and bp_window(s["pj"]) <= s["Pb"]
+    # two-part chunks carry two parts' state: fewer warps with more registers each
+    assert s["warps"] == (15 if (s["lc"], s["cl"]) == (16, 8) else 23)
+    assert 32 * (s["warps"] + 1) <= 1024
 
 
 def test_measured_choices_at_the_benchmark_sizes():
@@ -46,7 +49,7 @@ def test_measured_choices_at_the_benchmark_sizes():
         128: dict(guard=33, lc=16, cl=16, ring=3),     # whole 16-line chunks (-9% per epoch)
         256: dict(guard=33, lc=16, cl=16, ring=3),
         384: dict(guard=33, lc=16, cl=16, ring=3),
-        512: dict(guard=17, P=548, lc=16, cl=8, ring=3, pj=28),   # two-part chunks, 28-row tiles
+        512: dict(guard=17, P=548, lc=16, cl=8, ring=3, pj=28, warps=15),   # two-part chunks, 28-row tiles
         768: dict(guard=17, lc=8, cl=8, ring=3, pj=16),
         1024: dict(guard=17, lc=8, cl=8, ring=3, pj=28),
         2048: dict(guard=17, lc=2, cl=2, ring=5),
@@ -64,6 +67,6 @@ def test_plan_refuses_what_create_refuses():
         st, _ = plan(n, na, nb)
         assert st == N.MC_EINVAL
     lib = N.load()
-    out = (ctypes.c_int32 * 9)()
+    out = (ctypes.c_int32 * 10)()
     assert lib.mc_plan_shapes(None, SMS, out) == N.MC_EINVAL
     assert lib.mc_plan_shapes(ctypes.byref(N.mc_geometry(64, 8, 8)), 0, out) == N.MC_EINVAL
