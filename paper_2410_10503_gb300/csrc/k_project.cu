@@ -13,7 +13,9 @@
 // 16-line chunks and for 8-line chunks of large images); the consumer warps
 // wait on the chunk's "full" mbarrier and release it through its "empty"
 // mbarrier, so warps drift by up to NS - 1 chunks instead of meeting at a
-// block barrier every chunk.
+// block barrier every chunk.  A block has W consumer warps (forward_warps: 15
+// where 16-line chunks are sampled in two parts, whose state takes up to 128
+// registers a thread; 23 at 80 registers for every other shape).
 //
 // A group visits only the chunks its rays cross.  A sample is an FMA for the
 // position, one round-down add whose bits give both floor and shared address,
@@ -30,8 +32,9 @@
 // ui + CL, so every lane stays inside its line (at most index
 // G + n + 2 CL - 1 <= P - 1); and a lane is clamped only when all of its
 // samples in the part fall on zero pairs (indices up to 2 CL - 1 <= G - 2 in
-// front, from G + n behind), where the clamped samples read zeros too.  So the rays of a group that leave the image inside a chunk, or miss
-// it, need no predication and no separate edge path.
+// front, from G + n behind), where the clamped samples read zeros too.  So
+// the rays of a group that leave the image inside a chunk, or miss it, need
+// no predication and no separate edge path.
 #include "mc_kernels.h"
 
 namespace mcg {
