@@ -468,6 +468,15 @@ const char* mc_version(void);
  * mc_create refuses. */
 mc_status mc_plan_shapes(const mc_geometry* geom, int32_t sms, int32_t* out);
 
+/* The launch shapes and layouts the context uses now, in mc_plan_shapes'
+ * order (host, 10 int32): at creation they equal mc_plan_shapes for the
+ * context's geometry and device; MC_OPT_FORWARD_LINES,
+ * MC_OPT_BACKPROJECT_ROWS and mc_autotune change the chunk lines (with the
+ * part lines, ring stages and consumer warps that follow from them) and the
+ * rows per thread.  The subset launches' own options (MC_OPT_SUBSET_*) are not
+ * reported.  Reads host state only.  MC_EINVAL for a NULL argument. */
+mc_status mc_get_shapes(const mc_ctx* ctx, int32_t* out);
+
 /* Allocation-free forward operator, for callers that must not allocate
  * device memory (code running inside an allocator hook, a plugin with a
  * fixed memory budget, or a host whose GPU memory is already owned by its

@@ -23,7 +23,8 @@ import numpy as np
 
 from . import _native as N
 
-__all__ = ["Context", "Batch", "MCError", "lib", "version", "project_gate", "batch_spdhg_run", "shared_load_peak"]
+__all__ = ["Context", "Batch", "MCError", "lib", "version", "project_gate", "batch_spdhg_run", "shared_load_peak",
+           "plan_shapes"]
 
 try:  # torch is plumbing here (device memory, streams); optional for host arrays
     import torch
@@ -43,6 +44,21 @@ def lib():
 
 def version() -> str:
     return lib().mc_version().decode()
+
+
+SHAPE_KEYS = ("guard", "pitch", "layout_lines", "lines_per_chunk", "lines_per_part", "ring_stages",
+              "rows_per_thread", "dual_guard", "dual_pitch", "consumer_warps")
+
+
+def plan_shapes(n: int, n_angles: int, n_bins: int, sms: int) -> dict:
+    """The launch shapes and layouts a context of this geometry gets on a GPU
+    with `sms` SMs (mc_plan_shapes; host only, no device needed)."""
+    out = np.zeros(len(SHAPE_KEYS), np.int32)
+    st = lib().mc_plan_shapes(ctypes.byref(N.mc_geometry(int(n), int(n_angles), int(n_bins))), int(sms),
+                              out.ctypes.data)
+    if st != 0:
+        raise MCError(st, f"no shapes for n={n}, n_angles={n_angles}, n_bins={n_bins}, sms={sms}")
+    return dict(zip(SHAPE_KEYS, out.tolist()))
 
 
 def _is_tensor(a) -> bool:
@@ -369,6 +385,13 @@ class Context:
 
     def set_option(self, option: int, value: int):
         self._check(self._L.mc_set_option(self._h, option, int(value)))
+
+    def shapes(self) -> dict:
+        """The launch shapes and layouts this context uses now (mc_get_shapes),
+        keyed as plan_shapes."""
+        out = np.zeros(len(SHAPE_KEYS), np.int32)
+        self._check(self._L.mc_get_shapes(self._h, out.ctypes.data))
+        return dict(zip(SHAPE_KEYS, out.tolist()))
 
     def autotune(self, reps: int = 5) -> dict:
         """Time the projectors' launch shapes on this geometry and keep the

@@ -73,6 +73,7 @@ SIGNATURES = {
     "mc_load_state": (_I32, [_VP, _VP, _U64]),
     "mc_version": (ctypes.c_char_p, []),
     "mc_plan_shapes": (_I32, [ctypes.POINTER(mc_geometry), _I32, _VP]),
+    "mc_get_shapes": (_I32, [_VP, _VP]),
     "mc_measure_shared_load_peak": (_I32, [_I32, _VP]),
     "mc_forward_static": (_I32, [ctypes.POINTER(mc_geometry), _VP, _VP, _VP, _VP, ctypes.c_char_p, _I32]),
     "mc_forward_static_status": (_I32, [_VP, ctypes.c_char_p, _I32]),

@@ -1391,6 +1391,16 @@ mc_status mc_plan_shapes(const mc_geometry* geom, int32_t sms, int32_t* out)
     return MC_OK;
 }
 
+mc_status mc_get_shapes(const mc_ctx* c, int32_t* out)
+{
+    if (!c || !out) return MC_EINVAL;
+    const int cl = forward_part_lines(c->lc, c->guard);
+    const int32_t v[10] = {c->guard, c->P,  layout_lines(c->n), c->lc, cl, forward_ring(c->lc, c->P),
+                           c->pj,    c->Gb, c->Pb,              forward_warps(c->lc, cl)};
+    std::memcpy(out, v, sizeof v);
+    return MC_OK;
+}
+
 const char* mc_last_error(const mc_ctx* ctx)
 {
     if (ctx) return ctx->err.c_str();

@@ -250,12 +250,30 @@ def test_forward_chunk_sizes_match_oracle(mc, n, na, nb, lc):
     rig = _rigid(2, 41, rot=8.0, shift=6.0)
     ctx = mc.Context(n, na, nb, 2, rigid=rig)
     ctx.set_option(N.MC_OPT_FORWARD_LINES, lc)
+    sh = ctx.shapes()
+    two_parts = lc == 16 and sh["guard"] == 17
+    assert sh["lines_per_chunk"] == lc and sh["lines_per_part"] == (8 if two_parts else lc)
+    assert sh["consumer_warps"] == (15 if two_parts else 23)
     P = O.Problem(g, O.Motion(rigid=rig), np.zeros((2, na, nb)), 1.0)
     x = S.phantom(n, 6, 42, n / 16 + 0.5, n / 4 + 1)
     y = S.random_sinogram(na, nb, 43)
     assert rel_l2(host(ctx.project(cuda(x))), O.A(x, g)) <= TOL
     assert rel_l2(host(ctx.forward(1, cuda(x))), O.Ai(x, P, 1)) <= TOL
     assert rel_l2(host(ctx.adjoint(1, cuda(y))), O.Ait(y, P, 1)) <= TOL
+    ctx.close()
+
+
+@pytest.mark.parametrize("n,na,nb", [(16, 8, 23), (96, 30, 101), (384, 24, 401), (512, 20, 517),
+                                     (520, 8, 537), (768, 12, 785), (1024, 6, 1041), (2048, 5, 2900)])
+def test_context_shapes_match_plan(mc, n, na, nb):
+    """A new context uses the shapes mc_plan_shapes computes on the host for
+    its geometry and this GPU's SM count, and they drive its launches: the
+    projection at those shapes matches the oracle."""
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ctx = mc.Context(n, na, nb, 1, rigid=np.zeros((1, 3)))
+    assert ctx.shapes() == mc.plan_shapes(n, na, nb, sms)
+    x = S.phantom(n, 6, 44, n / 16 + 0.5, n / 4 + 1)
+    assert rel_l2(host(ctx.project(cuda(x))), O.A(x, O.Geometry(n, na, nb))) <= TOL
     ctx.close()
 
 
@@ -279,6 +297,7 @@ def test_backprojection_tile_heights_match_oracle(mc, n, na, nb, rows):
     rig = _rigid(2, 51, rot=8.0, shift=6.0)
     ctx = mc.Context(n, na, nb, 2, rigid=rig)
     ctx.set_option(N.MC_OPT_BACKPROJECT_ROWS, rows)
+    assert ctx.shapes()["rows_per_thread"] == rows
     P = O.Problem(g, O.Motion(rigid=rig), np.zeros((2, na, nb)), 1.0)
     y = S.random_sinogram(na, nb, 52)
     assert rel_l2(host(ctx.backproject(cuda(y))), O.At(y, g)) <= TOL

@@ -170,3 +170,30 @@ def test_subset_launch_shapes_and_autotune(mc, case):
         with pytest.raises(mc.MCError):
             ctx.set_option(opt, bad)
     ctx.close()
+
+
+def test_two_part_chunks_in_subset_launches(mc):
+    """At 512^2 the layouts keep the narrow guard and the forward streams
+    16-line chunks sampled in two 8-line parts with 15 consumer warps; the
+    subset launches run its banded instance.  64 angles x 529 bins, N = 2
+    rigid gates, S = 4 subsets of 16 angles, 4 epochs against the oracle's
+    block SPDHG, at 1 and 4 line bands."""
+    import ctypes
+    from paper_2410_10503_gb300 import _native as N
+    W = S.WORKLOADS["rigid512"].scaled(n=512, n_angles=64, n_bins=529, n_gates=2)
+    out = (ctypes.c_int32 * 10)()
+    assert N.load().mc_plan_shapes(ctypes.byref(N.mc_geometry(W.n, W.n_angles, W.n_bins)), 152, out) == 0
+    assert (out[0], out[3], out[4], out[9]) == (17, 16, 8, 15)       # guard, chunk, part, warps
+    P, sd = problem(W, "rigid")
+    Ssub, E = 4, 4
+    nb2 = O.block_norms2(P, Ssub, iters=8)      # only sets the step sizes, which both sides share
+    ref = O.spdhg(P, E, O.step_sizes(nb2[:-1].max(), P.alpha, P.N, P.N * Ssub), seed=sd["gates"],
+                  subsets=Ssub)
+    for bands in (1, 4):
+        ctx = context(mc, P)
+        ctx.set_subsets(Ssub)
+        ctx.set_norms(nb2)
+        ctx.set_option(N.MC_OPT_SUBSET_BANDS, bands)
+        x, _ = ctx.spdhg_run(E, seed=sd["gates"])
+        assert rel_l2(x, ref.x) <= 1e-4, bands
+        ctx.close()

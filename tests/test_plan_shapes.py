@@ -70,3 +70,12 @@ def test_plan_refuses_what_create_refuses():
     out = (ctypes.c_int32 * 10)()
     assert lib.mc_plan_shapes(None, SMS, out) == N.MC_EINVAL
     assert lib.mc_plan_shapes(ctypes.byref(N.mc_geometry(64, 8, 8)), 0, out) == N.MC_EINVAL
+
+
+def test_python_plan_shapes():
+    import paper_2410_10503_gb300 as M
+    sh = M.plan_shapes(512, 720, 729, SMS)
+    assert sh == dict(zip(M.SHAPE_KEYS, plan(512, 720, 729)[1].values()))
+    assert (sh["lines_per_chunk"], sh["lines_per_part"], sh["consumer_warps"], sh["rows_per_thread"]) == (16, 8, 15, 28)
+    with pytest.raises(M.MCError):
+        M.plan_shapes(4096, 8, 8, SMS)
