@@ -3046,7 +3046,8 @@ mc_status mc_batch_run(mc_batch* b, int32_t epochs, const mc_sampling* sampling,
         if (now != b->shape[q]) {
             if (failed) *failed = b->order[q];
             return bfail(b, MC_ESTATE, "slice %d: its launch shapes changed after mc_batch_create "
-                                      "(mc_autotune or mc_set_subsets); create the batch again", b->order[q]);
+                                      "(mc_autotune, mc_set_subsets or a shape option); create the batch again",
+                         b->order[q]);
         }
     }
     if (epochs == 0) return MC_OK;

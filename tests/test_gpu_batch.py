@@ -183,6 +183,11 @@ def test_merged_batch_refuses_changed_launch_shapes(mc, merged_slices):
             b.run(1, seeds=[1, 2])
     with mc.Batch([a, c]) as b:             # a new batch takes them
         b.run(1, seeds=[1, 2])
+        from paper_2410_10503_gb300 import _native as N
+        rows = 8 if c.shapes()["rows_per_thread"] != 8 else 14
+        c.set_option(N.MC_OPT_BACKPROJECT_ROWS, rows)      # so does a shape option
+        with pytest.raises(mc.MCError, match="launch shapes"):
+            b.run(1, seeds=[1, 2])
     a.close()
     c.close()
 
