@@ -816,9 +816,11 @@ struct GroupTable {
 };
 
 void group_chunk_costs(const mc_ctx* c, int k, int b0, int lc, std::vector<float>& cost);
+double load_wavefronts(const mc_ctx* c, int k);
 
-void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vector<double>& inv_k,
-                  const std::vector<double>& t_k, int S, int lc, GroupTable& gt)
+// The ray groups of the context's angle order (c->order), S subsets after
+// one another, each with its estimated cost in the forward at lc-line chunks.
+void build_groups(const mc_ctx* c, int S, int lc, GroupTable& gt)
 {
     const int na = c->na, nb = c->nb;
     const int gpa = (nb + 31) / 32;                        // groups per angle
@@ -830,15 +832,13 @@ void build_groups(const mc_ctx* c, const std::vector<int>& order, const std::vec
     gt.cum.reserve((size_t)na * gpa + 1);
     for (int sub = 0; sub < S; ++sub) {
         std::array<long long, 3> set{(long long)gt.groups.size(), -1, 0};
-        for (int k : order) {
+        for (int k : c->order) {
             if (k % S != sub) continue;
             const bool xd = (na <= 4 * k) && (4 * k <= 3 * na);
             if (xd && set[1] < 0) set[1] = (long long)gt.groups.size();
-            // a half-warp's 64-bit load (16 consecutive bins, |inv| pairs apart)
-            // takes about wf = 1 + min(1, 15 (|inv| - 1)) shared-memory
-            // wavefronts: one near the driving axis, two from ~20 degrees on.
-            // Measured block times on rigid512 fit chunks x (2.8 + wf) (R^2 0.91)
-            const double wf = 1.0 + std::min(1.0, 15.0 * (std::fabs(inv_k[k]) - 1.0));
+            // measured block times on rigid512 fit chunks x (2.8 + wf) (R^2
+            // 0.91), wf the wavefronts of a half-warp's 64-bit load
+            const double wf = load_wavefronts(c, k);
             for (int g = 0; g < gpa; ++g) {
                 // the work k_forward does for the group: all 32 lanes over every
                 // chunk of the union of its rays' line ranges, each chunk
@@ -1230,7 +1230,7 @@ mc_status build_tables(mc_ctx* c)
     c->t_k = t_k;
     fa = fwd_angles(c, forward_part_lines(c->lc, c->guard));
     GroupTable gt;
-    build_groups(c, order, inv_k, t_k, 1, c->lc, gt);
+    build_groups(c, 1, c->lc, gt);
     std::vector<RayItem> items;
     std::vector<int> set_off;
     int rpt = 2, ipb = 1;
@@ -1698,7 +1698,7 @@ mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min, 
 {
     std::vector<FwdAngle> fa = fwd_angles(c, forward_part_lines(lc, c->guard));
     GroupTable gt;
-    build_groups(c, c->order, c->inv_k, c->t_k, 1, lc, gt);
+    build_groups(c, 1, lc, gt);
     std::vector<RayItem> items;
     std::vector<int> off;
     int ipb = 1, rpt = 2;
@@ -1861,7 +1861,7 @@ mc_status mc_set_subsets(mc_ctx* c, int32_t subsets)
         // into ~SMs / B ranges, each repeated for every band
         const int bands = c->bands_opt > 0 ? c->bands_opt : std::min(8, std::max(1, subsets / 2));
         GroupTable gt;
-        build_groups(c, c->order, c->inv_k, c->t_k, subsets, c->lc, gt);
+        build_groups(c, subsets, c->lc, gt);
         std::vector<RayItem> cut;
         std::vector<int> cut_off;
         int ipb = 1, rpt = 2;
@@ -2968,7 +2968,7 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream,
             }
             b->b_owned[q] = 1;
             GroupTable gt;
-            build_groups(c, c->order, c->inv_k, c->t_k, 1, c->lc, gt);
+            build_groups(c, 1, c->lc, gt);
             std::vector<RayItem> items;
             std::vector<int> off;
             int ipb = 1, rpt = 2;
