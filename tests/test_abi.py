@@ -93,6 +93,7 @@ def test_null_context_calls_fail_cleanly(built):
     assert L.mc_autotune(None, 1, None) == N.MC_EINVAL
     assert L.mc_batch_spdhg_run(None, 0, 1, None, None) == N.MC_EINVAL
     assert L.mc_vjp(None, 0, None, None, None, None) == N.MC_EINVAL
+    assert L.mc_get_shapes(None, None) == N.MC_EINVAL
     L.mc_destroy(None)
 
 
