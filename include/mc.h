@@ -129,13 +129,15 @@ enum {
                                     4, 8, 14, 16 or 28); results change within float32
                                     rounding. */
     MC_OPT_FORWARD_LINES = 8,    /* lines per staged chunk of the forward projector
-                                    (2, 4, 8 or 16; the ring holds up to 5 chunks in
-                                    the shared memory a block may use, 16-line chunks
-                                    of large images fewer, and at least 2 must fit;
-                                    16 needs the image side rounded up to 8 to be a
-                                    multiple of 16): the forward's work items are cut
-                                    again for it (mc_autotune also tries every size).
-                                    Results change within float32 rounding. */
+                                    (2, 4, 8 or 16): its ring, in the shared memory a
+                                    block may use, holds 5 chunks, or 3 for 16-line
+                                    chunks and for 8-line chunks of large images, and
+                                    must fit (16-line chunks: images up to 528^2;
+                                    MC_EINVAL otherwise); 16 also needs the image side
+                                    rounded up to 8 to be a multiple of 16.  The
+                                    forward's work items are cut again for it
+                                    (mc_autotune also tries every size).  Results
+                                    change within float32 rounding. */
     MC_OPT_BACKPROJECT_ROWS = 9  /* rows per thread of the backprojection tiles (4, 8,
                                     14, 16: four blocks of 8 warps per SM; 28: two),
                                     overriding the creation-time choice (the grid
