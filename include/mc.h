@@ -215,13 +215,13 @@ mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out)
 /* Tune the launch shapes of the two projectors for this context's geometry
  * by timing them on the device (each candidate `reps` launches after one
  * warm-up, CUDA events on the context's stream): the forward's lines per
- * staged chunk (2, 4, 8, 16, as the layouts and shared memory allow), work items per block and
- * ray-group slots per warp, and the backprojector's rows per thread (4, 8,
- * 14, 16, 28).  The fastest setting is kept; results are unchanged bit for bit by
- * the item split and change within float32 rounding with the chunk size and
- * rows per thread.  out (nullable, host, 4 int32): {lines per chunk, items per
- * block, group slots per warp, rows per thread}.  Captured epoch graphs are
- * dropped.  The creation-time choice is a heuristic (the longest chunk whose
+ * staged chunk (2, 4, 8, 16, as the layouts and shared memory allow), work
+ * items per block and ray-group slots per warp, and the backprojector's rows
+ * per thread (4, 8, 14, 16, 28).  The fastest setting is kept; results are
+ * unchanged bit for bit by the item split and change within float32 rounding
+ * with the chunk size and rows per thread.  out (nullable, host, 4 int32):
+ * {lines per chunk, items per block, group slots per warp, rows per thread}.
+ * Captured epoch graphs are dropped.  The creation-time choice is a heuristic (the longest chunk whose
  * ring fits, fewest items, and the tile height whose grid fills every SM's
  * resident blocks with the least work on the busiest SM).  With angle
  * subsets (mc_set_subsets, S > 1) it also picks the subset forward's line
@@ -250,8 +250,8 @@ mc_status mc_set_subsets(mc_ctx* ctx, int32_t subsets);
  * pull-back warp by u_i).  field: 2 x n x n {ux (column), uy (row)} in px,
  * host or device, copied; values must be finite with |u| <= 1e5.  Rebuilds
  * that gate's D_i^T CSR in place, without allocating (every gate owns a
- * fixed slice of 4 n^2 entries, the most its taps can need).  A_i changes, so the
- * squared norms, the step sizes and x* are dropped: call mc_norms or
+ * fixed slice of 4 n^2 entries, the most its taps can need).  A_i changes,
+ * so the squared norms, the step sizes and x* are dropped: call mc_norms or
  * mc_set_norms (and mc_set_reference) again before the next run.  The
  * iterates are kept (a warm start).  MC_ESTATE for rigid-motion contexts. */
 mc_status mc_set_field(mc_ctx* ctx, int32_t gate, const float* field);
