@@ -221,9 +221,10 @@ mc_status mc_warp_adjoint(mc_ctx* ctx, int32_t gate, const float* v, float* out)
  * unchanged bit for bit by the item split and change within float32 rounding
  * with the chunk size and rows per thread.  out (nullable, host, 4 int32):
  * {lines per chunk, items per block, group slots per warp, rows per thread}.
- * Captured epoch graphs are dropped.  The creation-time choice is a heuristic (the longest chunk whose
- * ring fits, fewest items, and the tile height whose grid fills every SM's
- * resident blocks with the least work on the busiest SM).  With angle
+ * Captured epoch graphs are dropped.  The creation-time choice is a
+ * heuristic (the longest chunk whose ring fits, fewest items, and the tile
+ * height whose grid fills every SM's resident blocks with the least work on
+ * the busiest SM).  With angle
  * subsets (mc_set_subsets, S > 1) it also picks the subset forward's line
  * bands (MC_OPT_SUBSET_BANDS: 1, 2, 3, 4, 6 or 8, timed on the S blocks of
  * gate 0) and leaves the option at that value; norms, step sizes and
