@@ -470,9 +470,8 @@ const char* mc_version(void);
  * its pitch Pb, forward consumer warps per block (15 where 16-line chunks are
  * sampled in two parts, whose state wants up to 128 registers a thread; 23
  * otherwise), each block one more warp for the copies}.  The paper has no
- * counterpart: these are this library's own
- * layouts (Sec. II-A defines only the operators).  MC_EINVAL for a geometry
- * mc_create refuses. */
+ * counterpart: these are this library's own layouts (Sec. II-A defines only
+ * the operators).  MC_EINVAL for a geometry mc_create refuses. */
 mc_status mc_plan_shapes(const mc_geometry* geom, int32_t sms, int32_t* out);
 
 /* The launch shapes and layouts the context uses now, in mc_plan_shapes'
@@ -502,9 +501,9 @@ mc_status mc_get_shapes(const mc_ctx* ctx, int32_t* out);
  * attributes); make that first call before any stream capture (a first call
  * inside a capture returns MC_ESTATE).  Every later call made outside a
  * capture looks the address up again, so a device reset by the host
- * application leaves no stale pointer.  Every call
- * shares the array: calls that overlap on the GPU (different streams, or
- * different host threads) race and must be serialised by the caller.  Work
+ * application leaves no stale pointer.  Every call shares the array: calls
+ * that overlap on the GPU (different streams, or different host threads)
+ * race and must be serialised by the caller.  Work
  * is ordered on cuda_stream (NULL = legacy default stream) and the call
  * returns before it completes.  err (nullable, err_cap bytes) receives a
  * message when the call itself fails (arguments, sizes, launches).  A
