@@ -176,14 +176,17 @@ def test_merged_batch_refuses_changed_launch_shapes(mc, merged_slices):
     a = make_ctx(mc, P, nrm)
     W2, P2, sd2, nrm2 = merged_slices[2]
     c = make_ctx(mc, P2, nrm2)
+    from paper_2410_10503_gb300 import _native as N
     with mc.Batch([a, c]) as b:
         b.run(1, seeds=[1, 2])
-        a.autotune(reps=1)                  # new forward tables after the batch was made
+        # new forward tables after the batch was made (a chunk size other than
+        # the current one, so that the change does not depend on timings)
+        lc = 8 if a.shapes()["lines_per_chunk"] != 8 else 16
+        a.set_option(N.MC_OPT_FORWARD_LINES, lc)
         with pytest.raises(mc.MCError, match="launch shapes"):
             b.run(1, seeds=[1, 2])
     with mc.Batch([a, c]) as b:             # a new batch takes them
         b.run(1, seeds=[1, 2])
-        from paper_2410_10503_gb300 import _native as N
         rows = 8 if c.shapes()["rows_per_thread"] != 8 else 14
         c.set_option(N.MC_OPT_BACKPROJECT_ROWS, rows)      # so does a shape option
         with pytest.raises(mc.MCError, match="launch shapes"):
