@@ -377,10 +377,11 @@ mc_status mc_batch_spdhg_run(mc_ctx* const* ctxs, int32_t count, int32_t epochs,
  * slice's share of a merged launch is small (a block then streams the
  * slice's image once for more ray groups); these serve while the slices in
  * flight give every SM at least four such blocks, the slices' own items
- * otherwise (results do not depend on the cut).  Launch shapes changed after
- * creation (mc_autotune, mc_set_subsets, MC_OPT_FORWARD_LINES,
- * MC_OPT_BACKPROJECT_ROWS) make mc_batch_run return MC_ESTATE: create the
- * batch again.
+ * otherwise (results do not depend on the cut).  After a call that rebuilds
+ * a slice's forward tables or sets its launch shapes (mc_autotune,
+ * MC_OPT_FORWARD_LINES, MC_OPT_BACKPROJECT_ROWS), even to the values it had,
+ * mc_batch_run returns MC_ESTATE: create the batch again.  Slices with angle
+ * subsets (mc_set_subsets, S > 1) are refused too.
  * mc_batch_run runs `epochs` SPDHG epochs of every slice (slice i: epochs x
  * N_i iterations, sampling[i] as in mc_spdhg_run, p included); slices with
  * fewer gates finish first and leave the launches.  Per slice the result is

@@ -93,6 +93,8 @@ struct mc_ctx {
     RayItem* d_items = nullptr;
     int n_items = 0, ipb = 1, rpt = 1, lc = 1, P = 0, Gb = 0, Pb = 0, pj = 4;
     int guard = kGuardNarrow;         // zero pairs around each layout line (layout_guard)
+    uint64_t tables_gen = 0;          // bumped whenever the forward tables or the launch
+                                      // shapes change (batches made before refuse to run)
     size_t layout_stride = 0, dy_stride = 0;
     std::vector<int> order;           // angles, rows-driven first
     std::vector<double> inv_k, t_k;   // per angle: 1/|sin| or 1/|cos|, and the slope
@@ -1718,6 +1720,7 @@ mc_status install_forward_tables(mc_ctx* c, int lc, int ipb_start, int rpt_min, 
     c->ipb = ipb;
     c->rpt = rpt;
     c->n_items = (int)items.size();
+    ++c->tables_gen;
     return MC_OK;
 }
 
@@ -1798,6 +1801,7 @@ mc_status mc_autotune(mc_ctx* c, int32_t reps, int32_t* out)
         if (st == MC_OK && ms < best_bp) { best_bp = ms; best_pj = pj; }
     }
     c->pj = best_pj;
+    ++c->tables_gen;
     // with angle subsets: the subset forward's line bands, its tables rebuilt
     // for each candidate and timed on the S blocks of gate 0 (forward, then
     // backprojection, block after block as in an epoch); norms and step sizes
@@ -2328,6 +2332,7 @@ mc_status mc_set_option(mc_ctx* c, int32_t option, int64_t value)
         CK(cudaStreamSynchronize(c->stream));
         drop_graphs(c);
         c->pj = (int)value;
+        ++c->tables_gen;
         return MC_OK;
     case MC_OPT_SUBSET_ROWS:
         if (value != 0 && value != 4 && value != 8 && value != 14 && value != 16 && value != 28)
@@ -2543,7 +2548,9 @@ struct mc_batch {
     std::vector<RayItem*> d_bitems;
     std::vector<int> b_nitems, b_rpt;
     std::vector<char> b_owned;              // 0: the slice's own tables serve (no coarser cut)
-    std::vector<std::array<long long, 5>> shape;   // each context's tables at creation
+    // each context's table generation, item count, chunk lines, rows per
+    // thread and group slots at creation
+    std::vector<std::array<long long, 5>> shape;
     BpArgs* d_bp[2] = {nullptr, nullptr};
     WarpAdjArgs* d_wadj[2] = {nullptr, nullptr};
     BatchDraw* d_draw = nullptr;
@@ -2951,7 +2958,7 @@ mc_status mc_batch_create(mc_ctx* const* ctxs, int32_t count, void* cuda_stream,
         b->b_owned.assign(count, 0);
         for (int q = 0; q < count; ++q) {
             const mc_ctx* c = b->ctx[b->order[q]];
-            b->shape.push_back({(long long)(uintptr_t)c->d_items, c->n_items, c->lc, c->pj, c->rpt});
+            b->shape.push_back({(long long)c->tables_gen, c->n_items, c->lc, c->pj, c->rpt});
         }
         for (int q = 0; q < count && st == MC_OK; ++q) {
             mc_ctx* c = b->ctx[b->order[q]];
@@ -3042,11 +3049,11 @@ mc_status mc_batch_run(mc_batch* b, int32_t epochs, const mc_sampling* sampling,
     }
     for (int q = 0; q < B; ++q) {
         const mc_ctx* c = b->ctx[b->order[q]];
-        const std::array<long long, 5> now{(long long)(uintptr_t)c->d_items, c->n_items, c->lc, c->pj, c->rpt};
+        const std::array<long long, 5> now{(long long)c->tables_gen, c->n_items, c->lc, c->pj, c->rpt};
         if (now != b->shape[q]) {
             if (failed) *failed = b->order[q];
             return bfail(b, MC_ESTATE, "slice %d: its launch shapes changed after mc_batch_create "
-                                      "(mc_autotune, mc_set_subsets or a shape option); create the batch again",
+                                      "(mc_autotune or a shape option); create the batch again",
                          b->order[q]);
         }
     }
