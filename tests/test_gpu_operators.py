@@ -216,13 +216,15 @@ def test_autotune_keeps_parity(mc):
     x = S.phantom(n, 10, 22, 5, 40)
     y = S.random_sinogram(na, nb, 23)
     t = ctx.autotune(reps=2)
-    assert t["lines_per_chunk"] in (2, 4, 8, 16) and t["rows_per_thread"] in (4, 8, 14, 16)
+    assert t["lines_per_chunk"] in (2, 4, 8, 16) and t["rows_per_thread"] in (4, 8, 14, 16, 28)
+    assert ctx.shapes()["lines_per_chunk"] == t["lines_per_chunk"]
+    assert ctx.shapes()["rows_per_thread"] == t["rows_per_thread"]
     assert t["group_slots"] in (2, 4, 8) and t["items_per_block"] >= 1
     for i in range(N):
         assert rel_l2(host(ctx.forward(i, cuda(x))), O.Ai(x, P, i)) <= TOL
         assert rel_l2(host(ctx.adjoint(i, cuda(y))), O.Ait(y, P, i)) <= TOL
     fresh = mc.Context(n, na, nb, N, rigid=rig)
-    if t["lines_per_chunk"] == 16:     # the creation-time chunk at 128^2 (wide guard, 5-stage ring)
+    if t["lines_per_chunk"] == 16:     # the creation-time chunk at 128^2 (wide guard, 3-stage ring)
         np.testing.assert_array_equal(host(ctx.forward(1, cuda(x))), host(fresh.forward(1, cuda(x))))
 
 
